@@ -1,0 +1,203 @@
+/*
+ * lqcd.h -- C ABI of the GB300 Wilson / domain-wall Dirac library (liblqcd.so).
+ *
+ * What is computed.  The paper this library follows (Huth, Meyer, Wettig,
+ * "Lattice QCD on a novel vector architecture", Lattice 2019) benchmarks the
+ * Wilson Dirac operator (Sec. 3.3, Fig. 4d) built on Grid's stencil/shift
+ * (Sec. 3.1) and states no formula for it.  The library implements the
+ * textbook operator with these conventions (they are the ones the FP64 CPU
+ * oracle in oracle/ is pinned to):
+ *
+ *   (D psi)(x) = (m + 4) psi(x) - 1/2 (H psi)(x),
+ *   (H psi)(x) = sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu)
+ *                       + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu) ],
+ *   D^dag = gamma_5 D gamma_5  (the same with 1 -/+ gamma swapped),
+ *
+ * Wilson r = 1, Euclidean chiral basis gamma_k = [[0,-i sigma_k],[i sigma_k,0]]
+ * (k = x,y,z), gamma_t = [[0,1],[1,0]], gamma_5 = diag(1,1,-1,-1); a hop that
+ * crosses the lattice boundary in direction mu is multiplied by bc[mu].
+ * Even-odd: parity(x) = (x0+x1+x2+x3) mod 2, a = m + 4, and the even Schur
+ * complement is  Mhat = a - 1/(4a) H_eo H_oe.  Shamir domain wall:
+ *   (D_dw psi)(s) = D_W(-M5) psi(s) + psi(s) - P- psi(s+1) - P+ psi(s-1),
+ * P+- = (1 +- gamma_5)/2, with P- psi(Ls) := -mf P- psi(0) and
+ * P+ psi(-1) := -mf P+ psi(Ls-1); D_dw^dag swaps P+ and P- and uses D_W^dag.
+ *
+ * Every function returns an int status (LQ_OK = 0, negative on error) and
+ * never aborts, exits or throws.  Argument and layout checks run before any
+ * launch; a failed check launches nothing.  CUDA errors are returned as
+ * LQ_ERR_CUDA.  Apply calls are asynchronous on the given stream; cg_solve
+ * returns after the stream has drained, because it fills lq_cg_stats.  A
+ * handle is not thread-safe.  All field pointers are DEVICE pointers owned by
+ * the caller, 16-byte aligned; outputs must not overlap inputs.
+ *
+ * ------------------------------------------------------------------ layouts
+ * lexi(x) = x0 + L0*(x1 + L1*(x2 + L2*x3)); complex numbers are (re, im).
+ *
+ * Site-major ("LQ_F64", "LQ_F32"; the documented exchange layout):
+ *   gauge   [site][mu 4][row 3][col 3][re,im]        U_mu(x): link x -> x+mu
+ *   spinor  [rhs][site][spin 4][colour 3][re,im]     (full field, V sites)
+ *   half    [rhs][cb][spin 4][colour 3][re,im]       cb = lexi/2, one parity
+ *   5-d     [s][site][spin 4][colour 3][re,im]
+ *
+ * Native (LQ_NATIVE | precision; the layout the kernels stream): one parity
+ * block of Vh = V/2 sites is a set of planes; plane k holds chunk k of every
+ * site in cb order (structure of arrays, 16-byte chunks):
+ *   LQ_F64:  12 planes x Vh x 16 B, plane k = complex number k
+ *            (spin k/3, colour k%3);
+ *   LQ_F32:   6 planes x Vh x 16 B, plane k = complex numbers 2k, 2k+1;
+ *   LQ_F16 / LQ_BF16: 3 planes x Vh x 16 B (plane k = complex 4k..4k+3,
+ *            stored divided by the site norm), then 1 plane x Vh x 4 B of
+ *            FP32 site norms (norm = max |real component| of the site).
+ * A full native field is [parity 0 block][parity 1 block]; rhs (or s) is the
+ * slowest index.  lq_field_bytes() gives every size.
+ */
+#ifndef LQCD_H
+#define LQCD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    LQ_OK = 0,
+    LQ_ERR_ARG = -1,           /* bad argument (null, range, aliasing, unsupported combination) */
+    LQ_ERR_LAYOUT = -2,        /* misaligned pointer or unsupported lattice shape */
+    LQ_ERR_CUDA = -3,          /* a CUDA runtime call or launch failed */
+    LQ_ERR_NOMEM = -4,         /* device allocation failed */
+    LQ_ERR_NOT_CONVERGED = -5, /* solver hit maxiter; x holds the best iterate */
+    LQ_ERR_BREAKDOWN = -6,     /* solver breakdown (<p,Ap> <= 0, NaN/Inf scalar) */
+    LQ_ERR_TIMEOUT = -7,       /* a bounded device-side wait ran out */
+    LQ_ERR_NAN = -8            /* NaN or Inf in an input or the residual */
+};
+
+/* Precisions; OR with LQ_NATIVE for a native-layout field. */
+enum { LQ_F64 = 0, LQ_F32 = 1, LQ_F16 = 2, LQ_BF16 = 3 };
+#define LQ_NATIVE 0x10
+
+/* parity argument of the Wilson apply calls */
+enum {
+    LQ_FULL = -1,       /* in, out: full fields;   out = D in            */
+    LQ_EVEN = 0,        /* in: odd half, out: even half; out = D_eo in = -1/2 H_eo in */
+    LQ_ODD = 1,         /* in: even half, out: odd half; out = D_oe in = -1/2 H_oe in */
+    LQ_SCHUR_EVEN = 2   /* in, out: even halves;    out = Mhat in          */
+};
+
+typedef struct {
+    int dims[4];     /* L0..L3 (x fastest); each even and >= 2, V/2 < 2^31 */
+    int bc[4];       /* +1 periodic, -1 antiperiodic; e.g. {1,1,1,-1} */
+    double mass;     /* Wilson bare mass m */
+    double r;        /* Wilson r; must be 1 (the kernels use the rank-2 spin projectors) */
+    int Ls;          /* domain-wall extent; 0 = no domain-wall operator */
+    double M5;       /* domain-wall height */
+    double mf;       /* domain-wall quark mass */
+    int compress12;  /* 1: links stored as their first two rows, row 3 = conj(row1 x row2) */
+} lq_params;
+
+typedef struct lq_handle lq_handle;
+
+/*
+ * lq_create: build a handle for one gauge field.
+ *   U       device pointer, site-major gauge field in precision U_prec (LQ_F64
+ *           or LQ_F32); read during the call only (packed into the handle's
+ *           own native copies).  The links must be SU(3) when compress12 = 1.
+ *   stream  cudaStream_t used for the packing; the call synchronises it.
+ * The handle owns its packed links (one copy per precision, made on first
+ * use) and its workspace; lq_destroy frees them.
+ */
+int lq_create(lq_handle **h, const lq_params *p, const void *U, int U_prec, void *stream);
+int lq_destroy(lq_handle *h);
+
+/*
+ * lq_field_bytes: bytes of a field in format fmt holding nrhs right-hand
+ * sides (or Ls slices) of `subset` sites: LQ_FULL (V sites), LQ_EVEN/LQ_ODD
+ * (V/2 sites); five_d != 0 multiplies by Ls (the rhs count is then ignored).
+ */
+int lq_field_bytes(const lq_handle *h, int fmt, int subset, int nrhs, int five_d, size_t *bytes);
+
+/*
+ * lq_convert: copy nrhs fields from one format to another (site-major <->
+ * native, precision change).  subset as in lq_field_bytes; five_d selects the
+ * 5-d layout.  dst and src must not overlap.  Site-major formats are
+ * LQ_F64 / LQ_F32; LQ_F16 / LQ_BF16 exist only as native formats.
+ */
+int lq_convert(lq_handle *h, void *dst, int dst_fmt, const void *src, int src_fmt, int subset, int nrhs,
+               int five_d, void *stream);
+
+/*
+ * dslash_apply / dslash_dag_apply: Wilson operator D (or D^dag) on nrhs
+ * fields, as selected by `parity` (LQ_FULL, LQ_EVEN, LQ_ODD, LQ_SCHUR_EVEN).
+ * fmt gives layout and arithmetic of in and out: LQ_F64 / LQ_F32 site-major
+ * (converted to native and back inside the call, using handle workspace), or
+ * LQ_NATIVE | p (streamed directly).  FP64 fields compute in FP64; FP32, FP16
+ * and BF16 fields compute in FP32 with links stored in the same precision.
+ */
+int dslash_apply(lq_handle *h, void *out, const void *in, int fmt, int parity, int nrhs, void *stream);
+int dslash_dag_apply(lq_handle *h, void *out, const void *in, int fmt, int parity, int nrhs, void *stream);
+
+/*
+ * dwf_dslash_apply: Shamir domain-wall operator D_dw (dagger != 0: D_dw^dag)
+ * on one 5-d field of Ls slices (lq_params.Ls), layout by fmt as above.
+ */
+int dwf_dslash_apply(lq_handle *h, void *out, const void *in, int fmt, int dagger, void *stream);
+
+/* ------------------------------------------------------------------- CG */
+
+enum {
+    LQ_OP_WILSON_NORMAL = 0,    /* A = D^dag D on full fields           */
+    LQ_OP_WILSON_EO_NORMAL = 1, /* A = Mhat^dag Mhat on even half fields */
+    LQ_OP_DWF_NORMAL = 2        /* A = D_dw^dag D_dw on 5-d fields       */
+};
+enum {
+    LQ_CG_PLAIN = 0,   /* CG in the precision of fmt (FP64 or FP32) */
+    LQ_CG_MIXED = 1,   /* FP64 defect correction around an inner CG in `inner` precision */
+    LQ_CG_BLOCK = 2,   /* block CG over nrhs right-hand sides (inner precision `inner`) */
+    LQ_CG_BATCHED = 3  /* nrhs independent CGs sharing each link load */
+};
+
+typedef struct {
+    int op;            /* LQ_OP_* */
+    int mode;          /* LQ_CG_* */
+    int fmt;           /* format of x and b (site-major or native) */
+    int nrhs;          /* number of right-hand sides (>= 1) */
+    double tol;        /* stop when |b - A x| / |b| < tol (per right-hand side) */
+    int maxiter;       /* total inner iterations allowed */
+    int inner;         /* inner precision for LQ_CG_MIXED / LQ_CG_BLOCK (LQ_F32, LQ_F16, LQ_BF16) */
+    double inner_tol;  /* relative reduction asked of each inner solve (0: library default) */
+    int x0_is_guess;   /* 1: x holds an initial guess on entry (restart); 0: start from x = 0 */
+} lq_cg_params;
+
+typedef struct {
+    int iters;                /* total operator applications of A (inner + outer) */
+    int outer_iters;          /* defect-correction restarts (0 for plain CG) */
+    int status;               /* LQ_OK or an error code for this right-hand side */
+    double true_rel_residual; /* |b - A x| / |b| recomputed in FP64 at the end */
+    double time_ms;           /* wall time of the solve */
+} lq_cg_stats;
+
+/*
+ * cg_solve: solve A x = b (A from cp->op) for cp->nrhs right-hand sides.
+ * stats must point to cp->nrhs entries.  Returns LQ_OK when every right-hand
+ * side reached tol, LQ_ERR_NOT_CONVERGED (x = best iterate) or another error.
+ */
+int cg_solve(lq_handle *h, void *x, const void *b, const lq_cg_params *cp, lq_cg_stats *stats, void *stream);
+
+/*
+ * lq_batch_cg_solve: nlat independent lattices (one handle each), each with
+ * cp->nrhs right-hand sides, solved together: every operator and vector step
+ * of all lattices is one launch of a persistent kernel walking a work list,
+ * and the iteration is captured once in a CUDA graph and replayed.  xs[i],
+ * bs[i] belong to hs[i]; stats holds nlat * cp->nrhs entries (lattice-major).
+ */
+int lq_batch_cg_solve(lq_handle **hs, int nlat, void **xs, const void **bs, const lq_cg_params *cp,
+                      lq_cg_stats *stats, void *stream);
+
+/* Human-readable text for a status code (static storage). */
+const char *lq_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LQCD_H */

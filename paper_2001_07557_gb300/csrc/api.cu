@@ -1,0 +1,405 @@
+// api.cu -- the C ABI: handle life cycle, argument/layout checks, format
+// conversion around the native hop kernels, and the Wilson / domain-wall apply
+// calls.  Every entry point returns a status and never aborts.
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "handle.h"
+
+namespace lq {
+
+cudaError_t launch_hop(int prec, const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st) {
+    switch (prec) {
+    case LQ_F64: return launch_hop_f64(a, r12, dag, epi, block, st);
+    case LQ_F32: return launch_hop_f32(a, r12, dag, epi, block, st);
+    case LQ_F16: return launch_hop_f16(a, r12, dag, epi, block, st);
+    default: return launch_hop_bf16(a, r12, dag, epi, block, st);
+    }
+}
+
+int ensure_ws(lq_handle* h, int k, size_t bytes, void** out) {
+    lq_handle::Buf& b = h->ws[k];
+    if (b.bytes < bytes) {
+        if (b.ptr) cudaFree(b.ptr);
+        b.ptr = nullptr;
+        b.bytes = 0;
+        if (cudaMalloc(&b.ptr, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            b.ptr = nullptr;
+            return LQ_ERR_NOMEM;
+        }
+        b.bytes = bytes;
+    }
+    *out = b.ptr;
+    return LQ_OK;
+}
+
+int get_links(lq_handle* h, int prec, const char** links, size_t* link_block, cudaStream_t st) {
+    const bool r12 = h->p.compress12 != 0;
+    void*& L = h->links[prec][r12];
+    const size_t lb = (size_t)link_site_bytes(prec, r12) * h->g.Vh;
+    if (!L) {
+        if (cudaMalloc(&L, lb * 8) != cudaSuccess) {
+            cudaGetLastError();
+            L = nullptr;
+            return LQ_ERR_NOMEM;
+        }
+        cudaError_t e = launch_links_to_native(prec, r12, L, h->U_prec, h->U_sm, h->g, st);
+        if (e != cudaSuccess) return LQ_ERR_CUDA;
+    }
+    *links = static_cast<const char*>(L);
+    *link_block = lb;
+    return LQ_OK;
+}
+
+static HopArgs base_args(lq_handle* h, const char* links, size_t lb) {
+    HopArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.links = links;
+    a.link_block = lb;
+    a.g = h->g;
+    return a;
+}
+
+int native_wilson_full(lq_handle* h, int prec, char* out, const char* in, int nrhs, bool dag, cudaStream_t st) {
+    const char* L;
+    size_t lb;
+    int rc = get_links(h, prec, &L, &lb, st);
+    if (rc) return rc;
+    const size_t blk = native_block_bytes(h, prec);
+    HopArgs a = base_args(h, L, lb);
+    for (int p = 0; p < 2; ++p) {
+        a.in[p] = in + (size_t)(1 - p) * blk;
+        a.x[p] = in + (size_t)p * blk;
+        a.out[p] = out + (size_t)p * blk;
+    }
+    a.in_rhs = a.out_rhs = a.x_rhs = 2 * blk;
+    a.parity0 = 0;
+    a.nparity = 2;
+    a.nrhs = nrhs;
+    a.c_hop = -0.5;
+    a.c_diag = h->p.mass + 4.0;
+    return status_of(launch_hop(prec, a, h->p.compress12 != 0, dag, EPI_DIAG, h->hop_block[prec], st));
+}
+
+int native_wilson_block(lq_handle* h, int prec, char* out, const char* in, int out_parity, int nrhs, bool dag,
+                        double c_hop, cudaStream_t st) {
+    const char* L;
+    size_t lb;
+    int rc = get_links(h, prec, &L, &lb, st);
+    if (rc) return rc;
+    const size_t blk = native_block_bytes(h, prec);
+    HopArgs a = base_args(h, L, lb);
+    a.in[out_parity] = in;
+    a.out[out_parity] = out;
+    a.in_rhs = a.out_rhs = blk;
+    a.parity0 = out_parity;
+    a.nparity = 1;
+    a.nrhs = nrhs;
+    a.c_hop = c_hop;
+    return status_of(launch_hop(prec, a, h->p.compress12 != 0, dag, EPI_HOP, h->hop_block[prec], st));
+}
+
+int native_wilson_schur(lq_handle* h, int prec, char* out, const char* in, char* tmp, int nrhs, bool dag,
+                        cudaStream_t st) {
+    // out = a in - 1/(4a) H_eo H_oe in
+    const double am = h->p.mass + 4.0;
+    int rc = native_wilson_block(h, prec, tmp, in, 1, nrhs, dag, 1.0, st);
+    if (rc) return rc;
+    const char* L;
+    size_t lb;
+    rc = get_links(h, prec, &L, &lb, st);
+    if (rc) return rc;
+    const size_t blk = native_block_bytes(h, prec);
+    HopArgs a = base_args(h, L, lb);
+    a.in[0] = tmp;
+    a.out[0] = out;
+    a.x[0] = in;
+    a.in_rhs = a.out_rhs = a.x_rhs = blk;
+    a.parity0 = 0;
+    a.nparity = 1;
+    a.nrhs = nrhs;
+    a.c_hop = -1.0 / (4.0 * am);
+    a.c_diag = am;
+    return status_of(launch_hop(prec, a, h->p.compress12 != 0, dag, EPI_DIAG, h->hop_block[prec], st));
+}
+
+int native_dwf(lq_handle* h, int prec, char* out, const char* in, bool dag, cudaStream_t st) {
+    const char* L;
+    size_t lb;
+    int rc = get_links(h, prec, &L, &lb, st);
+    if (rc) return rc;
+    const size_t blk = native_block_bytes(h, prec);
+    HopArgs a = base_args(h, L, lb);
+    for (int p = 0; p < 2; ++p) {
+        a.in[p] = in + (size_t)(1 - p) * blk;
+        a.x[p] = in + (size_t)p * blk;
+        a.out[p] = out + (size_t)p * blk;
+    }
+    a.in_rhs = a.out_rhs = a.x_rhs = 2 * blk;
+    a.parity0 = 0;
+    a.nparity = 2;
+    a.nrhs = h->p.Ls;
+    a.Ls = h->p.Ls;
+    a.mf = h->p.mf;
+    a.c_hop = -0.5;
+    a.c_diag = 5.0 - h->p.M5;
+    return status_of(launch_hop(prec, a, h->p.compress12 != 0, dag, EPI_DWF, h->hop_block[prec], st));
+}
+
+}  // namespace lq
+
+using namespace lq;
+
+namespace {
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + nb && y < x + na;
+}
+
+bool valid_fmt(int fmt) {
+    const int prec = fmt & 0xF;
+    const bool native = (fmt & LQ_NATIVE) != 0;
+    if ((fmt & ~(0xF | LQ_NATIVE)) != 0) return false;
+    if (prec < LQ_F64 || prec > LQ_BF16) return false;
+    if (!native && prec > LQ_F32) return false;
+    return true;
+}
+
+size_t field_bytes(const lq_handle* h, int fmt, int subset, int nrhs) {
+    const int prec = fmt & 0xF;
+    const bool native = (fmt & LQ_NATIVE) != 0;
+    const size_t sites = (subset == LQ_FULL ? 2 : 1) * (size_t)h->g.Vh;
+    if (native) return sites * (size_t)spinor_site_bytes(prec) * nrhs;
+    return sites * 24 * (prec == LQ_F64 ? 8 : 4) * nrhs;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+int wilson_apply(lq_handle* h, void* out, const void* in, int fmt, int parity, int nrhs, cudaStream_t st,
+                 bool dag) {
+    if (!h || !out || !in) return LQ_ERR_ARG;
+    if (!valid_fmt(fmt) || nrhs < 1) return LQ_ERR_ARG;
+    if (parity < LQ_FULL || parity > LQ_SCHUR_EVEN) return LQ_ERR_ARG;
+    if (!aligned16(out) || !aligned16(in)) return LQ_ERR_LAYOUT;
+    const int subset = parity == LQ_FULL ? LQ_FULL : LQ_EVEN;
+    const size_t nb = field_bytes(h, fmt, subset, nrhs);
+    if (overlap(out, nb, in, nb)) return LQ_ERR_ARG;
+    DeviceGuard dg(h->device);
+    const int prec = fmt & 0xF;
+    const bool native = (fmt & LQ_NATIVE) != 0;
+    const bool full = parity == LQ_FULL;
+    const int in_par = parity == LQ_FULL ? 0 : parity == LQ_SCHUR_EVEN ? 0 : 1 - parity;
+    const int out_par = parity == LQ_FULL ? 0 : parity == LQ_SCHUR_EVEN ? 0 : parity;
+    const size_t nat = field_bytes(h, prec | LQ_NATIVE, subset, nrhs);
+    const char* nin = static_cast<const char*>(in);
+    char* nout = static_cast<char*>(out);
+    int rc;
+    if (!native) {
+        void *a, *b;
+        if ((rc = ensure_ws(h, WS_IN, nat, &a)) || (rc = ensure_ws(h, WS_OUT, nat, &b))) return rc;
+        if (launch_spinor_to_native(prec, a, prec, in, h->g, full, in_par, nrhs, st) != cudaSuccess)
+            return LQ_ERR_CUDA;
+        nin = static_cast<const char*>(a);
+        nout = static_cast<char*>(b);
+    }
+    if (parity == LQ_FULL) {
+        rc = native_wilson_full(h, prec, nout, nin, nrhs, dag, st);
+    } else if (parity == LQ_SCHUR_EVEN) {
+        void* t;
+        if ((rc = ensure_ws(h, WS_TMP, nat, &t))) return rc;
+        rc = native_wilson_schur(h, prec, nout, nin, static_cast<char*>(t), nrhs, dag, st);
+    } else {
+        rc = native_wilson_block(h, prec, nout, nin, parity, nrhs, dag, -0.5, st);
+    }
+    if (rc) return rc;
+    if (!native) {
+        if (launch_spinor_from_native(prec, out, prec, nout, h->g, full, out_par, nrhs, st) != cudaSuccess)
+            return LQ_ERR_CUDA;
+    }
+    return LQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lq_create(lq_handle** hp, const lq_params* p, const void* U, int U_prec, void* stream) {
+    if (!hp || !p || !U) return LQ_ERR_ARG;
+    *hp = nullptr;
+    if (U_prec != LQ_F64 && U_prec != LQ_F32) return LQ_ERR_ARG;
+    if (!aligned16(U)) return LQ_ERR_LAYOUT;
+    long long V = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        if (p->dims[mu] < 2 || (p->dims[mu] & 1)) return LQ_ERR_LAYOUT;
+        if (p->bc[mu] != 1 && p->bc[mu] != -1) return LQ_ERR_ARG;
+        V *= p->dims[mu];
+    }
+    if (V / 2 >= (1LL << 31) / 16) return LQ_ERR_LAYOUT;  // plane offsets stay in 32-bit products
+    if (p->r != 1.0) return LQ_ERR_ARG;
+    if (p->Ls < 0 || p->Ls > 4096) return LQ_ERR_ARG;
+    lq_handle* h = new (std::nothrow) lq_handle;
+    if (!h) return LQ_ERR_NOMEM;
+    std::memset(h, 0, sizeof(*h));
+    h->p = *p;
+    for (int mu = 0; mu < 4; ++mu) {
+        h->g.L[mu] = p->dims[mu];
+        h->g.bc[mu] = p->bc[mu];
+    }
+    h->g.Lh0 = p->dims[0] / 2;
+    h->g.Vh = (int)(V / 2);
+    for (int k = 0; k < 4; ++k) h->hop_block[k] = 128;
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        delete h;
+        return LQ_ERR_CUDA;
+    }
+    h->U_prec = U_prec;
+    const size_t ub = (size_t)V * 72 * (U_prec == LQ_F64 ? 8 : 4);
+    if (cudaMalloc(&h->U_sm, ub) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return LQ_ERR_NOMEM;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(h->U_sm, U, ub, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        lq_destroy(h);
+        return LQ_ERR_CUDA;
+    }
+    *hp = h;
+    return LQ_OK;
+}
+
+int lq_destroy(lq_handle* h) {
+    if (!h) return LQ_ERR_ARG;
+    DeviceGuard dg(h->device);
+    cudaDeviceSynchronize();
+    if (h->U_sm) cudaFree(h->U_sm);
+    for (auto& l : h->links)
+        for (void* q : l)
+            if (q) cudaFree(q);
+    for (auto& b : h->ws)
+        if (b.ptr) cudaFree(b.ptr);
+    delete h;
+    return LQ_OK;
+}
+
+int lq_field_bytes(const lq_handle* h, int fmt, int subset, int nrhs, int five_d, size_t* bytes) {
+    if (!h || !bytes || !valid_fmt(fmt)) return LQ_ERR_ARG;
+    if (subset < LQ_FULL || subset > LQ_ODD) return LQ_ERR_ARG;
+    if (five_d) {
+        if (h->p.Ls < 1) return LQ_ERR_ARG;
+        *bytes = field_bytes(h, fmt, LQ_FULL, h->p.Ls);
+        return LQ_OK;
+    }
+    if (nrhs < 1) return LQ_ERR_ARG;
+    *bytes = field_bytes(h, fmt, subset, nrhs);
+    return LQ_OK;
+}
+
+int lq_convert(lq_handle* h, void* dst, int dst_fmt, const void* src, int src_fmt, int subset, int nrhs, int five_d,
+               void* stream) {
+    if (!h || !dst || !src || !valid_fmt(dst_fmt) || !valid_fmt(src_fmt)) return LQ_ERR_ARG;
+    if (subset < LQ_FULL || subset > LQ_ODD) return LQ_ERR_ARG;
+    if (!aligned16(dst) || !aligned16(src)) return LQ_ERR_LAYOUT;
+    if (five_d) {
+        if (h->p.Ls < 1) return LQ_ERR_ARG;
+        subset = LQ_FULL;
+        nrhs = h->p.Ls;
+    }
+    if (nrhs < 1) return LQ_ERR_ARG;
+    if (overlap(dst, field_bytes(h, dst_fmt, subset, nrhs), src, field_bytes(h, src_fmt, subset, nrhs)))
+        return LQ_ERR_ARG;
+    DeviceGuard dg(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool full = subset == LQ_FULL;
+    const int parity = full ? 0 : subset;
+    const int dp = dst_fmt & 0xF, sp = src_fmt & 0xF;
+    const bool dn = (dst_fmt & LQ_NATIVE) != 0, sn = (src_fmt & LQ_NATIVE) != 0;
+    cudaError_t e;
+    if (dn && sn) {
+        e = launch_native_convert(dp, dst, sp, src, h->g.Vh, nrhs * (full ? 2 : 1), st);
+    } else if (dn && !sn) {
+        e = launch_spinor_to_native(dp, dst, sp, src, h->g, full, parity, nrhs, st);
+    } else if (!dn && sn) {
+        e = launch_spinor_from_native(dp, dst, sp, src, h->g, full, parity, nrhs, st);
+    } else {
+        // site-major -> site-major precision change goes through a native FP64 copy
+        void* t;
+        int rc = ensure_ws(h, WS_IN, field_bytes(h, LQ_F64 | LQ_NATIVE, subset, nrhs), &t);
+        if (rc) return rc;
+        e = launch_spinor_to_native(LQ_F64, t, sp, src, h->g, full, parity, nrhs, st);
+        if (e == cudaSuccess) e = launch_spinor_from_native(dp, dst, LQ_F64, t, h->g, full, parity, nrhs, st);
+    }
+    return status_of(e);
+}
+
+int dslash_apply(lq_handle* h, void* out, const void* in, int fmt, int parity, int nrhs, void* stream) {
+    return wilson_apply(h, out, in, fmt, parity, nrhs, static_cast<cudaStream_t>(stream), false);
+}
+
+int dslash_dag_apply(lq_handle* h, void* out, const void* in, int fmt, int parity, int nrhs, void* stream) {
+    return wilson_apply(h, out, in, fmt, parity, nrhs, static_cast<cudaStream_t>(stream), true);
+}
+
+int dwf_dslash_apply(lq_handle* h, void* out, const void* in, int fmt, int dagger, void* stream) {
+    if (!h || !out || !in || !valid_fmt(fmt)) return LQ_ERR_ARG;
+    if (h->p.Ls < 1) return LQ_ERR_ARG;
+    if (!aligned16(out) || !aligned16(in)) return LQ_ERR_LAYOUT;
+    const size_t nb = field_bytes(h, fmt, LQ_FULL, h->p.Ls);
+    if (overlap(out, nb, in, nb)) return LQ_ERR_ARG;
+    DeviceGuard dg(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int prec = fmt & 0xF;
+    const bool native = (fmt & LQ_NATIVE) != 0;
+    const int Ls = h->p.Ls;
+    const char* nin = static_cast<const char*>(in);
+    char* nout = static_cast<char*>(out);
+    int rc;
+    if (!native) {
+        const size_t nat = field_bytes(h, prec | LQ_NATIVE, LQ_FULL, Ls);
+        void *a, *b;
+        if ((rc = ensure_ws(h, WS_IN, nat, &a)) || (rc = ensure_ws(h, WS_OUT, nat, &b))) return rc;
+        if (launch_spinor_to_native(prec, a, prec, in, h->g, true, 0, Ls, st) != cudaSuccess) return LQ_ERR_CUDA;
+        nin = static_cast<const char*>(a);
+        nout = static_cast<char*>(b);
+    }
+    rc = native_dwf(h, prec, nout, nin, dagger != 0, st);
+    if (rc) return rc;
+    if (!native) {
+        if (launch_spinor_from_native(prec, out, prec, nout, h->g, true, 0, Ls, st) != cudaSuccess)
+            return LQ_ERR_CUDA;
+    }
+    return LQ_OK;
+}
+
+const char* lq_status_string(int status) {
+    switch (status) {
+    case LQ_OK: return "ok";
+    case LQ_ERR_ARG: return "invalid argument";
+    case LQ_ERR_LAYOUT: return "unsupported layout or misaligned pointer";
+    case LQ_ERR_CUDA: return "CUDA error";
+    case LQ_ERR_NOMEM: return "out of device memory";
+    case LQ_ERR_NOT_CONVERGED: return "solver did not converge";
+    case LQ_ERR_BREAKDOWN: return "solver breakdown";
+    case LQ_ERR_TIMEOUT: return "device-side wait timed out";
+    case LQ_ERR_NAN: return "NaN or Inf encountered";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

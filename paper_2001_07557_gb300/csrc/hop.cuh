@@ -1,0 +1,164 @@
+// hop.cuh -- the Wilson hopping kernel (one thread per output site) and its
+// epilogues.  Included by one translation unit per storage precision.
+//
+// For output parity p the kernel computes, per site x of parity p,
+//   out(x) = c_hop * (H psi)(x) + c_diag * x_in(x) [+ 5th-dimension terms]
+// where psi is the parity 1-p field.  The 8 neighbours are gathered from the
+// native structure-of-arrays blocks (16-byte vector loads, consecutive
+// threads on consecutive sites), spin-projected to half spinors, multiplied
+// by U or U^dag in registers, reconstructed and accumulated (Sec. 3.1 of the
+// paper builds the same stencil from shifts of whole SIMD arrays; here the
+// shift is a per-thread neighbour index).
+#pragma once
+
+#include "lqcd_internal.cuh"
+#include "lqcd_kernels.h"
+
+namespace lq {
+
+template <int P, bool R12, bool DAG, int EPI>
+__global__ void __launch_bounds__(128) wilson_hop_kernel(const HopArgs a) {
+    using T = typename Prec<P>::real;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const Geom& g = a.g;
+    if (i >= g.Vh) return;
+    const int yb = blockIdx.y;
+    const int p = a.parity0 + (a.nparity == 2 ? (yb & 1) : 0);
+    const int rhs = a.nparity == 2 ? (yb >> 1) : yb;
+
+    const char* __restrict__ in = a.in[p] + (size_t)rhs * a.in_rhs;
+    int x[4];
+    cb_coords(g, i, p, x);
+
+    // forward (x+mu) and backward (x-mu) checkerboard indices and phases
+    const int xh = x[0] >> 1;
+    int nf[4], nb[4];
+    bool sf[4], sb[4];
+    {
+        int xf = x[0] + 1, xb = x[0] - 1;
+        sf[0] = (xf == g.L[0]);
+        sb[0] = (xb < 0);
+        if (sf[0]) xf = 0;
+        if (sb[0]) xb = g.L[0] - 1;
+        nf[0] = i - xh + (xf >> 1);
+        nb[0] = i - xh + (xb >> 1);
+        int step = g.Lh0;
+#pragma unroll
+        for (int mu = 1; mu < 4; ++mu) {
+            const bool top = (x[mu] == g.L[mu] - 1), bot = (x[mu] == 0);
+            sf[mu] = top;
+            sb[mu] = bot;
+            nf[mu] = top ? i - (g.L[mu] - 1) * step : i + step;
+            nb[mu] = bot ? i + (g.L[mu] - 1) * step : i - step;
+            step *= g.L[mu];
+        }
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            sf[mu] = sf[mu] && (g.bc[mu] < 0);
+            sb[mu] = sb[mu] && (g.bc[mu] < 0);
+        }
+    }
+
+    cplx<T> acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = {(T)0, (T)0};
+
+    // forward: (1 - gamma) U_mu(x) psi(x+mu); dagger: (1 + gamma)
+    constexpr int SF = DAG ? +1 : -1;
+    constexpr int SB = -SF;
+    const char* __restrict__ Lp = a.links + (size_t)(p * 4) * a.link_block;
+    const char* __restrict__ Lq = a.links + (size_t)((1 - p) * 4) * a.link_block;
+
+#define LQ_HOP_DIR(MU)                                                   \
+    {                                                                    \
+        cplx<T> s[12], h[6], uh[6], u[9];                                \
+        load_spinor<P, T>(in, g.Vh, nf[MU], s);                          \
+        load_link<P, R12, T>(Lp + (size_t)(MU)*a.link_block, g.Vh, i, u); \
+        project<MU, SF>(s, h);                                           \
+        if (sf[MU]) {                                                    \
+            _Pragma("unroll") for (int k = 0; k < 6; ++k) h[k] = cneg(h[k]); \
+        }                                                                \
+        su3_mul<false>(u, h, uh);                                        \
+        reconstruct_add<MU, SF>(acc, uh);                                \
+    }                                                                    \
+    {                                                                    \
+        cplx<T> s[12], h[6], uh[6], u[9];                                \
+        load_spinor<P, T>(in, g.Vh, nb[MU], s);                          \
+        load_link<P, R12, T>(Lq + (size_t)(MU)*a.link_block, g.Vh, nb[MU], u); \
+        project<MU, SB>(s, h);                                           \
+        if (sb[MU]) {                                                    \
+            _Pragma("unroll") for (int k = 0; k < 6; ++k) h[k] = cneg(h[k]); \
+        }                                                                \
+        su3_mul<true>(u, h, uh);                                         \
+        reconstruct_add<MU, SB>(acc, uh);                                \
+    }
+
+    LQ_HOP_DIR(0)
+    LQ_HOP_DIR(1)
+    LQ_HOP_DIR(2)
+    LQ_HOP_DIR(3)
+#undef LQ_HOP_DIR
+
+    const T ch = (T)a.c_hop;
+    cplx<T> o[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) o[k] = {ch * acc[k].re, ch * acc[k].im};
+
+    if constexpr (EPI >= EPI_DIAG) {
+        const T cd = (T)a.c_diag;
+        const char* __restrict__ xb = a.x[p] + (size_t)rhs * a.x_rhs;
+        cplx<T> xs[12];
+        load_spinor<P, T>(xb, g.Vh, i, xs);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            o[k].re = fma(cd, xs[k].re, o[k].re);
+            o[k].im = fma(cd, xs[k].im, o[k].im);
+        }
+    }
+    if constexpr (EPI == EPI_DWF) {
+        // P+ = upper spins (gamma_5 = diag(1,1,-1,-1)).  Non-dagger: upper from
+        // s-1, lower from s+1; dagger swaps.  Coefficient -1, or +mf across the wall.
+        const int Ls = a.Ls;
+        const int s = rhs;
+        const int s_up = DAG ? (s + 1 == Ls ? 0 : s + 1) : (s == 0 ? Ls - 1 : s - 1);
+        const int s_dn = DAG ? (s == 0 ? Ls - 1 : s - 1) : (s + 1 == Ls ? 0 : s + 1);
+        const bool wrap_up = DAG ? (s + 1 == Ls) : (s == 0);
+        const bool wrap_dn = DAG ? (s == 0) : (s + 1 == Ls);
+        const T c_up = wrap_up ? (T)a.mf : (T)-1;
+        const T c_dn = wrap_dn ? (T)a.mf : (T)-1;
+        cplx<T> su[12], sd[12];
+        load_spinor<P, T>(a.x[p] + (size_t)s_up * a.x_rhs, g.Vh, i, su);
+        load_spinor<P, T>(a.x[p] + (size_t)s_dn * a.x_rhs, g.Vh, i, sd);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            o[k].re = fma(c_up, su[k].re, o[k].re);
+            o[k].im = fma(c_up, su[k].im, o[k].im);
+            o[6 + k].re = fma(c_dn, sd[6 + k].re, o[6 + k].re);
+            o[6 + k].im = fma(c_dn, sd[6 + k].im, o[6 + k].im);
+        }
+    }
+    store_spinor<P, T>(a.out[p] + (size_t)rhs * a.out_rhs, g.Vh, i, o);
+}
+
+template <int P>
+cudaError_t launch_hop_prec(const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st) {
+    dim3 grid((a.g.Vh + block - 1) / block, a.nrhs * a.nparity);
+    dim3 blk(block);
+#define LQ_LAUNCH(R, D, E) wilson_hop_kernel<P, R, D, E><<<grid, blk, 0, st>>>(a)
+#define LQ_EPI(R, D)                       \
+    switch (epi) {                         \
+    case EPI_HOP: LQ_LAUNCH(R, D, EPI_HOP); break;   \
+    case EPI_DIAG: LQ_LAUNCH(R, D, EPI_DIAG); break; \
+    default: LQ_LAUNCH(R, D, EPI_DWF); break;        \
+    }
+    if (r12) {
+        if (dag) { LQ_EPI(true, true) } else { LQ_EPI(true, false) }
+    } else {
+        if (dag) { LQ_EPI(false, true) } else { LQ_EPI(false, false) }
+    }
+#undef LQ_EPI
+#undef LQ_LAUNCH
+    return cudaGetLastError();
+}
+
+}  // namespace lq

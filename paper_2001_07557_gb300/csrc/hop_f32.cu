@@ -1,0 +1,8 @@
+// hop_f32.cu -- Wilson hop kernels with F32 storage (one translation unit per precision).
+#include "hop.cuh"
+
+namespace lq {
+cudaError_t launch_hop_f32(const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st) {
+    return launch_hop_prec<LQ_F32>(a, r12, dag, epi, block, st);
+}
+}  // namespace lq

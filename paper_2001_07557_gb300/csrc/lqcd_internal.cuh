@@ -1,0 +1,379 @@
+// lqcd_internal.cuh -- device-side building blocks of the Wilson hop:
+// lattice geometry, native-layout loads/stores in every storage precision,
+// chiral-basis spin projection / reconstruction, SU(3) x half-spinor products.
+//
+// Operator conventions (the paper names the Wilson Dirac operator, Sec. 3.3,
+// Fig. 4d, without writing it): H psi(x) = sum_mu (1 - gamma_mu) U_mu(x)
+// psi(x+mu) + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu), chiral basis
+// gamma_mu = [[0, A_mu], [A_mu^dag, 0]] with A_k = -i sigma_k, A_t = 1.
+// Then (1 + s gamma_mu) psi = [h; s A_mu^dag h] with h = psi_up + s A_mu psi_dn,
+// so each hop needs one 2-spin x 3-colour half spinor (the rank-2 projector
+// of r = 1), two 3x3 complex products, and a reconstruction.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <type_traits>
+
+#include "lqcd.h"
+
+namespace lq {
+
+// ------------------------------------------------------------------ geometry
+
+struct Geom {
+    int L[4];   // L0..L3
+    int Lh0;    // L0 / 2
+    int Vh;     // sites per parity
+    int bc[4];  // +1 / -1 boundary phase per direction
+};
+
+// Coordinates of the site with checkerboard index cb and parity p.
+__device__ __forceinline__ void cb_coords(const Geom& g, int cb, int p, int x[4]) {
+    int t = cb;
+    int xh = t % g.Lh0;
+    t /= g.Lh0;
+    x[1] = t % g.L[1];
+    t /= g.L[1];
+    x[2] = t % g.L[2];
+    x[3] = t / g.L[2];
+    x[0] = 2 * xh + ((p + x[1] + x[2] + x[3]) & 1);
+}
+
+// ------------------------------------------------------------------ complex
+
+template <typename T>
+struct cplx {
+    T re, im;
+};
+
+template <typename T>
+__device__ __forceinline__ cplx<T> cadd(cplx<T> a, cplx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename T>
+__device__ __forceinline__ cplx<T> csub(cplx<T> a, cplx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename T>
+__device__ __forceinline__ cplx<T> cmul_i(cplx<T> a) { return {-a.im, a.re}; }  // i a
+template <typename T>
+__device__ __forceinline__ cplx<T> cneg(cplx<T> a) { return {-a.re, -a.im}; }
+
+// a + S*b for a compile-time sign S
+template <int S, typename T>
+__device__ __forceinline__ cplx<T> cadds(cplx<T> a, cplx<T> b) {
+    if constexpr (S > 0) return cadd(a, b);
+    else return csub(a, b);
+}
+
+// acc += a * b
+template <typename T>
+__device__ __forceinline__ void cmac(cplx<T>& acc, cplx<T> a, cplx<T> b) {
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(-a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(a.im, b.re, acc.im);
+}
+// acc += conj(a) * b
+template <typename T>
+__device__ __forceinline__ void cmac_conj(cplx<T>& acc, cplx<T> a, cplx<T> b) {
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(-a.im, b.re, acc.im);
+}
+
+// ----------------------------------------------------- storage precisions
+
+template <int P>
+struct Prec;
+template <>
+struct Prec<LQ_F64> {
+    using real = double;
+    static constexpr int spinor_bytes = 192;  // 12 planes x 16 B
+    static constexpr bool has_norm = false;
+};
+template <>
+struct Prec<LQ_F32> {
+    using real = float;
+    static constexpr int spinor_bytes = 96;  // 6 planes x 16 B
+    static constexpr bool has_norm = false;
+};
+template <>
+struct Prec<LQ_F16> {
+    using real = float;
+    static constexpr int spinor_bytes = 52;  // 3 planes x 16 B + 4 B norm
+    static constexpr bool has_norm = true;
+};
+template <>
+struct Prec<LQ_BF16> {
+    using real = float;
+    static constexpr int spinor_bytes = 52;
+    static constexpr bool has_norm = true;
+};
+
+// Link planes per (parity, mu) block: bytes of one site's link.
+__host__ __device__ constexpr int link_site_bytes(int prec, bool r12) {
+    return prec == LQ_F64 ? (r12 ? 96 : 144) : prec == LQ_F32 ? (r12 ? 48 : 72) : (r12 ? 24 : 36);
+}
+__host__ __device__ constexpr int spinor_site_bytes(int prec) {
+    return prec == LQ_F64 ? 192 : prec == LQ_F32 ? 96 : 52;
+}
+
+// two 16-bit values <-> float2
+__device__ __forceinline__ float2 h2f(uint32_t v, std::integral_constant<int, LQ_F16>) {
+    __half2 h = *reinterpret_cast<__half2*>(&v);
+    return __half22float2(h);
+}
+__device__ __forceinline__ float2 h2f(uint32_t v, std::integral_constant<int, LQ_BF16>) {
+    __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&v);
+    return __bfloat1622float2(h);
+}
+__device__ __forceinline__ uint32_t f2h(float a, float b, std::integral_constant<int, LQ_F16>) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+__device__ __forceinline__ uint32_t f2h(float a, float b, std::integral_constant<int, LQ_BF16>) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// ------------------------------------------------------------ spinor access
+// A parity block of Vh sites; s[k] = complex number k = (spin k/3, colour k%3).
+
+template <int P, typename T>
+__device__ __forceinline__ void load_spinor(const char* __restrict__ blk, int Vh, int i, cplx<T> (&s)[12]) {
+    if constexpr (P == LQ_F64) {
+        const double2* q = reinterpret_cast<const double2*>(blk);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            double2 v = __ldg(q + (size_t)k * Vh + i);
+            s[k] = {(T)v.x, (T)v.y};
+        }
+    } else if constexpr (P == LQ_F32) {
+        const float4* q = reinterpret_cast<const float4*>(blk);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            float4 v = __ldg(q + (size_t)k * Vh + i);
+            s[2 * k] = {(T)v.x, (T)v.y};
+            s[2 * k + 1] = {(T)v.z, (T)v.w};
+        }
+    } else {
+        const uint4* q = reinterpret_cast<const uint4*>(blk);
+        const float nrm = __ldg(reinterpret_cast<const float*>(blk + (size_t)48 * Vh) + i);
+        std::integral_constant<int, P> tag;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint4 v = __ldg(q + (size_t)k * Vh + i);
+            float2 a = h2f(v.x, tag), b = h2f(v.y, tag), c = h2f(v.z, tag), d = h2f(v.w, tag);
+            s[4 * k + 0] = {a.x * nrm, a.y * nrm};
+            s[4 * k + 1] = {b.x * nrm, b.y * nrm};
+            s[4 * k + 2] = {c.x * nrm, c.y * nrm};
+            s[4 * k + 3] = {d.x * nrm, d.y * nrm};
+        }
+    }
+}
+
+template <int P, typename T>
+__device__ __forceinline__ void store_spinor(char* __restrict__ blk, int Vh, int i, const cplx<T> (&s)[12]) {
+    if constexpr (P == LQ_F64) {
+        double2* q = reinterpret_cast<double2*>(blk);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) q[(size_t)k * Vh + i] = make_double2((double)s[k].re, (double)s[k].im);
+    } else if constexpr (P == LQ_F32) {
+        float4* q = reinterpret_cast<float4*>(blk);
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            q[(size_t)k * Vh + i] =
+                make_float4((float)s[2 * k].re, (float)s[2 * k].im, (float)s[2 * k + 1].re, (float)s[2 * k + 1].im);
+    } else {
+        float m = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf((float)s[k].re), fabsf((float)s[k].im)));
+        const float inv = m > 0.f ? 1.0f / m : 0.f;
+        uint4* q = reinterpret_cast<uint4*>(blk);
+        std::integral_constant<int, P> tag;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint4 v;
+            v.x = f2h((float)s[4 * k + 0].re * inv, (float)s[4 * k + 0].im * inv, tag);
+            v.y = f2h((float)s[4 * k + 1].re * inv, (float)s[4 * k + 1].im * inv, tag);
+            v.z = f2h((float)s[4 * k + 2].re * inv, (float)s[4 * k + 2].im * inv, tag);
+            v.w = f2h((float)s[4 * k + 3].re * inv, (float)s[4 * k + 3].im * inv, tag);
+            q[(size_t)k * Vh + i] = v;
+        }
+        reinterpret_cast<float*>(blk + (size_t)48 * Vh)[i] = m;
+    }
+}
+
+// -------------------------------------------------------------- link access
+// One (parity, mu) block of Vh links.  u[3*row + col].
+
+template <typename T>
+__device__ __forceinline__ void reconstruct_row2(cplx<T> (&u)[9]) {
+    // row2 = conj(row0 x row1) for a special unitary matrix
+    u[6] = {u[1].re * u[5].re - u[1].im * u[5].im - (u[2].re * u[4].re - u[2].im * u[4].im),
+            -(u[1].re * u[5].im + u[1].im * u[5].re - (u[2].re * u[4].im + u[2].im * u[4].re))};
+    u[7] = {u[2].re * u[3].re - u[2].im * u[3].im - (u[0].re * u[5].re - u[0].im * u[5].im),
+            -(u[2].re * u[3].im + u[2].im * u[3].re - (u[0].re * u[5].im + u[0].im * u[5].re))};
+    u[8] = {u[0].re * u[4].re - u[0].im * u[4].im - (u[1].re * u[3].re - u[1].im * u[3].im),
+            -(u[0].re * u[4].im + u[0].im * u[4].re - (u[1].re * u[3].im + u[1].im * u[3].re))};
+}
+
+template <int P, bool R12, typename T>
+__device__ __forceinline__ void load_link(const char* __restrict__ blk, int Vh, int i, cplx<T> (&u)[9]) {
+    if constexpr (P == LQ_F64) {
+        const double2* q = reinterpret_cast<const double2*>(blk);
+        constexpr int n = R12 ? 6 : 9;
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+            double2 v = __ldg(q + (size_t)k * Vh + i);
+            u[k] = {(T)v.x, (T)v.y};
+        }
+    } else if constexpr (P == LQ_F32) {
+        if constexpr (R12) {
+            const float4* q = reinterpret_cast<const float4*>(blk);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                float4 v = __ldg(q + (size_t)k * Vh + i);
+                u[2 * k] = {(T)v.x, (T)v.y};
+                u[2 * k + 1] = {(T)v.z, (T)v.w};
+            }
+        } else {
+            const float2* q = reinterpret_cast<const float2*>(blk);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                float2 v = __ldg(q + (size_t)k * Vh + i);
+                u[k] = {(T)v.x, (T)v.y};
+            }
+        }
+    } else {
+        std::integral_constant<int, P> tag;
+        if constexpr (R12) {
+            const uint2* q = reinterpret_cast<const uint2*>(blk);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                uint2 v = __ldg(q + (size_t)k * Vh + i);
+                float2 a = h2f(v.x, tag), b = h2f(v.y, tag);
+                u[2 * k] = {a.x, a.y};
+                u[2 * k + 1] = {b.x, b.y};
+            }
+        } else {
+            const uint32_t* q = reinterpret_cast<const uint32_t*>(blk);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                float2 a = h2f(__ldg(q + (size_t)k * Vh + i), tag);
+                u[k] = {a.x, a.y};
+            }
+        }
+    }
+    if constexpr (R12) reconstruct_row2(u);
+}
+
+template <int P, bool R12>
+__device__ __forceinline__ void store_link(char* __restrict__ blk, int Vh, int i, const cplx<double> (&u)[9]) {
+    if constexpr (P == LQ_F64) {
+        double2* q = reinterpret_cast<double2*>(blk);
+        constexpr int n = R12 ? 6 : 9;
+#pragma unroll
+        for (int k = 0; k < n; ++k) q[(size_t)k * Vh + i] = make_double2(u[k].re, u[k].im);
+    } else if constexpr (P == LQ_F32) {
+        if constexpr (R12) {
+            float4* q = reinterpret_cast<float4*>(blk);
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                q[(size_t)k * Vh + i] = make_float4((float)u[2 * k].re, (float)u[2 * k].im, (float)u[2 * k + 1].re,
+                                                    (float)u[2 * k + 1].im);
+        } else {
+            float2* q = reinterpret_cast<float2*>(blk);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) q[(size_t)k * Vh + i] = make_float2((float)u[k].re, (float)u[k].im);
+        }
+    } else {
+        std::integral_constant<int, P> tag;
+        if constexpr (R12) {
+            uint2* q = reinterpret_cast<uint2*>(blk);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                uint2 v;
+                v.x = f2h((float)u[2 * k].re, (float)u[2 * k].im, tag);
+                v.y = f2h((float)u[2 * k + 1].re, (float)u[2 * k + 1].im, tag);
+                q[(size_t)k * Vh + i] = v;
+            }
+        } else {
+            uint32_t* q = reinterpret_cast<uint32_t*>(blk);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) q[(size_t)k * Vh + i] = f2h((float)u[k].re, (float)u[k].im, tag);
+        }
+    }
+}
+
+// ----------------------------------------------------- spin projection
+// (1 + S gamma_mu) psi = [h; S A_mu^dag h], h = psi_up + S A_mu psi_dn.
+// h[c] = spin 0 colour c, h[3 + c] = spin 1 colour c.
+
+template <int MU, int S, typename T>
+__device__ __forceinline__ void project(const cplx<T> (&s)[12], cplx<T> (&h)[6]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const cplx<T> p0 = s[c], p1 = s[3 + c], p2 = s[6 + c], p3 = s[9 + c];
+        if constexpr (MU == 0) {  // A = -i sigma_x: A psi_dn = (-i p3, -i p2)
+            h[c] = cadds<-S>(p0, cmul_i(p3));
+            h[3 + c] = cadds<-S>(p1, cmul_i(p2));
+        } else if constexpr (MU == 1) {  // A = -i sigma_y = [[0,-1],[1,0]]: (-p3, p2)
+            h[c] = cadds<-S>(p0, p3);
+            h[3 + c] = cadds<S>(p1, p2);
+        } else if constexpr (MU == 2) {  // A = -i sigma_z = diag(-i, i): (-i p2, i p3)
+            h[c] = cadds<-S>(p0, cmul_i(p2));
+            h[3 + c] = cadds<S>(p1, cmul_i(p3));
+        } else {  // A = 1
+            h[c] = cadds<S>(p0, p2);
+            h[3 + c] = cadds<S>(p1, p3);
+        }
+    }
+}
+
+// acc += [uh; S A_mu^dag uh]
+template <int MU, int S, typename T>
+__device__ __forceinline__ void reconstruct_add(cplx<T> (&acc)[12], const cplx<T> (&uh)[6]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const cplx<T> a = uh[c], b = uh[3 + c];
+        acc[c] = cadd(acc[c], a);
+        acc[3 + c] = cadd(acc[3 + c], b);
+        if constexpr (MU == 0) {  // A^dag = [[0, i],[i, 0]]: (i b, i a)
+            acc[6 + c] = cadds<S>(acc[6 + c], cmul_i(b));
+            acc[9 + c] = cadds<S>(acc[9 + c], cmul_i(a));
+        } else if constexpr (MU == 1) {  // A^dag = [[0, 1],[-1, 0]]: (b, -a)
+            acc[6 + c] = cadds<S>(acc[6 + c], b);
+            acc[9 + c] = cadds<-S>(acc[9 + c], a);
+        } else if constexpr (MU == 2) {  // A^dag = diag(i, -i): (i a, -i b)
+            acc[6 + c] = cadds<S>(acc[6 + c], cmul_i(a));
+            acc[9 + c] = cadds<-S>(acc[9 + c], cmul_i(b));
+        } else {
+            acc[6 + c] = cadds<S>(acc[6 + c], a);
+            acc[9 + c] = cadds<S>(acc[9 + c], b);
+        }
+    }
+}
+
+// uh = U h (ADJ: U^dag h), per spin component
+template <bool ADJ, typename T>
+__device__ __forceinline__ void su3_mul(const cplx<T> (&u)[9], const cplx<T> (&h)[6], cplx<T> (&uh)[6]) {
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            cplx<T> acc = {(T)0, (T)0};
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                if constexpr (ADJ) cmac_conj(acc, u[3 * j + i], h[3 * sp + j]);
+                else cmac(acc, u[3 * i + j], h[3 * sp + j]);
+            }
+            uh[3 * sp + i] = acc;
+        }
+    }
+}
+
+}  // namespace lq

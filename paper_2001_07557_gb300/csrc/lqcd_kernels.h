@@ -1,0 +1,54 @@
+// lqcd_kernels.h -- host-side interface between the C ABI layer and the
+// kernels (launch descriptors and launcher declarations).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+#include "lqcd_internal.cuh"
+
+namespace lq {
+
+enum { EPI_HOP = 0, EPI_DIAG = 1, EPI_DWF = 2 };
+
+// One hop launch.  Pointers are indexed by OUTPUT parity p: in[p] is the
+// parity 1-p input block of rhs 0, out[p] / x[p] the parity-p blocks of rhs 0.
+// Consecutive rhs (or 5th-dimension slices) are *_rhs bytes apart.
+struct HopArgs {
+    const char* links;  // native links of the launch precision: [parity][mu] blocks
+    size_t link_block;  // bytes of one (parity, mu) block
+    Geom g;
+    const char* in[2];
+    char* out[2];
+    const char* x[2];
+    size_t in_rhs, out_rhs, x_rhs;
+    int parity0;  // first output parity
+    int nparity;  // 1 (one parity) or 2 (both: full-lattice operator)
+    int nrhs;     // right-hand sides, or Ls for the domain-wall epilogue
+    double c_hop, c_diag;
+    int Ls;
+    double mf;
+};
+
+cudaError_t launch_hop(int prec, const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st);
+cudaError_t launch_hop_f64(const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st);
+cudaError_t launch_hop_f32(const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st);
+cudaError_t launch_hop_f16(const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st);
+cudaError_t launch_hop_bf16(const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st);
+
+// ----------------------------------------------------------- conversions
+// Spinor fields.  "site-major" = [rhs][site][4][3][2] in F64/F32, sites either
+// the full lattice in lexicographic order (full = true) or one parity in cb
+// order (full = false).  Native = [rhs][parity][planes] (full) or [rhs][planes].
+cudaError_t launch_spinor_to_native(int dst_prec, void* dst, int src_prec, const void* src, const Geom& g,
+                                    bool full, int parity, int nrhs, cudaStream_t st);
+cudaError_t launch_spinor_from_native(int dst_prec, void* dst, int src_prec, const void* src, const Geom& g,
+                                      bool full, int parity, int nrhs, cudaStream_t st);
+cudaError_t launch_native_convert(int dst_prec, void* dst, int src_prec, const void* src, int Vh, int nblocks,
+                                  cudaStream_t st);
+// Gauge links: site-major [site][mu][3][3][2] (F64/F32) -> native [parity][mu] blocks.
+cudaError_t launch_links_to_native(int dst_prec, bool r12, void* dst, int src_prec, const void* src, const Geom& g,
+                                   cudaStream_t st);
+
+}  // namespace lq

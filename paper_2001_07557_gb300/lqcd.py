@@ -1,0 +1,181 @@
+"""Thin ctypes binding of liblqcd.so: the C entry points under the same names.
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  Field arguments are torch CUDA tensors (their data_ptr() is passed)
+or raw integer device pointers; streams are torch.cuda.Stream objects, raw
+cudaStream_t integers, or None for the current torch stream.  A non-zero
+status raises LqError.  There is no CPU fallback: importing the binding
+without a built liblqcd.so raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblqcd.so")
+
+LQ_OK = 0
+LQ_F64, LQ_F32, LQ_F16, LQ_BF16 = 0, 1, 2, 3
+LQ_NATIVE = 0x10
+LQ_FULL, LQ_EVEN, LQ_ODD, LQ_SCHUR_EVEN = -1, 0, 1, 2
+LQ_OP_WILSON_NORMAL, LQ_OP_WILSON_EO_NORMAL, LQ_OP_DWF_NORMAL = 0, 1, 2
+LQ_CG_PLAIN, LQ_CG_MIXED, LQ_CG_BLOCK, LQ_CG_BATCHED = 0, 1, 2, 3
+STATUS = {0: "LQ_OK", -1: "LQ_ERR_ARG", -2: "LQ_ERR_LAYOUT", -3: "LQ_ERR_CUDA", -4: "LQ_ERR_NOMEM",
+          -5: "LQ_ERR_NOT_CONVERGED", -6: "LQ_ERR_BREAKDOWN", -7: "LQ_ERR_TIMEOUT", -8: "LQ_ERR_NAN"}
+
+# every function the header declares
+EXPORTS = ["lq_create", "lq_destroy", "lq_field_bytes", "lq_convert", "dslash_apply", "dslash_dag_apply",
+           "dwf_dslash_apply", "cg_solve", "lq_batch_cg_solve", "lq_status_string"]
+
+
+class LqError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({status})")
+
+
+class lq_params(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int * 4), ("bc", ctypes.c_int * 4), ("mass", ctypes.c_double),
+                ("r", ctypes.c_double), ("Ls", ctypes.c_int), ("M5", ctypes.c_double), ("mf", ctypes.c_double),
+                ("compress12", ctypes.c_int)]
+
+
+class lq_cg_params(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("mode", ctypes.c_int), ("fmt", ctypes.c_int), ("nrhs", ctypes.c_int),
+                ("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("inner", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("x0_is_guess", ctypes.c_int)]
+
+
+class lq_cg_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int), ("status", ctypes.c_int),
+                ("true_rel_residual", ctypes.c_double), ("time_ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load liblqcd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2001_07557_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        L.lq_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(lq_params), vp, i, vp]
+        L.lq_destroy.argtypes = [vp]
+        L.lq_field_bytes.argtypes = [vp, i, i, i, i, ctypes.POINTER(sz)]
+        L.lq_convert.argtypes = [vp, vp, i, vp, i, i, i, i, vp]
+        L.dslash_apply.argtypes = [vp, vp, vp, i, i, i, vp]
+        L.dslash_dag_apply.argtypes = [vp, vp, vp, i, i, i, vp]
+        L.dwf_dslash_apply.argtypes = [vp, vp, vp, i, i, vp]
+        L.cg_solve.argtypes = [vp, vp, vp, ctypes.POINTER(lq_cg_params), ctypes.POINTER(lq_cg_stats), vp]
+        L.lq_batch_cg_solve.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                        ctypes.POINTER(lq_cg_params), ctypes.POINTER(lq_cg_stats), vp]
+        L.lq_status_string.argtypes = [i]
+        L.lq_status_string.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            if name != "lq_status_string":
+                getattr(L, name).restype = i
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(rc, where):
+    if rc != LQ_OK:
+        raise LqError(rc, where)
+    return rc
+
+
+def make_params(dims, bc=(1, 1, 1, -1), mass=0.0, r=1.0, Ls=0, M5=0.0, mf=0.0, compress12=False) -> lq_params:
+    p = lq_params()
+    p.dims = (ctypes.c_int * 4)(*[int(d) for d in dims])
+    p.bc = (ctypes.c_int * 4)(*[int(b) for b in bc])
+    p.mass, p.r, p.Ls, p.M5, p.mf = float(mass), float(r), int(Ls), float(M5), float(mf)
+    p.compress12 = int(bool(compress12))
+    return p
+
+
+def lq_create(params: lq_params, U, U_prec=LQ_F64, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().lq_create(ctypes.byref(h), ctypes.byref(params), _ptr(U), U_prec, _stream(stream)), "lq_create")
+    return h.value
+
+
+def lq_destroy(h: int) -> None:
+    _check(lib().lq_destroy(h), "lq_destroy")
+
+
+def lq_field_bytes(h: int, fmt: int, subset: int = LQ_FULL, nrhs: int = 1, five_d: bool = False) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().lq_field_bytes(h, fmt, subset, nrhs, int(five_d), ctypes.byref(n)), "lq_field_bytes")
+    return n.value
+
+
+def lq_convert(h, dst, dst_fmt, src, src_fmt, subset=LQ_FULL, nrhs=1, five_d=False, stream=None):
+    _check(lib().lq_convert(h, _ptr(dst), dst_fmt, _ptr(src), src_fmt, subset, nrhs, int(five_d), _stream(stream)),
+           "lq_convert")
+
+
+def dslash_apply(h, out, inp, fmt, parity=LQ_FULL, nrhs=1, stream=None):
+    _check(lib().dslash_apply(h, _ptr(out), _ptr(inp), fmt, parity, nrhs, _stream(stream)), "dslash_apply")
+
+
+def dslash_dag_apply(h, out, inp, fmt, parity=LQ_FULL, nrhs=1, stream=None):
+    _check(lib().dslash_dag_apply(h, _ptr(out), _ptr(inp), fmt, parity, nrhs, _stream(stream)), "dslash_dag_apply")
+
+
+def dwf_dslash_apply(h, out, inp, fmt, dagger=False, stream=None):
+    _check(lib().dwf_dslash_apply(h, _ptr(out), _ptr(inp), fmt, int(dagger), _stream(stream)), "dwf_dslash_apply")
+
+
+def make_cg_params(op, mode=LQ_CG_PLAIN, fmt=LQ_F64, nrhs=1, tol=1e-10, maxiter=100000, inner=LQ_F32,
+                   inner_tol=0.0, x0_is_guess=False) -> lq_cg_params:
+    c = lq_cg_params()
+    c.op, c.mode, c.fmt, c.nrhs, c.tol, c.maxiter = int(op), int(mode), int(fmt), int(nrhs), float(tol), int(maxiter)
+    c.inner, c.inner_tol, c.x0_is_guess = int(inner), float(inner_tol), int(bool(x0_is_guess))
+    return c
+
+
+def cg_solve(h, x, b, cp: lq_cg_params, stream=None, check=True):
+    """Returns (status, [lq_cg_stats per right-hand side])."""
+    stats = (lq_cg_stats * max(1, cp.nrhs))()
+    rc = lib().cg_solve(h, _ptr(x), _ptr(b), ctypes.byref(cp), stats, _stream(stream))
+    if check and rc not in (LQ_OK,):
+        raise LqError(rc, "cg_solve")
+    return rc, list(stats)
+
+
+def lq_batch_cg_solve(hs, xs, bs, cp: lq_cg_params, stream=None, check=True):
+    n = len(hs)
+    H = (ctypes.c_void_p * n)(*hs)
+    X = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
+    B = (ctypes.c_void_p * n)(*[_ptr(b) for b in bs])
+    stats = (lq_cg_stats * (n * max(1, cp.nrhs)))()
+    rc = lib().lq_batch_cg_solve(H, n, X, B, ctypes.byref(cp), stats, _stream(stream))
+    if check and rc != LQ_OK:
+        raise LqError(rc, "lq_batch_cg_solve")
+    return rc, list(stats)
+
+
+def lq_status_string(status: int) -> str:
+    return lib().lq_status_string(status).decode()

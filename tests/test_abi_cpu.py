@@ -1,0 +1,68 @@
+"""CPU-side checks of the C ABI: the library builds, loads, exports every
+function include/lqcd.h declares, and its structs match the header's layout.
+No compute call is made (there is no GPU here)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2001_07557_gb300 import build as lqbuild
+from paper_2001_07557_gb300 import lqcd
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lqcd.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    lqbuild.build()
+    return lqcd.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_binding_exports():
+    assert declared_functions() == sorted(lqcd.EXPORTS)
+
+
+def test_every_declared_symbol_is_exported(L):
+    out = subprocess.run(["nm", "-D", "--defined-only", lqcd.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    names = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    for fn in declared_functions():
+        assert fn in names, fn
+        assert getattr(L, fn) is not None
+
+
+def test_struct_layout_matches_header(tmp_path):
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lqcd.h"\nint main(void){'
+                   'printf("%zu %zu %zu %zu %zu\\n", sizeof(lq_params), sizeof(lq_cg_params), sizeof(lq_cg_stats),'
+                   ' offsetof(lq_params, compress12), offsetof(lq_cg_params, x0_is_guess));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    want = [ctypes.sizeof(lqcd.lq_params), ctypes.sizeof(lqcd.lq_cg_params), ctypes.sizeof(lqcd.lq_cg_stats),
+            lqcd.lq_params.compress12.offset, lqcd.lq_cg_params.x0_is_guess.offset]
+    assert got == want
+
+
+def test_status_strings(L):
+    assert lqcd.lq_status_string(0) == "ok"
+    assert lqcd.lq_status_string(-5) == "solver did not converge"
+    assert lqcd.lq_status_string(12345) == "unknown status"
+
+
+def test_null_arguments_are_rejected_before_any_launch(L):
+    p = lqcd.make_params((4, 4, 4, 4))
+    h = ctypes.c_void_p()
+    assert L.lq_create(ctypes.byref(h), ctypes.byref(p), None, 0, None) == -1
+    assert L.lq_create(None, ctypes.byref(p), None, 0, None) == -1
+    assert L.dslash_apply(None, None, None, 0, -1, 1, None) == -1
+    assert L.lq_destroy(None) == -1
