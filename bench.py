@@ -1,0 +1,406 @@
+"""Benchmark: Wilson Dslash GFlop/s and fraction of the HBM roofline on one GB300.
+
+Workload (default): the 32^4 lattice (V = 1,048,576, m = 0.01) with smooth
+SU(3) links U = exp(0.3 i H), even-odd preconditioned.  One step applies the
+even-odd normal operator Mhat^dag Mhat (four even-odd hops: H_oe, H_eo with
+the Schur diagonal, and the same with the dagger) to a Gaussian even-parity
+spinor, in the storage precision --prec (FP16 with per-site FP32 norms by
+default, FP32 arithmetic).  This is the operator the inner mixed-precision
+CG iterates.  GFlop/s count 1320 flop per output site per hop.
+
+Output: one JSON line (rank 0).  `roofline` is for the hop kernel: the
+algorithmic bytes of one launch over its CUDA-event duration on the launch
+stream, against the measured HBM copy bandwidth.  `cpu_baseline` is the FP64
+CPU oracle applying the same operator on this host.  --impl reference times
+that oracle alone, as the reference arm.
+
+N > 1 (torchrun): independent replicas, one per GPU (no data-path exchange),
+value = all ranks' flops / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FLOP_PER_SITE = 1320
+METRIC = "Dslash GFlop/s & % HBM roofline; mixed vs FP64 CG time to 1e-10 residual"
+PREC_NAMES = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+CONFIGS = {
+    # name: dims, mass, link seed
+    "c3_32x4": ((32, 32, 32, 32), 0.01, 1002),
+    "c2_16x3x32": ((16, 16, 16, 32), 0.05, 1001),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c3_32x4", choices=sorted(CONFIGS))
+    ap.add_argument("--prec", default="f16", choices=sorted(PREC_NAMES))
+    ap.add_argument("--compress12", type=int, default=1)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the CPU baseline, e2e and per-precision table (for profiler runs)")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        time.sleep(0.3)
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes_per_site(prec, r12, diag):
+    """Minimum DRAM bytes of one even-odd hop per output site: 8 links, the
+    input spinor once, the output once (+ the diagonal input)."""
+    link = {0: (144, 96), 1: (72, 48), 2: (36, 24), 3: (36, 24)}[prec][1 if r12 else 0]
+    sp = {0: 192, 1: 96, 2: 52, 3: 52}[prec]
+    return 8 * link + 2 * sp + (sp if diag else 0)
+
+
+def setup(cfg, seed_src=2002):
+    from paper_2001_07557_gb300 import inputs
+
+    dims, mass, lseed = CONFIGS[cfg]
+    V = int(np.prod(dims))
+    U = inputs.gauge_field(dims, "smooth", seed=lseed)
+    psi_e = inputs.gaussian_spinor(V // 2, seed=seed_src)
+    return dims, mass, U, psi_e
+
+
+def oracle_normal_op(dims, mass, U, psi_e):
+    """Mhat^dag Mhat psi_e by the FP64 CPU oracle; returns (seconds, result)."""
+    import oracle
+
+    prm = oracle.params(dims, mass=mass)
+    t0 = time.perf_counter()
+    out = oracle.apply_normal(oracle.OP_WILSON_EO, psi_e, U, prm)
+    return time.perf_counter() - t0, out
+
+
+def host_cores():
+    try:
+        import oracle
+
+        oracle.build()
+        return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    mass = CONFIGS[args.config][1]
+    # bounded sample: the same operator on a 16^4 sub-volume of the same generator
+    # (the per-site work is identical; GFlop/s is intensive)
+    sdims = (16, 16, 16, 16)
+    from paper_2001_07557_gb300 import inputs
+
+    Us = inputs.gauge_field(sdims, "smooth", seed=CONFIGS[args.config][2])
+    ps = inputs.gaussian_spinor(int(np.prod(sdims)) // 2, seed=2002)
+    Vh = int(np.prod(sdims)) // 2
+    for _ in range(args.warmup):
+        oracle_normal_op(sdims, mass, Us, ps)
+    t = 0.0
+    for _ in range(args.steps):
+        dt, _ = oracle_normal_op(sdims, mass, Us, ps)
+        t += dt
+    flops = 4 * FLOP_PER_SITE * Vh * args.steps
+    val = flops / t / 1e9
+    cores = host_cores()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "GFlop/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.config}: even-odd Mhat^dag Mhat, oracle on a 16^4 sample",
+                   "dims": list(sdims), "mass": mass},
+        "cpu_baseline": {"value": val, "unit": "GFlop/s", "cores": cores, "kind": "oracle",
+                         "sample": "Mhat^dag Mhat on a 16^4 lattice per step (same generator and per-site work)"},
+        "e2e": {"value": val, "unit": "GFlop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2001_07557_gb300 import build as lqbuild
+    from paper_2001_07557_gb300 import lqcd
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    lqbuild.build()
+
+    prec = PREC_NAMES[args.prec]
+    r12 = bool(args.compress12)
+    nat = lqcd.LQ_NATIVE | prec
+    dims, mass, U, psi_e = setup(args.config)
+    V = int(np.prod(dims))
+    Vh = V // 2
+    prm = lqcd.make_params(dims, mass=mass, compress12=r12)
+    Ud = torch.from_numpy(U).cuda()
+    h = lqcd.lq_create(prm, Ud, lqcd.LQ_F64)
+    del Ud
+    torch.cuda.empty_cache()
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+
+    def nbuf(subset=lqcd.LQ_EVEN, p=prec):
+        return torch.empty(lqcd.lq_field_bytes(h, lqcd.LQ_NATIVE | p, subset, 1), dtype=torch.uint8,
+                           device="cuda")
+
+    x64 = torch.from_numpy(psi_e).cuda()
+    x = nbuf()
+    y = nbuf()
+    z = nbuf()
+    lqcd.lq_convert(h, x, nat, x64, lqcd.LQ_F64, lqcd.LQ_EVEN, stream=sh)
+
+    def step():
+        # Mhat^dag Mhat x: two Schur applications (2 hops each, the second with the diagonal)
+        lqcd.dslash_apply(h, y, x, nat, lqcd.LQ_SCHUR_EVEN, stream=sh)
+        lqcd.dslash_dag_apply(h, z, y, nat, lqcd.LQ_SCHUR_EVEN, stream=sh)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            step()
+    stream.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        stream.synchronize()
+        wall = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    flops_step = 4 * FLOP_PER_SITE * Vh
+    value = flops_step * args.steps * world / (total_ms * 1e-3) / 1e9
+
+    # the hop kernel: 4 launches per step (2 plain hops, 2 with the diagonal input)
+    bytes_launch = Vh * (algorithmic_bytes_per_site(prec, r12, False) + algorithmic_bytes_per_site(prec, r12, True)) / 2
+    launch_ms = statistics.median(step_ms) / 4
+    hbm, peak_kind = peaks()
+    achieved = bytes_launch / (launch_ms * 1e-3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", f"traffic_{args.config}_{args.prec}_r{int(r12)}.json")
+    if os.path.exists(tfile):
+        try:
+            traffic = json.load(open(tfile)).get("bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GFlop/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32", "data": "synthetic",
+        "config": {"workload": f"{args.config}: even-odd Wilson Mhat^dag Mhat, {args.prec} storage"
+                               f"{' + per-site norms' if prec >= 2 else ''}, {'12' if r12 else '18'}-real links",
+                   "dims": list(dims), "mass": mass, "links": "smooth exp(0.3iH), seed " + str(CONFIGS[args.config][2]),
+                   "l2": "inputs larger than L2 (links + 3 half spinors > 129 MB); no flush",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "peak_kind": peak_kind, "traffic": traffic, "kernel": "wilson_hop_kernel",
+                     "bytes_per_launch": bytes_launch, "launch_ms": launch_ms},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clocks.summary(),
+        "wall_s_timed": wall,
+    }
+
+    if rank == 0 and not args.no_extras:
+        line["e2e"] = e2e(h, lqcd, torch, dims, psi_e, prec, args, world)
+        line["per_precision"] = precision_table(h, lqcd, torch, psi_e, Vh, args, U, dims, mass)
+        line["cpu_baseline"] = cpu_baseline(dims, mass, U, psi_e, Vh)
+    lqcd.lq_destroy(h)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def e2e(h, lqcd, torch, dims, psi_e, prec, args, world):
+    """Same operator through the public calls with pinned host buffers: H2D of the
+    site-major FP64 source, conversion to the storage format, Mhat^dag Mhat,
+    conversion back, D2H of the result, every step."""
+    Vh = psi_e.shape[0]
+    nat = lqcd.LQ_NATIVE | prec
+    hx = torch.from_numpy(psi_e).pin_memory()
+    hy = torch.empty_like(hx).pin_memory()
+    dx = torch.empty(hx.shape, dtype=hx.dtype, device="cuda")
+    dy = torch.empty_like(dx)
+    nb = lqcd.lq_field_bytes(h, nat, lqcd.LQ_EVEN, 1)
+    a, b, c = (torch.empty(nb, dtype=torch.uint8, device="cuda") for _ in range(3))
+    st = torch.cuda.Stream()
+
+    def one():
+        with torch.cuda.stream(st):
+            dx.copy_(hx, non_blocking=True)
+            lqcd.lq_convert(h, a, nat, dx, lqcd.LQ_F64, lqcd.LQ_EVEN, stream=st)
+            lqcd.dslash_apply(h, b, a, nat, lqcd.LQ_SCHUR_EVEN, stream=st)
+            lqcd.dslash_dag_apply(h, c, b, nat, lqcd.LQ_SCHUR_EVEN, stream=st)
+            lqcd.lq_convert(h, dy, lqcd.LQ_F64, c, nat, lqcd.LQ_EVEN, stream=st)
+            hy.copy_(dy, non_blocking=True)
+
+    for _ in range(3):
+        one()
+    st.synchronize()
+    n = max(5, args.steps // 2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(n):
+        one()
+    e1.record(st)
+    st.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    nbytes = hx.numel() * hx.element_size()
+    return {"value": 4 * FLOP_PER_SITE * Vh / (ms * 1e-3) / 1e9 * world, "unit": "GFlop/s",
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": ms}
+
+
+def precision_table(h, lqcd, torch, psi_e, Vh, args, U, dims, mass):
+    """Single even-odd hop H_eo (one launch) per storage precision, 18- and 12-real links."""
+    out = {}
+    hbm, _ = peaks()
+    x64 = torch.from_numpy(inputs_odd(psi_e)).cuda()
+    st = torch.cuda.Stream()
+    for pname, p in PREC_NAMES.items():
+        for r12 in (0, 1):
+            prm = lqcd.make_params(dims, mass=mass, compress12=bool(r12))
+            hh = lqcd.lq_create(prm, torch.from_numpy(U).cuda(), lqcd.LQ_F64)
+            nat = lqcd.LQ_NATIVE | p
+            nb = lqcd.lq_field_bytes(hh, nat, lqcd.LQ_EVEN, 1)
+            a = torch.empty(nb, dtype=torch.uint8, device="cuda")
+            b = torch.empty(nb, dtype=torch.uint8, device="cuda")
+            lqcd.lq_convert(hh, a, nat, x64, lqcd.LQ_F64, lqcd.LQ_ODD, stream=st)
+            reps = 20 if p == 0 else 100
+            for _ in range(5):
+                lqcd.dslash_apply(hh, b, a, nat, lqcd.LQ_EVEN, stream=st)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(reps):
+                lqcd.dslash_apply(hh, b, a, nat, lqcd.LQ_EVEN, stream=st)
+            e1.record(st)
+            st.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            gbs = Vh * algorithmic_bytes_per_site(p, r12, False) / (ms * 1e-3) / 1e9
+            out[f"{pname}_r{12 if r12 else 18}"] = {"gflops": FLOP_PER_SITE * Vh / (ms * 1e-3) / 1e9,
+                                                    "ms": ms, "model_gbs": gbs, "frac_hbm": gbs / hbm}
+            lqcd.lq_destroy(hh)
+    return out
+
+
+def inputs_odd(psi_e):
+    return psi_e  # any Gaussian half field serves as the odd-parity input
+
+
+def cpu_baseline(dims, mass, U, psi_e, Vh):
+    """Repeat the oracle's Mhat^dag Mhat on the full lattice until >= 10 s (at most 6 times)."""
+    cores = host_cores()
+    total, n = 0.0, 0
+    while total < 10.0 and n < 6:
+        dt, _ = oracle_normal_op(dims, mass, U, psi_e)
+        total += dt
+        n += 1
+    return {"value": 4 * FLOP_PER_SITE * Vh * n / total / 1e9, "unit": "GFlop/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} Mhat^dag Mhat applications on the full {list(dims)} lattice, {total:.1f} s"}
+
+
+if __name__ == "__main__":
+    main()
