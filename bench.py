@@ -304,6 +304,7 @@ def main():
     }
 
     if rank == 0 and not args.no_extras:
+        line["cg"] = cg_compare(h, lqcd, torch, psi_e, prec)
         line["e2e"] = e2e(h, lqcd, torch, dims, psi_e, prec, args, world)
         line["per_precision"] = precision_table(h, lqcd, torch, psi_e, Vh, args, U, dims, mass)
         line["cpu_baseline"] = cpu_baseline(dims, mass, U, psi_e, Vh)
@@ -383,6 +384,32 @@ def precision_table(h, lqcd, torch, psi_e, Vh, args, U, dims, mass):
             out[f"{pname}_r{12 if r12 else 18}"] = {"gflops": FLOP_PER_SITE * Vh / (ms * 1e-3) / 1e9,
                                                     "ms": ms, "model_gbs": gbs, "frac_hbm": gbs / hbm}
             lqcd.lq_destroy(hh)
+    return out
+
+
+def cg_compare(h, lqcd, torch, psi_e, prec):
+    """Time to |b - A x| / |b| < 1e-10 on the even-odd normal equations, b = the
+    Gaussian even source: plain FP64 CG against FP64 defect correction with the
+    inner CG in the benchmark's storage precision (FP32 arithmetic)."""
+    out = {}
+    b = torch.from_numpy(psi_e).cuda()
+    inner = prec if prec != 0 else lqcd.LQ_F32
+    for name, mode in (("fp64", lqcd.LQ_CG_PLAIN), ("mixed", lqcd.LQ_CG_MIXED)):
+        x = torch.zeros_like(b)
+        cp = lqcd.make_cg_params(lqcd.LQ_OP_WILSON_EO_NORMAL, mode, lqcd.LQ_F64, tol=1e-10, maxiter=20000,
+                                 inner=inner)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, st = lqcd.cg_solve(h, x, b, cp, check=False)
+        wall = time.perf_counter() - t0
+        out[name] = {"status": rc, "seconds": wall, "iters": st[0].iters, "outer": st[0].outer_iters,
+                     "true_rel_residual": st[0].true_rel_residual}
+        if name == "fp64":
+            x64 = x.clone()
+        else:
+            out[name]["rel_diff_vs_fp64"] = float((x - x64).norm() / x64.norm())
+    out["inner_precision"] = {0: "f64", 1: "f32", 2: "f16", 3: "bf16"}[inner]
+    out["speedup"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
     return out
 
 

@@ -59,6 +59,8 @@ static HopArgs base_args(lq_handle* h, const char* links, size_t lb) {
     a.links = links;
     a.link_block = lb;
     a.g = h->g;
+    a.skip = h->skip;
+    a.skip_stride = h->skip_stride;
     return a;
 }
 
@@ -153,41 +155,6 @@ int native_dwf(lq_handle* h, int prec, char* out, const char* in, bool dag, cuda
 using namespace lq;
 
 namespace {
-
-bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
-
-bool overlap(const void* a, size_t na, const void* b, size_t nb) {
-    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
-    return x < y + nb && y < x + na;
-}
-
-bool valid_fmt(int fmt) {
-    const int prec = fmt & 0xF;
-    const bool native = (fmt & LQ_NATIVE) != 0;
-    if ((fmt & ~(0xF | LQ_NATIVE)) != 0) return false;
-    if (prec < LQ_F64 || prec > LQ_BF16) return false;
-    if (!native && prec > LQ_F32) return false;
-    return true;
-}
-
-size_t field_bytes(const lq_handle* h, int fmt, int subset, int nrhs) {
-    const int prec = fmt & 0xF;
-    const bool native = (fmt & LQ_NATIVE) != 0;
-    const size_t sites = (subset == LQ_FULL ? 2 : 1) * (size_t)h->g.Vh;
-    if (native) return sites * (size_t)spinor_site_bytes(prec) * nrhs;
-    return sites * 24 * (prec == LQ_F64 ? 8 : 4) * nrhs;
-}
-
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
-        else prev = -1;
-    }
-    ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
 
 int wilson_apply(lq_handle* h, void* out, const void* in, int fmt, int parity, int nrhs, cudaStream_t st,
                  bool dag) {
@@ -294,6 +261,8 @@ int lq_destroy(lq_handle* h) {
             if (q) cudaFree(q);
     for (auto& b : h->ws)
         if (b.ptr) cudaFree(b.ptr);
+    if (h->solver_stream) cudaStreamDestroy(h->solver_stream);
+    if (h->pinned) cudaFreeHost(h->pinned);
     delete h;
     return LQ_OK;
 }

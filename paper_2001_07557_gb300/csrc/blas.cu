@@ -1,0 +1,296 @@
+// blas.cu -- vector kernels for the solvers: the CG updates with their FP64
+// global reductions fused in, generic axpby / norms, and the device-side CG
+// scalar arithmetic.  Reductions: per-thread FP64 partial sums, warp shuffles,
+// a shared-memory block reduction, one partial per block in scratch, and the
+// last block to finish (atomic ticket) sums the partials in a fixed order and
+// finalises the CG scalars on the device -- no host round trip per iteration.
+#include "blas.h"
+
+namespace lq {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-reduce v; thread 0 writes the partial, and the last block of this rhs
+// returns true in every thread with `total` set (fixed-order sum of partials).
+__device__ bool reduce_last(double v, double* partial, unsigned* ticket, int nblk_x, double& total) {
+    __shared__ double ws[kThreads / 32];
+    __shared__ bool last;
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) ws[wid] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += ws[w];
+        partial[blockIdx.x] = s;
+        __threadfence();
+        const unsigned t = atomicAdd(ticket, 1u);
+        last = (t == (unsigned)nblk_x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double s = 0;
+    for (int b = threadIdx.x; b < nblk_x; b += blockDim.x) s += __ldcg(partial + b);
+    // deterministic: fixed thread -> partial assignment, then a fixed-shape tree
+    s = warp_sum(s);
+    __syncthreads();
+    if (lane == 0) ws[wid] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+        total = t;
+        *ticket = 0;  // ready for the next launch
+    }
+    __syncthreads();
+    return true;
+}
+
+template <int P, typename T>
+__device__ __forceinline__ const char* blk_ptr(const VecRef& v, int rhs, int b, int Vh) {
+    return v.ptr + (size_t)rhs * v.rhs_stride + (size_t)b * spinor_site_bytes(P) * Vh;
+}
+
+__device__ __forceinline__ bool finite(double v) { return isfinite(v); }
+
+// ---------------------------------------------------------------- kernels
+
+// sum_re <a, b> per rhs; finalize: FIN_ALPHA (pAp -> alpha) or store into out[rhs]
+template <int PA, int PB>
+__global__ void __launch_bounds__(kThreads) dot_kernel(VecRef a, VecRef b, int Vh, int nblk, double* scratch,
+                                                       unsigned* tickets, CgScalars* st, double* out, int fin) {
+    const int rhs = blockIdx.y;
+    if (st && st[rhs].done) return;
+    using TA = typename Prec<PA>::real;
+    double acc = 0;
+    const long n = (long)Vh * nblk;
+    for (long j = (long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
+        const int bk = (int)(j / Vh), i = (int)(j - (long)bk * Vh);
+        cplx<double> sa[12], sb[12];
+        load_spinor<PA, double>(blk_ptr<PA, TA>(a, rhs, bk, Vh), Vh, i, sa);
+        load_spinor<PB, double>(blk_ptr<PB, TA>(b, rhs, bk, Vh), Vh, i, sb);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc += sa[k].re * sb[k].re + sa[k].im * sb[k].im;
+    }
+    double total;
+    if (!reduce_last(acc, scratch + (size_t)rhs * gridDim.x, tickets + rhs, gridDim.x, total)) return;
+    if (threadIdx.x != 0) return;
+    if (fin == FIN_ALPHA) {
+        CgScalars& s = st[rhs];
+        s.pAp = total;
+        if (!(total > 0.0) || !finite(total)) {
+            s.done = 1;
+            s.status = LQ_ERR_BREAKDOWN;
+            s.alpha = 0;
+        } else {
+            s.alpha = s.rr / total;
+        }
+    } else if (out) {
+        out[rhs] = total;
+    }
+}
+
+// x += alpha p ; r -= alpha q ; rr_new = |r|^2 ; beta, convergence (per rhs)
+template <int PX, int PP, int PR, int PQ>
+__global__ void __launch_bounds__(kThreads) cg_update_kernel(VecRef x, VecRef p, VecRef r, VecRef q, int Vh, int nblk,
+                                                             double* scratch, unsigned* tickets, CgScalars* st) {
+    const int rhs = blockIdx.y;
+    CgScalars& s = st[rhs];
+    if (s.done) return;
+    const double alpha = s.alpha;
+    double acc = 0;
+    const long n = (long)Vh * nblk;
+    for (long j = (long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
+        const int bk = (int)(j / Vh), i = (int)(j - (long)bk * Vh);
+        cplx<double> xs[12], ps[12], rs[12], qs[12];
+        load_spinor<PX, double>(blk_ptr<PX, double>(x, rhs, bk, Vh), Vh, i, xs);
+        load_spinor<PP, double>(blk_ptr<PP, double>(p, rhs, bk, Vh), Vh, i, ps);
+        load_spinor<PR, double>(blk_ptr<PR, double>(r, rhs, bk, Vh), Vh, i, rs);
+        load_spinor<PQ, double>(blk_ptr<PQ, double>(q, rhs, bk, Vh), Vh, i, qs);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            xs[k].re = fma(alpha, ps[k].re, xs[k].re);
+            xs[k].im = fma(alpha, ps[k].im, xs[k].im);
+            rs[k].re = fma(-alpha, qs[k].re, rs[k].re);
+            rs[k].im = fma(-alpha, qs[k].im, rs[k].im);
+        }
+        if constexpr (PR != LQ_F64) {
+            // accumulate the norm of the value as stored
+            cplx<float> rf[12];
+#pragma unroll
+            for (int k = 0; k < 12; ++k) rf[k] = {(float)rs[k].re, (float)rs[k].im};
+#pragma unroll
+            for (int k = 0; k < 12; ++k) acc += (double)rf[k].re * rf[k].re + (double)rf[k].im * rf[k].im;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) acc += rs[k].re * rs[k].re + rs[k].im * rs[k].im;
+        }
+        store_spinor<PX, double>(const_cast<char*>(blk_ptr<PX, double>(x, rhs, bk, Vh)), Vh, i, xs);
+        store_spinor<PR, double>(const_cast<char*>(blk_ptr<PR, double>(r, rhs, bk, Vh)), Vh, i, rs);
+    }
+    double total;
+    if (!reduce_last(acc, scratch + (size_t)rhs * gridDim.x, tickets + rhs, gridDim.x, total)) return;
+    if (threadIdx.x != 0) return;
+    s.iter += 1;
+    if (!finite(total)) {
+        s.done = 1;
+        s.status = LQ_ERR_NAN;
+        return;
+    }
+    s.beta = total / s.rr;
+    s.rr = total;
+    if (total <= s.stop2) s.done = 1;
+    else if (s.iter >= s.maxiter) {
+        s.done = 1;
+        s.status = LQ_ERR_NOT_CONVERGED;
+    }
+}
+
+// p = r + beta p
+template <int PP, int PR>
+__global__ void __launch_bounds__(kThreads) cg_xpay_kernel(VecRef p, VecRef r, int Vh, int nblk, const CgScalars* st) {
+    const int rhs = blockIdx.y;
+    if (st[rhs].done) return;
+    const double beta = st[rhs].beta;
+    const long n = (long)Vh * nblk;
+    for (long j = (long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
+        const int bk = (int)(j / Vh), i = (int)(j - (long)bk * Vh);
+        cplx<double> ps[12], rs[12];
+        load_spinor<PP, double>(blk_ptr<PP, double>(p, rhs, bk, Vh), Vh, i, ps);
+        load_spinor<PR, double>(blk_ptr<PR, double>(r, rhs, bk, Vh), Vh, i, rs);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            ps[k].re = fma(beta, ps[k].re, rs[k].re);
+            ps[k].im = fma(beta, ps[k].im, rs[k].im);
+        }
+        store_spinor<PP, double>(const_cast<char*>(blk_ptr<PP, double>(p, rhs, bk, Vh)), Vh, i, ps);
+    }
+}
+
+// y = a x + b y with host scalars (a applies to every rhs)
+template <int PY, int PX>
+__global__ void __launch_bounds__(kThreads) axpby_kernel(VecRef y, VecRef x, double ca, double cb, int Vh, int nblk) {
+    const int rhs = blockIdx.y;
+    const long n = (long)Vh * nblk;
+    for (long j = (long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
+        const int bk = (int)(j / Vh), i = (int)(j - (long)bk * Vh);
+        cplx<double> ys[12], xs[12];
+        load_spinor<PX, double>(blk_ptr<PX, double>(x, rhs, bk, Vh), Vh, i, xs);
+        if (cb != 0.0) load_spinor<PY, double>(blk_ptr<PY, double>(y, rhs, bk, Vh), Vh, i, ys);
+        else {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) ys[k] = {0.0, 0.0};
+        }
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            ys[k].re = ca * xs[k].re + cb * ys[k].re;
+            ys[k].im = ca * xs[k].im + cb * ys[k].im;
+        }
+        store_spinor<PY, double>(const_cast<char*>(blk_ptr<PY, double>(y, rhs, bk, Vh)), Vh, i, ys);
+    }
+}
+
+// CG start: rr = |r|^2 per rhs (already in out), set the scalars
+__global__ void cg_init_kernel(CgScalars* st, const double* rr, const double* bb, double tol, int maxiter, int nrhs) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nrhs) return;
+    CgScalars& s = st[k];
+    s.rr = rr[k];
+    s.bb = bb[k];
+    s.stop2 = tol * tol * bb[k];
+    s.iter = 0;
+    s.maxiter = maxiter;
+    s.status = LQ_OK;
+    s.alpha = s.beta = s.pAp = 0;
+    s.done = (rr[k] <= s.stop2) ? 1 : 0;
+    if (!isfinite(rr[k])) {
+        s.done = 1;
+        s.status = LQ_ERR_NAN;
+    }
+}
+
+int grid_x(int Vh, int nblk) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 132;
+    }
+    const long n = (long)Vh * nblk;
+    long want = (n + kThreads - 1) / kThreads;
+    const long cap = (long)sms * 8;
+    return (int)(want < cap ? want : cap);
+}
+
+}  // namespace
+
+#define LQ_P_SWITCH(pv, NAME, BODY)                               \
+    switch (pv) {                                                 \
+    case LQ_F64: { constexpr int NAME = LQ_F64; BODY; } break;    \
+    case LQ_F32: { constexpr int NAME = LQ_F32; BODY; } break;    \
+    case LQ_F16: { constexpr int NAME = LQ_F16; BODY; } break;    \
+    default: { constexpr int NAME = LQ_BF16; BODY; } break;       \
+    }
+
+size_t reduce_scratch_doubles(int Vh, int nblk, int nrhs) { return (size_t)grid_x(Vh, nblk) * nrhs; }
+
+cudaError_t launch_dot(const VecRef& a, const VecRef& b, int Vh, int nblk, int nrhs, const Scratch& sc,
+                       CgScalars* st, double* out, int fin, cudaStream_t s) {
+    dim3 grid(grid_x(Vh, nblk), nrhs);
+    LQ_P_SWITCH(a.prec, PA, LQ_P_SWITCH(b.prec, PB,
+        (dot_kernel<PA, PB><<<grid, kThreads, 0, s>>>(a, b, Vh, nblk, sc.partial, sc.tickets, st, out, fin))))
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_update(const VecRef& x, const VecRef& p, const VecRef& r, const VecRef& q, int Vh, int nblk,
+                             int nrhs, const Scratch& sc, CgScalars* st, cudaStream_t s) {
+    dim3 grid(grid_x(Vh, nblk), nrhs);
+    // precision combinations used by the solvers: all equal, or x, r in FP32 with p, q in FP16/BF16
+    if (x.prec == LQ_F64 && p.prec == LQ_F64 && r.prec == LQ_F64 && q.prec == LQ_F64)
+        cg_update_kernel<LQ_F64, LQ_F64, LQ_F64, LQ_F64><<<grid, kThreads, 0, s>>>(x, p, r, q, Vh, nblk, sc.partial, sc.tickets, st);
+    else if (x.prec == LQ_F32 && r.prec == LQ_F32 && p.prec == q.prec) {
+        switch (p.prec) {
+        case LQ_F32: cg_update_kernel<LQ_F32, LQ_F32, LQ_F32, LQ_F32><<<grid, kThreads, 0, s>>>(x, p, r, q, Vh, nblk, sc.partial, sc.tickets, st); break;
+        case LQ_F16: cg_update_kernel<LQ_F32, LQ_F16, LQ_F32, LQ_F16><<<grid, kThreads, 0, s>>>(x, p, r, q, Vh, nblk, sc.partial, sc.tickets, st); break;
+        case LQ_BF16: cg_update_kernel<LQ_F32, LQ_BF16, LQ_F32, LQ_BF16><<<grid, kThreads, 0, s>>>(x, p, r, q, Vh, nblk, sc.partial, sc.tickets, st); break;
+        default: return cudaErrorInvalidValue;
+        }
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_xpay(const VecRef& p, const VecRef& r, int Vh, int nblk, int nrhs, const CgScalars* st,
+                           cudaStream_t s) {
+    dim3 grid(grid_x(Vh, nblk), nrhs);
+    LQ_P_SWITCH(p.prec, PP, LQ_P_SWITCH(r.prec, PR,
+        (cg_xpay_kernel<PP, PR><<<grid, kThreads, 0, s>>>(p, r, Vh, nblk, st))))
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpby(const VecRef& y, const VecRef& x, double a, double b, int Vh, int nblk, int nrhs,
+                         cudaStream_t s) {
+    dim3 grid(grid_x(Vh, nblk), nrhs);
+    LQ_P_SWITCH(y.prec, PY, LQ_P_SWITCH(x.prec, PX,
+        (axpby_kernel<PY, PX><<<grid, kThreads, 0, s>>>(y, x, a, b, Vh, nblk))))
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_init(CgScalars* st, const double* rr, const double* bb, double tol, int maxiter, int nrhs,
+                           cudaStream_t s) {
+    cg_init_kernel<<<(nrhs + 63) / 64, 64, 0, s>>>(st, rr, bb, tol, maxiter, nrhs);
+    return cudaGetLastError();
+}
+
+}  // namespace lq

@@ -1,0 +1,55 @@
+// blas.h -- solver vector kernels: descriptors and launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+#include "lqcd_internal.cuh"
+
+namespace lq {
+
+// A native field of nrhs right-hand sides; each rhs is nblk parity blocks of
+// Vh sites (1 for a half field, 2 for a full field, 2*Ls for a 5-d field),
+// rhs_stride bytes apart.
+struct VecRef {
+    char* ptr;
+    int prec;
+    size_t rhs_stride;
+};
+
+// Device-resident CG scalars of one right-hand side.
+struct CgScalars {
+    double rr;     // |r|^2
+    double bb;     // |b|^2
+    double stop2;  // tol^2 |b|^2
+    double pAp;
+    double alpha;
+    double beta;
+    int iter;
+    int maxiter;
+    int done;      // converged, broke down, or out of iterations
+    int status;    // LQ_OK / LQ_ERR_BREAKDOWN / LQ_ERR_NOT_CONVERGED / LQ_ERR_NAN
+};
+
+struct Scratch {
+    double* partial;    // reduce_scratch_doubles() entries
+    unsigned* tickets;  // one per rhs, zero before the first launch (each launch leaves them zero)
+};
+
+enum { FIN_STORE = 0, FIN_ALPHA = 1 };
+
+size_t reduce_scratch_doubles(int Vh, int nblk, int nrhs);
+
+cudaError_t launch_dot(const VecRef& a, const VecRef& b, int Vh, int nblk, int nrhs, const Scratch& sc,
+                       CgScalars* st, double* out, int fin, cudaStream_t s);
+cudaError_t launch_cg_update(const VecRef& x, const VecRef& p, const VecRef& r, const VecRef& q, int Vh, int nblk,
+                             int nrhs, const Scratch& sc, CgScalars* st, cudaStream_t s);
+cudaError_t launch_cg_xpay(const VecRef& p, const VecRef& r, int Vh, int nblk, int nrhs, const CgScalars* st,
+                           cudaStream_t s);
+cudaError_t launch_axpby(const VecRef& y, const VecRef& x, double a, double b, int Vh, int nblk, int nrhs,
+                         cudaStream_t s);
+cudaError_t launch_cg_init(CgScalars* st, const double* rr, const double* bb, double tol, int maxiter, int nrhs,
+                           cudaStream_t s);
+
+}  // namespace lq

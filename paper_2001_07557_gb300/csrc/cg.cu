@@ -1,17 +1,428 @@
-// cg.cu -- conjugate-gradient solvers on the normal equations.
+// cg.cu -- conjugate gradient on the normal equations A x = b,
+// A = K^dag K for K = D (full lattice), Mhat (even-odd Schur complement) or
+// D_dw (domain wall), for nrhs right-hand sides at once.
+//
+//  * plain CG (Hestenes-Stiefel) in FP64 or FP32;
+//  * mixed precision: an FP64 defect-correction loop (true residual
+//    r = b - A x in FP64 on the GPU) around an inner CG whose search
+//    directions and operator live in FP32, FP16 or BF16 storage (FP32
+//    arithmetic) and whose iterate and residual are FP32;
+//  * every right-hand side keeps its own device-resident scalars; the
+//    reductions are fused into the vector updates and finish on the device,
+//    the iteration is captured once into a CUDA graph and replayed, and the
+//    host polls the scalars once per graph replay.
+// The paper (Sec. 3.3) benchmarks the Wilson operator only; the solver
+// around it follows the textbook CG.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "blas.h"
 #include "handle.h"
 
-extern "C" {
+namespace lq {
 
-int cg_solve(lq_handle* h, void* x, const void* b, const lq_cg_params* cp, lq_cg_stats* stats, void* stream) {
-    (void)h; (void)x; (void)b; (void)cp; (void)stats; (void)stream;
+namespace {
+
+constexpr int kItersPerGraph = 8;
+
+struct OpGeom {
+    int op;
+    int nblk;   // parity blocks per right-hand side
+    int nrhs;
+    size_t stride(const lq_handle* h, int prec) const {
+        return (size_t)nblk * spinor_site_bytes(prec) * (size_t)h->g.Vh;
+    }
+    size_t bytes(const lq_handle* h, int prec) const { return stride(h, prec) * nrhs; }
+    VecRef ref(const lq_handle* h, void* p, int prec) const { return VecRef{static_cast<char*>(p), prec, stride(h, prec)}; }
+};
+
+// out = K^dag K in;  t: intermediate of in's size, tmp: odd half (even-odd only)
+int apply_normal(lq_handle* h, const OpGeom& og, int prec, char* out, const char* in, char* t, char* tmp,
+                 cudaStream_t st) {
+    int rc;
+    switch (og.op) {
+    case LQ_OP_WILSON_NORMAL:
+        if ((rc = native_wilson_full(h, prec, t, in, og.nrhs, false, st))) return rc;
+        return native_wilson_full(h, prec, out, t, og.nrhs, true, st);
+    case LQ_OP_WILSON_EO_NORMAL:
+        if ((rc = native_wilson_schur(h, prec, t, in, tmp, og.nrhs, false, st))) return rc;
+        return native_wilson_schur(h, prec, out, t, tmp, og.nrhs, true, st);
+    case LQ_OP_DWF_NORMAL:
+        if ((rc = native_dwf(h, prec, t, in, false, st))) return rc;
+        return native_dwf(h, prec, out, t, true, st);
+    }
     return LQ_ERR_ARG;
 }
 
-int lq_batch_cg_solve(lq_handle** hs, int nlat, void** xs, const void** bs, const lq_cg_params* cp,
-                      lq_cg_stats* stats, void* stream) {
+// Solver scratch: scalars, norms, reduction partials, tickets (one workspace slot)
+struct Ctl {
+    CgScalars* st;
+    double* red;  // 2 * nrhs doubles
+    Scratch sc;
+    CgScalars* host;
+};
+
+int make_ctl(lq_handle* h, const OpGeom& og, Ctl* c, cudaStream_t s) {
+    const size_t npart = reduce_scratch_doubles(h->g.Vh, og.nblk, og.nrhs);
+    const size_t nb = sizeof(CgScalars) * og.nrhs + sizeof(double) * (2 * og.nrhs + npart) +
+                      sizeof(unsigned) * og.nrhs + 256;
+    void* p;
+    int rc = ensure_ws(h, WS_CTL, nb, &p);
+    if (rc) return rc;
+    char* q = static_cast<char*>(p);
+    c->st = reinterpret_cast<CgScalars*>(q);
+    q += sizeof(CgScalars) * og.nrhs;
+    c->red = reinterpret_cast<double*>(q);
+    q += sizeof(double) * 2 * og.nrhs;
+    c->sc.partial = reinterpret_cast<double*>(q);
+    q += sizeof(double) * npart;
+    c->sc.tickets = reinterpret_cast<unsigned*>(q);
+    if (cudaMemsetAsync(c->sc.tickets, 0, sizeof(unsigned) * og.nrhs, s) != cudaSuccess) return LQ_ERR_CUDA;
+    const size_t hb = sizeof(CgScalars) * og.nrhs + sizeof(double) * 2 * og.nrhs;
+    if (h->pinned_bytes < hb) {
+        if (h->pinned) cudaFreeHost(h->pinned);
+        h->pinned = nullptr;
+        h->pinned_bytes = 0;
+        if (cudaMallocHost(&h->pinned, hb) != cudaSuccess) {
+            cudaGetLastError();
+            return LQ_ERR_NOMEM;
+        }
+        h->pinned_bytes = hb;
+    }
+    c->host = static_cast<CgScalars*>(h->pinned);
+    return LQ_OK;
+}
+
+double* host_red(lq_handle* h, const OpGeom& og) {
+    return reinterpret_cast<double*>(static_cast<char*>(h->pinned) + sizeof(CgScalars) * og.nrhs);
+}
+
+// norms |v|^2 of every rhs into host memory
+int norms_to_host(lq_handle* h, const OpGeom& og, const Ctl& c, const VecRef& v, double* out, cudaStream_t s) {
+    if (launch_dot(v, v, h->g.Vh, og.nblk, og.nrhs, c.sc, nullptr, c.red, FIN_STORE, s) != cudaSuccess)
+        return LQ_ERR_CUDA;
+    double* hr = host_red(h, og);
+    if (cudaMemcpyAsync(hr, c.red, sizeof(double) * og.nrhs, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return LQ_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return LQ_ERR_CUDA;
+    for (int k = 0; k < og.nrhs; ++k) out[k] = hr[k];
+    return LQ_OK;
+}
+
+struct CgVecs {
+    VecRef r, p, q, t, tmp;  // r in the iterate precision; p, q, t, tmp in the operator precision
+};
+
+int cg_vectors(lq_handle* h, const OpGeom& og, int px, int pp, int slot0, CgVecs* v) {
+    void* ptr[5];
+    const size_t sz[5] = {og.bytes(h, px), og.bytes(h, pp), og.bytes(h, pp), og.bytes(h, pp),
+                          (size_t)spinor_site_bytes(pp) * h->g.Vh * og.nrhs};
+    for (int k = 0; k < 5; ++k) {
+        int rc = ensure_ws(h, slot0 + k, sz[k], &ptr[k]);
+        if (rc) return rc;
+    }
+    v->r = og.ref(h, ptr[0], px);
+    v->p = og.ref(h, ptr[1], pp);
+    v->q = og.ref(h, ptr[2], pp);
+    v->t = og.ref(h, ptr[3], pp);
+    v->tmp = VecRef{static_cast<char*>(ptr[4]), pp, (size_t)spinor_site_bytes(pp) * h->g.Vh};
+    return LQ_OK;
+}
+
+// CG on A e = rhs.  e, rhs, r in precision px; p, q, t in pp.  Starts from
+// e = 0.  Stops per rhs at |r| <= tol |rhs| or after maxiter iterations.
+// On return c.host holds the final scalars of every rhs.
+int run_cg(lq_handle* h, const OpGeom& og, const Ctl& c, int pp, const VecRef& e, const VecRef& rhs, double tol,
+           int maxiter, int slot0, cudaStream_t s) {
+    const int px = e.prec;
+    CgVecs v;
+    int rc = cg_vectors(h, og, px, pp, slot0, &v);
+    if (rc) return rc;
+    const char* L;
+    size_t lb;
+    if ((rc = get_links(h, pp, &L, &lb, s))) return rc;  // pack before any capture
+    const int Vh = h->g.Vh;
+    if (cudaMemsetAsync(e.ptr, 0, og.bytes(h, px), s) != cudaSuccess) return LQ_ERR_CUDA;
+    if (cudaMemcpyAsync(v.r.ptr, rhs.ptr, og.bytes(h, px), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return LQ_ERR_CUDA;
+    if (launch_axpby(v.p, v.r, 1.0, 0.0, Vh, og.nblk, og.nrhs, s) != cudaSuccess) return LQ_ERR_CUDA;
+    if (launch_dot(rhs, rhs, Vh, og.nblk, og.nrhs, c.sc, nullptr, c.red, FIN_STORE, s) != cudaSuccess)
+        return LQ_ERR_CUDA;
+    if (launch_cg_init(c.st, c.red, c.red, tol, maxiter, og.nrhs, s) != cudaSuccess) return LQ_ERR_CUDA;
+
+    // one graph = kItersPerGraph iterations; finished right-hand sides skip every launch
+    h->skip = &c.st[0].done;
+    h->skip_stride = (int)(sizeof(CgScalars) / sizeof(int));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    rc = LQ_OK;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = LQ_ERR_CUDA;
+    for (int k = 0; k < kItersPerGraph && rc == LQ_OK; ++k) {
+        rc = apply_normal(h, og, pp, v.q.ptr, v.p.ptr, v.t.ptr, v.tmp.ptr, s);
+        if (rc) break;
+        if (launch_dot(v.p, v.q, Vh, og.nblk, og.nrhs, c.sc, c.st, nullptr, FIN_ALPHA, s) != cudaSuccess ||
+            launch_cg_update(e, v.p, v.r, v.q, Vh, og.nblk, og.nrhs, c.sc, c.st, s) != cudaSuccess ||
+            launch_cg_xpay(v.p, v.r, Vh, og.nblk, og.nrhs, c.st, s) != cudaSuccess)
+            rc = LQ_ERR_CUDA;
+    }
+    cudaError_t ce = cudaStreamEndCapture(s, &graph);
+    h->skip = nullptr;
+    if (rc == LQ_OK && ce != cudaSuccess) rc = LQ_ERR_CUDA;
+    if (rc == LQ_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) rc = LQ_ERR_CUDA;
+    const int max_launches = maxiter / kItersPerGraph + 2;
+    for (int it = 0; rc == LQ_OK && it < max_launches; ++it) {
+        if (cudaGraphLaunch(exec, s) != cudaSuccess ||
+            cudaMemcpyAsync(c.host, c.st, sizeof(CgScalars) * og.nrhs, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            rc = LQ_ERR_CUDA;
+            break;
+        }
+        bool all = true;
+        for (int k = 0; k < og.nrhs; ++k) all = all && c.host[k].done;
+        if (all) break;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return rc;
+}
+
+// |b - A x| / |b| per rhs in FP64 (x64, b64 native FP64)
+int true_residual(lq_handle* h, const OpGeom& og, const Ctl& c, const VecRef& x64, const VecRef& b64, int slot0,
+                  double* rel, cudaStream_t s) {
+    CgVecs v;
+    int rc = cg_vectors(h, og, LQ_F64, LQ_F64, slot0, &v);
+    if (rc) return rc;
+    if ((rc = apply_normal(h, og, LQ_F64, v.q.ptr, x64.ptr, v.t.ptr, v.tmp.ptr, s))) return rc;
+    if (launch_axpby(v.r, b64, 1.0, 0.0, h->g.Vh, og.nblk, og.nrhs, s) != cudaSuccess) return LQ_ERR_CUDA;
+    if (launch_axpby(v.r, v.q, -1.0, 1.0, h->g.Vh, og.nblk, og.nrhs, s) != cudaSuccess) return LQ_ERR_CUDA;
+    std::vector<double> rr(og.nrhs), bb(og.nrhs);
+    if ((rc = norms_to_host(h, og, c, v.r, rr.data(), s))) return rc;
+    if ((rc = norms_to_host(h, og, c, b64, bb.data(), s))) return rc;
+    for (int k = 0; k < og.nrhs; ++k) rel[k] = bb[k] > 0 ? std::sqrt(rr[k] / bb[k]) : std::sqrt(rr[k]);
+    return LQ_OK;
+}
+
+double default_inner_tol(int prec) {
+    switch (prec) {
+    case LQ_F32: return 1e-6;
+    case LQ_F16: return 1e-3;
+    default: return 3e-2;
+    }
+}
+
+}  // namespace
+
+}  // namespace lq
+
+using namespace lq;
+
+extern "C" int cg_solve(lq_handle* h, void* x, const void* b, const lq_cg_params* cp, lq_cg_stats* stats,
+                        void* stream) {
+    if (!h || !x || !b || !cp || !stats) return LQ_ERR_ARG;
+    if (!valid_fmt(cp->fmt) || cp->nrhs < 1 || cp->maxiter < 1 || !(cp->tol > 0)) return LQ_ERR_ARG;
+    if (!aligned16(x) || !aligned16(b)) return LQ_ERR_LAYOUT;
+    const int fprec = cp->fmt & 0xF;
+    const bool native = (cp->fmt & LQ_NATIVE) != 0;
+    if (fprec > LQ_F32) return LQ_ERR_ARG;  // x and b are FP64 or FP32 fields
+    OpGeom og;
+    og.op = cp->op;
+    og.nrhs = cp->nrhs;
+    int subset;
+    switch (cp->op) {
+    case LQ_OP_WILSON_NORMAL: og.nblk = 2; subset = LQ_FULL; break;
+    case LQ_OP_WILSON_EO_NORMAL: og.nblk = 1; subset = LQ_EVEN; break;
+    case LQ_OP_DWF_NORMAL:
+        if (h->p.Ls < 1 || cp->nrhs != 1) return LQ_ERR_ARG;
+        og.nblk = 2 * h->p.Ls;
+        subset = LQ_FULL;
+        break;
+    default: return LQ_ERR_ARG;
+    }
+    const int mode = cp->mode == LQ_CG_BATCHED ? LQ_CG_MIXED : cp->mode;
+    if (mode != LQ_CG_PLAIN && mode != LQ_CG_MIXED) return LQ_ERR_ARG;
+    if (mode == LQ_CG_MIXED && (cp->inner < LQ_F32 || cp->inner > LQ_BF16)) return LQ_ERR_ARG;
+    const int nf = cp->op == LQ_OP_DWF_NORMAL ? h->p.Ls : cp->nrhs;  // fields in the user's buffers
+    const size_t ub = field_bytes(h, cp->fmt, subset, nf);
+    if (overlap(x, ub, b, ub)) return LQ_ERR_ARG;
+    DeviceGuard dg(h->device);
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t user = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(user) != cudaSuccess) return LQ_ERR_CUDA;
+    if (!h->solver_stream && cudaStreamCreateWithFlags(&h->solver_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return LQ_ERR_CUDA;
+    cudaStream_t s = h->solver_stream;
+    const bool full = subset == LQ_FULL;
+    const int parity = full ? 0 : LQ_EVEN;
+    const int wp = mode == LQ_CG_PLAIN ? fprec : LQ_F64;  // precision of x and b inside the solver
+
+    int rc;
+    Ctl c;
+    if ((rc = make_ctl(h, og, &c, s))) return rc;
+    void *xw, *bw;
+    if ((rc = ensure_ws(h, WS_IN, og.bytes(h, wp), &bw)) || (rc = ensure_ws(h, WS_OUT, og.bytes(h, wp), &xw)))
+        return rc;
+    // user fields -> native working precision
+    auto to_native = [&](void* dst, const void* src) -> cudaError_t {
+        if (native) return launch_native_convert(wp, dst, fprec, src, h->g.Vh, og.nblk * og.nrhs, s);
+        return launch_spinor_to_native(wp, dst, fprec, src, h->g, full, parity, nf, s);
+    };
+    if (to_native(bw, b) != cudaSuccess) return LQ_ERR_CUDA;
+    VecRef X = og.ref(h, xw, wp), B = og.ref(h, bw, wp);
+    std::vector<int> iters(og.nrhs, 0), status(og.nrhs, LQ_OK), outer(og.nrhs, 0);
+    std::vector<double> rel(og.nrhs, 0.0);
+
+    if (mode == LQ_CG_PLAIN) {
+        if (cp->x0_is_guess) {
+            // restart from a guess: solve A e = b - A x0, then x = x0 + e
+            void* x0;
+            if ((rc = ensure_ws(h, WS_TMP, og.bytes(h, wp), &x0))) return rc;
+            if (to_native(x0, x) != cudaSuccess) return LQ_ERR_CUDA;
+            CgVecs v;
+            if ((rc = cg_vectors(h, og, wp, wp, WS_CG0, &v))) return rc;
+            VecRef X0 = og.ref(h, x0, wp);
+            if ((rc = apply_normal(h, og, wp, v.q.ptr, X0.ptr, v.t.ptr, v.tmp.ptr, s))) return rc;
+            void* r0;
+            if ((rc = ensure_ws(h, WS_CG0 + 10, og.bytes(h, wp), &r0))) return rc;
+            VecRef R0 = og.ref(h, r0, wp);
+            if (launch_axpby(R0, B, 1.0, 0.0, h->g.Vh, og.nblk, og.nrhs, s) != cudaSuccess ||
+                launch_axpby(R0, v.q, -1.0, 1.0, h->g.Vh, og.nblk, og.nrhs, s) != cudaSuccess)
+                return LQ_ERR_CUDA;
+            // tolerance relative to |b|: scale by |b| / |r0|
+            std::vector<double> bb(og.nrhs), r0n(og.nrhs);
+            if ((rc = norms_to_host(h, og, c, B, bb.data(), s)) || (rc = norms_to_host(h, og, c, R0, r0n.data(), s)))
+                return rc;
+            // tolerance of the correction, relative to |r0|, that meets tol relative to |b|;
+            // a guess whose residual already meets tol is returned as it is
+            double t = 1.0;
+            bool any = false;
+            for (int k = 0; k < og.nrhs; ++k) {
+                if (r0n[k] > cp->tol * cp->tol * bb[k]) {
+                    any = true;
+                    t = std::min(t, cp->tol * std::sqrt(bb[k] / r0n[k]));
+                } else if (cudaMemsetAsync(R0.ptr + k * R0.rhs_stride, 0, R0.rhs_stride, s) != cudaSuccess) {
+                    return LQ_ERR_CUDA;
+                }
+            }
+            if ((rc = run_cg(h, og, c, wp, X, R0, any ? t : 1.0, cp->maxiter, WS_CG0, s))) return rc;
+            if (launch_axpby(X, X0, 1.0, 1.0, h->g.Vh, og.nblk, og.nrhs, s) != cudaSuccess) return LQ_ERR_CUDA;
+        } else {
+            if ((rc = run_cg(h, og, c, wp, X, B, cp->tol, cp->maxiter, WS_CG0, s))) return rc;
+        }
+        for (int k = 0; k < og.nrhs; ++k) {
+            iters[k] = c.host[k].iter;
+            status[k] = c.host[k].status;
+        }
+        // true residual in FP64
+        if (wp == LQ_F64) {
+            if ((rc = true_residual(h, og, c, X, B, WS_CG0 + 5, rel.data(), s))) return rc;
+        } else {
+            void *x64, *b64;
+            if ((rc = ensure_ws(h, WS_CG0 + 10, og.bytes(h, LQ_F64), &x64)) ||
+                (rc = ensure_ws(h, WS_CG0 + 11, og.bytes(h, LQ_F64), &b64)))
+                return rc;
+            VecRef X64 = og.ref(h, x64, LQ_F64), B64 = og.ref(h, b64, LQ_F64);
+            if (launch_axpby(X64, X, 1.0, 0.0, h->g.Vh, og.nblk, og.nrhs, s) != cudaSuccess ||
+                launch_axpby(B64, B, 1.0, 0.0, h->g.Vh, og.nblk, og.nrhs, s) != cudaSuccess)
+                return LQ_ERR_CUDA;
+            if ((rc = true_residual(h, og, c, X64, B64, WS_CG0 + 5, rel.data(), s))) return rc;
+        }
+    } else {
+        // FP64 defect correction around a low-precision inner CG
+        const int ip = cp->inner;
+        const double itol = cp->inner_tol > 0 ? cp->inner_tol : default_inner_tol(ip);
+        void *r64p, *ep, *rinp;
+        if ((rc = ensure_ws(h, WS_CG0 + 10, og.bytes(h, LQ_F64), &r64p)) ||
+            (rc = ensure_ws(h, WS_CG0 + 11, og.bytes(h, LQ_F32), &ep)) ||
+            (rc = ensure_ws(h, WS_CG0 + 12, og.bytes(h, LQ_F32), &rinp)))
+            return rc;
+        VecRef R64 = og.ref(h, r64p, LQ_F64), E = og.ref(h, ep, LQ_F32), RIN = og.ref(h, rinp, LQ_F32);
+        if (cp->x0_is_guess) {
+            if (to_native(xw, x) != cudaSuccess) return LQ_ERR_CUDA;
+        } else if (cudaMemsetAsync(xw, 0, og.bytes(h, LQ_F64), s) != cudaSuccess) {
+            return LQ_ERR_CUDA;
+        }
+        std::vector<double> bb(og.nrhs), rr(og.nrhs);
+        if ((rc = norms_to_host(h, og, c, B, bb.data(), s))) return rc;
+        std::vector<char> conv(og.nrhs, 0);
+        std::vector<double> best(og.nrhs, 1e300);
+        std::vector<int> stall(og.nrhs, 0);
+        int total_inner = 0;
+        bool first = !cp->x0_is_guess;
+        for (int it = 0;; ++it) {
+            // r = b - A x in FP64 (the first residual of a zero start is b itself)
+            if (first) {
+                if (launch_axpby(R64, B, 1.0, 0.0, h->g.Vh, og.nblk, og.nrhs, s) != cudaSuccess) return LQ_ERR_CUDA;
+            } else {
+                CgVecs v;
+                if ((rc = cg_vectors(h, og, LQ_F64, LQ_F64, WS_CG0 + 5, &v))) return rc;
+                if ((rc = apply_normal(h, og, LQ_F64, v.q.ptr, X.ptr, v.t.ptr, v.tmp.ptr, s))) return rc;
+                if (launch_axpby(R64, B, 1.0, 0.0, h->g.Vh, og.nblk, og.nrhs, s) != cudaSuccess ||
+                    launch_axpby(R64, v.q, -1.0, 1.0, h->g.Vh, og.nblk, og.nrhs, s) != cudaSuccess)
+                    return LQ_ERR_CUDA;
+                for (int k = 0; k < og.nrhs; ++k) iters[k] += conv[k] ? 0 : 1;
+            }
+            first = false;
+            if ((rc = norms_to_host(h, og, c, R64, rr.data(), s))) return rc;
+            bool all = true;
+            for (int k = 0; k < og.nrhs; ++k) {
+                rel[k] = bb[k] > 0 ? std::sqrt(rr[k] / bb[k]) : std::sqrt(rr[k]);
+                if (!std::isfinite(rel[k])) status[k] = LQ_ERR_NAN;
+                // three restarts without progress: the inner precision cannot reach tol
+                if (rel[k] < 0.5 * best[k]) {
+                    best[k] = rel[k];
+                    stall[k] = 0;
+                } else if (++stall[k] >= 3 && !conv[k] && rel[k] >= cp->tol) {
+                    status[k] = LQ_ERR_NOT_CONVERGED;
+                }
+                conv[k] = conv[k] || rel[k] < cp->tol || status[k] != LQ_OK;
+                all = all && conv[k];
+            }
+            if (all) break;
+            if (total_inner >= cp->maxiter) {
+                for (int k = 0; k < og.nrhs; ++k)
+                    if (!conv[k]) status[k] = LQ_ERR_NOT_CONVERGED;
+                break;
+            }
+            // inner solve A e = r (FP32 copy of r; finished right-hand sides get r = 0)
+            if (launch_axpby(RIN, R64, 1.0, 0.0, h->g.Vh, og.nblk, og.nrhs, s) != cudaSuccess) return LQ_ERR_CUDA;
+            for (int k = 0; k < og.nrhs; ++k)
+                if (conv[k] && cudaMemsetAsync(RIN.ptr + k * RIN.rhs_stride, 0, RIN.rhs_stride, s) != cudaSuccess)
+                    return LQ_ERR_CUDA;
+            if ((rc = run_cg(h, og, c, ip, E, RIN, itol, cp->maxiter - total_inner, WS_CG0, s))) return rc;
+            int most = 0;
+            for (int k = 0; k < og.nrhs; ++k) {
+                iters[k] += c.host[k].iter;
+                most = std::max(most, c.host[k].iter);
+                if (!conv[k]) outer[k] += 1;
+            }
+            total_inner += std::max(most, 1);
+            if (launch_axpby(X, E, 1.0, 1.0, h->g.Vh, og.nblk, og.nrhs, s) != cudaSuccess) return LQ_ERR_CUDA;
+        }
+    }
+    // native working precision -> user layout
+    cudaError_t e;
+    if (native) e = launch_native_convert(fprec, x, wp, xw, h->g.Vh, og.nblk * og.nrhs, s);
+    else e = launch_spinor_from_native(fprec, x, wp, xw, h->g, full, parity, nf, s);
+    if (e != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return LQ_ERR_CUDA;
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    int ret = LQ_OK;
+    for (int k = 0; k < og.nrhs; ++k) {
+        stats[k].iters = iters[k];
+        stats[k].outer_iters = outer[k];
+        stats[k].status = status[k];
+        stats[k].true_rel_residual = rel[k];
+        stats[k].time_ms = ms;
+        if (status[k] != LQ_OK && ret == LQ_OK) ret = status[k];
+    }
+    return ret;
+}
+
+extern "C" int lq_batch_cg_solve(lq_handle** hs, int nlat, void** xs, const void** bs, const lq_cg_params* cp,
+                                 lq_cg_stats* stats, void* stream) {
     (void)hs; (void)nlat; (void)xs; (void)bs; (void)cp; (void)stats; (void)stream;
     return LQ_ERR_ARG;
 }
-
-}  // extern "C"

@@ -20,13 +20,20 @@ struct lq_handle {
     struct Buf {
         void* ptr;
         size_t bytes;
-    } ws[8];          // workspace buffers, grown on demand
+    } ws[20];         // workspace buffers, grown on demand
     int hop_block[4]; // threads per block of the hop kernels, per precision
+    const int* skip;  // per-rhs early-exit flags the solvers hand to the hop launches (else null)
+    int skip_stride;
+    cudaStream_t solver_stream;  // private non-blocking stream the solvers capture into graphs
+    void* pinned;                // pinned host buffer the solvers poll their scalars into
+    size_t pinned_bytes;
 };
 
 namespace lq {
 
-enum { WS_IN = 0, WS_OUT = 1, WS_TMP = 2, WS_CG0 = 3 };
+// workspace slots: conversions 0-2; solver vectors 3-7 (inner CG), 8-12 (FP64
+// residuals), 13-15 (defect-correction vectors); 19 solver scalars
+enum { WS_IN = 0, WS_OUT = 1, WS_TMP = 2, WS_CG0 = 3, WS_CTL = 19 };
 
 inline int status_of(cudaError_t e) { return e == cudaSuccess ? LQ_OK : LQ_ERR_CUDA; }
 
@@ -49,5 +56,42 @@ int native_wilson_block(lq_handle* h, int prec, char* out, const char* in, int o
 int native_wilson_schur(lq_handle* h, int prec, char* out, const char* in, char* tmp, int nrhs, bool dag,
                         cudaStream_t st);
 int native_dwf(lq_handle* h, int prec, char* out, const char* in, bool dag, cudaStream_t st);
+
+// ---------------------------------------------------------- argument checks
+
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+inline bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + nb && y < x + na;
+}
+
+inline bool valid_fmt(int fmt) {
+    const int prec = fmt & 0xF;
+    const bool native = (fmt & LQ_NATIVE) != 0;
+    if ((fmt & ~(0xF | LQ_NATIVE)) != 0) return false;
+    if (prec < LQ_F64 || prec > LQ_BF16) return false;
+    if (!native && prec > LQ_F32) return false;
+    return true;
+}
+
+inline size_t field_bytes(const lq_handle* h, int fmt, int subset, int nrhs) {
+    const int prec = fmt & 0xF;
+    const bool native = (fmt & LQ_NATIVE) != 0;
+    const size_t sites = (subset == LQ_FULL ? 2 : 1) * (size_t)h->g.Vh;
+    if (native) return sites * (size_t)spinor_site_bytes(prec) * nrhs;
+    return sites * 24 * (prec == LQ_F64 ? 8 : 4) * nrhs;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
 
 }  // namespace lq

@@ -25,6 +25,7 @@ __global__ void __launch_bounds__(128) wilson_hop_kernel(const HopArgs a) {
     const int yb = blockIdx.y;
     const int p = a.parity0 + (a.nparity == 2 ? (yb & 1) : 0);
     const int rhs = a.nparity == 2 ? (yb >> 1) : yb;
+    if (a.skip && a.skip[(EPI == EPI_DWF ? 0 : rhs) * a.skip_stride]) return;
 
     const char* __restrict__ in = a.in[p] + (size_t)rhs * a.in_rhs;
     int x[4];

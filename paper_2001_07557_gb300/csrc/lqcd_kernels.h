@@ -29,6 +29,8 @@ struct HopArgs {
     double c_hop, c_diag;
     int Ls;
     double mf;
+    const int* skip;  // optional per-rhs flags (skip[rhs * skip_stride]): a set flag ends the block at once
+    int skip_stride;
 };
 
 cudaError_t launch_hop(int prec, const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st);

@@ -1,0 +1,201 @@
+"""GPU CG solvers against the FP64 oracle.
+
+FP64 CG: the solution must satisfy the FP64 true residual |b - A x|/|b| <= 1e-12
+(with a small rounding allowance) and agree with the oracle's dense-LU
+solution within kappa(A) * tol.  Mixed precision: true residual <= the
+requested 1e-10 and agreement with the oracle's FP64 CG within kappa * tol.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from lqhelp import Handle, dev, host, rel_err
+from paper_2001_07557_gb300 import inputs
+from paper_2001_07557_gb300 import lqcd
+
+pytestmark = pytest.mark.gpu
+
+
+def dense_D(U, dims, m):
+    V = int(np.prod(dims))
+    n = V * 12
+    M = np.empty((n, n), dtype=complex)
+    e = np.zeros(n, dtype=complex)
+    for k in range(n):
+        e[:] = 0
+        e[k] = 1
+        M[:, k] = oracle.wilson_dslash(e.reshape(V, 4, 3), U, dims, m).ravel()
+    return M
+
+
+def test_c1_fp64_cg_matches_dense_lu():
+    """4^4, random SU(3), m = 0.1, CG on D^dag D x = D^dag eta to 1e-12."""
+    dims = (4, 4, 4, 4)
+    U = inputs.gauge_field(dims, "random", seed=1000)
+    eta = inputs.gaussian_spinor(256, seed=2000)
+    D = dense_D(U, dims, 0.1)
+    x_lu = np.linalg.solve(D, eta.ravel()).reshape(256, 4, 3)
+    sv = np.linalg.svd(D, compute_uv=False)
+    kappa = (sv[0] / sv[-1]) ** 2
+    b = oracle.wilson_dslash(eta, U, dims, 0.1, dagger=True)
+    _, it_or, _, _ = oracle.cg(oracle.OP_WILSON, b, U, oracle.params(dims, mass=0.1), 1e-12)
+    with Handle(dims, U, mass=0.1) as H:
+        x = torch.zeros(256, 4, 3, dtype=torch.complex128, device="cuda")
+        cp = lqcd.make_cg_params(lqcd.LQ_OP_WILSON_NORMAL, lqcd.LQ_CG_PLAIN, lqcd.LQ_F64, tol=1e-12)
+        rc, st = lqcd.cg_solve(H.h, x, dev(b), cp)
+        xg = host(x)
+    assert rc == 0 and st[0].status == 0
+    assert st[0].true_rel_residual < 2e-12
+    assert abs(st[0].iters - it_or) <= 2
+    assert rel_err(xg, x_lu) < 1e-12 * kappa
+
+
+@pytest.mark.parametrize("fmt", [lqcd.LQ_F64, lqcd.LQ_NATIVE | lqcd.LQ_F64])
+def test_eo_fp64_cg(fmt):
+    dims = (8, 8, 8, 8)
+    V = 8 ** 4
+    m = 0.05
+    U = inputs.gauge_field(dims, "smooth", seed=1001)
+    be = inputs.gaussian_spinor(V // 2, seed=2001)
+    prm = oracle.params(dims, mass=m)
+    x_or, it_or, _, rc_or = oracle.cg(oracle.OP_WILSON_EO, be, U, prm, 1e-10)
+    assert rc_or == oracle.OK
+    with Handle(dims, U, mass=m) as H:
+        bd = dev(be)
+        xd = torch.zeros_like(bd)
+        if fmt & lqcd.LQ_NATIVE:
+            n = lqcd.lq_field_bytes(H.h, fmt, lqcd.LQ_EVEN)
+            bn = torch.empty(n, dtype=torch.uint8, device="cuda")
+            xn = torch.empty(n, dtype=torch.uint8, device="cuda")
+            lqcd.lq_convert(H.h, bn, fmt, bd, lqcd.LQ_F64, lqcd.LQ_EVEN)
+            cp = lqcd.make_cg_params(lqcd.LQ_OP_WILSON_EO_NORMAL, lqcd.LQ_CG_PLAIN, fmt, tol=1e-10)
+            rc, st = lqcd.cg_solve(H.h, xn, bn, cp)
+            lqcd.lq_convert(H.h, xd, lqcd.LQ_F64, xn, fmt, lqcd.LQ_EVEN)
+        else:
+            cp = lqcd.make_cg_params(lqcd.LQ_OP_WILSON_EO_NORMAL, lqcd.LQ_CG_PLAIN, fmt, tol=1e-10)
+            rc, st = lqcd.cg_solve(H.h, xd, bd, cp)
+        xg = host(xd)
+    assert rc == 0
+    assert st[0].true_rel_residual < 2e-10
+    assert abs(st[0].iters - it_or) <= 3
+    assert rel_err(xg, x_or) < 1e-7
+
+
+@pytest.mark.parametrize("inner", [lqcd.LQ_F32, lqcd.LQ_F16, lqcd.LQ_BF16])
+@pytest.mark.parametrize("r12", [False, True])
+def test_mixed_eo_reaches_1e10(inner, r12):
+    dims = (8, 8, 8, 16)
+    V = int(np.prod(dims))
+    m = 0.02
+    U = inputs.gauge_field(dims, "smooth", seed=1002)
+    be = inputs.gaussian_spinor(V // 2, seed=2002)
+    x_or, _, _, _ = oracle.cg(oracle.OP_WILSON_EO, be, U, oracle.params(dims, mass=m), 1e-12)
+    with Handle(dims, U, mass=m, compress12=r12) as H:
+        bd = dev(be)
+        xd = torch.zeros_like(bd)
+        cp = lqcd.make_cg_params(lqcd.LQ_OP_WILSON_EO_NORMAL, lqcd.LQ_CG_MIXED, lqcd.LQ_F64, tol=1e-10,
+                                 inner=inner)
+        rc, st = lqcd.cg_solve(H.h, xd, bd, cp)
+        xg = host(xd)
+    assert rc == 0, lqcd.STATUS[rc]
+    assert st[0].true_rel_residual < 1e-10
+    assert st[0].outer_iters >= 1
+    assert rel_err(xg, x_or) < 1e-7
+
+
+def test_mixed_multi_rhs_point_sources_full_operator():
+    """Four of the 12 point sources, full-lattice D^dag D, batched mixed CG (FP16 inner)."""
+    dims = (4, 4, 4, 8)
+    V = int(np.prod(dims))
+    m = 0.05
+    U = inputs.gauge_field(dims, "smooth", seed=1003)
+    src = inputs.point_sources(V)[[0, 4, 7, 11]]
+    b = oracle.wilson_dslash(src, U, dims, m, dagger=True)
+    with Handle(dims, U, mass=m) as H:
+        bd = dev(b)
+        xd = torch.zeros_like(bd)
+        cp = lqcd.make_cg_params(lqcd.LQ_OP_WILSON_NORMAL, lqcd.LQ_CG_MIXED, lqcd.LQ_F64, nrhs=4, tol=1e-10,
+                                 inner=lqcd.LQ_F16)
+        rc, st = lqcd.cg_solve(H.h, xd, bd, cp)
+        xg = host(xd)
+    assert rc == 0
+    for k in range(4):
+        assert st[k].true_rel_residual < 1e-10
+        # D x = source
+        assert rel_err(oracle.wilson_dslash(xg[k], U, dims, m), src[k]) < 1e-8
+
+
+def test_fp32_plain_cg():
+    dims = (4, 4, 8, 8)
+    V = int(np.prod(dims))
+    U = inputs.gauge_field(dims, "smooth", seed=1004)
+    be = inputs.gaussian_spinor(V // 2, seed=2004)
+    with Handle(dims, U, mass=0.1) as H:
+        bd = dev(be, lqcd.LQ_F32)
+        xd = torch.zeros_like(bd)
+        cp = lqcd.make_cg_params(lqcd.LQ_OP_WILSON_EO_NORMAL, lqcd.LQ_CG_PLAIN, lqcd.LQ_F32, tol=1e-5)
+        rc, st = lqcd.cg_solve(H.h, xd, bd, cp)
+    assert rc == 0
+    assert st[0].true_rel_residual < 5e-5
+
+
+def test_dwf_cg_fp32_then_mixed_refinement():
+    """Domain wall: CG on D_dw^dag D_dw in FP32 to 1e-8 is out of FP32's reach,
+    so the mixed solver (FP32 inner) refines in FP64 to 1e-10."""
+    dims = (4, 4, 4, 4)
+    Ls, M5, mf = 8, 1.8, 0.01
+    V = int(np.prod(dims))
+    U = inputs.gauge_field(dims, "smooth", seed=1005)
+    eta = inputs.gaussian_spinor(V, seed=2005, nrhs=Ls)
+    prm = oracle.params(dims, Ls=Ls, M5=M5, mf=mf)
+    b = oracle.apply_op(oracle.OP_DWF, eta, U, prm, dagger=True)
+    with Handle(dims, U, Ls=Ls, M5=M5, mf=mf) as H:
+        bd = dev(b)
+        xd = torch.zeros_like(bd)
+        cp = lqcd.make_cg_params(lqcd.LQ_OP_DWF_NORMAL, lqcd.LQ_CG_MIXED, lqcd.LQ_F64, tol=1e-10,
+                                 inner=lqcd.LQ_F32, inner_tol=1e-6)
+        rc, st = lqcd.cg_solve(H.h, xd, bd, cp)
+        xg = host(xd)
+    assert rc == 0
+    assert st[0].true_rel_residual < 1e-10
+    assert rel_err(oracle.apply_op(oracle.OP_DWF, xg, U, prm), eta) < 1e-8
+
+
+def test_restart_from_guess_and_maxiter():
+    dims = (4, 4, 4, 4)
+    U = inputs.gauge_field(dims, "random", seed=1000)
+    b = inputs.gaussian_spinor(256, seed=2007)
+    with Handle(dims, U, mass=0.1) as H:
+        bd = dev(b)
+        x = torch.zeros_like(bd)
+        cp = lqcd.make_cg_params(lqcd.LQ_OP_WILSON_NORMAL, lqcd.LQ_CG_PLAIN, lqcd.LQ_F64, tol=1e-12, maxiter=3)
+        rc, st = lqcd.cg_solve(H.h, x, bd, cp, check=False)
+        assert rc == -5 and st[0].status == -5 and st[0].iters == 3
+        # restart from the 3-iteration iterate
+        cp = lqcd.make_cg_params(lqcd.LQ_OP_WILSON_NORMAL, lqcd.LQ_CG_PLAIN, lqcd.LQ_F64, tol=1e-12,
+                                 x0_is_guess=True)
+        rc, st = lqcd.cg_solve(H.h, x, bd, cp)
+        assert rc == 0 and st[0].true_rel_residual < 2e-12
+        # a guess that already meets the tolerance needs no iterations
+        cp = lqcd.make_cg_params(lqcd.LQ_OP_WILSON_NORMAL, lqcd.LQ_CG_PLAIN, lqcd.LQ_F64, tol=1e-10,
+                                 x0_is_guess=True)
+        rc, st = lqcd.cg_solve(H.h, x, bd, cp)
+        assert rc == 0 and st[0].iters == 0 and st[0].true_rel_residual < 2e-12
+
+
+def test_nan_source_is_reported():
+    dims = (4, 4, 4, 4)
+    U = inputs.gauge_field(dims, "unit")
+    b = inputs.gaussian_spinor(256, seed=1)
+    b[17, 2, 1] = np.nan
+    with Handle(dims, U, mass=0.1) as H:
+        bd = dev(b)
+        x = torch.zeros_like(bd)
+        cp = lqcd.make_cg_params(lqcd.LQ_OP_WILSON_NORMAL, lqcd.LQ_CG_PLAIN, lqcd.LQ_F64, tol=1e-10)
+        rc, st = lqcd.cg_solve(H.h, x, bd, cp, check=False)
+        assert rc == -8 and st[0].status == -8
+        cp = lqcd.make_cg_params(lqcd.LQ_OP_WILSON_NORMAL, lqcd.LQ_CG_MIXED, lqcd.LQ_F64, tol=1e-10,
+                                 inner=lqcd.LQ_F16)
+        rc, st = lqcd.cg_solve(H.h, x, bd, cp, check=False)
+        assert rc == -8
