@@ -142,6 +142,21 @@ int dslash_dag_apply(lq_handle *h, void *out, const void *in, int fmt, int parit
  */
 int dwf_dslash_apply(lq_handle *h, void *out, const void *in, int fmt, int dagger, void *stream);
 
+/*
+ * lq_dot: FP64 complex inner products <a, b> = sum_x conj(a(x)) . b(x) of
+ * nrhs pairs of fields (layout and precision fmt, sites as in lq_field_bytes;
+ * five_d != 0: one 5-d field of Ls slices).  result: DEVICE pointer to
+ * 2 * nrhs doubles, (re, im) per right-hand side, written asynchronously on
+ * `stream`.  Products are formed in the field's arithmetic precision and
+ * summed in FP64 (warp shuffles, one partial per block, fixed-order final
+ * sum by the last block), so repeated calls give identical results.  The
+ * reduction partials live in handle workspace that grows (cudaMalloc) on
+ * first use.  It is the global reduction the CG solvers iterate on (the
+ * paper's benchmark, Sec. 3.3, times the operator alone).
+ */
+int lq_dot(lq_handle *h, double *result, const void *a, const void *b, int fmt, int subset, int nrhs, int five_d,
+           void *stream);
+
 /* ------------------------------------------------------------------- CG */
 
 enum {

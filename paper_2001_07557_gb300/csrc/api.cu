@@ -5,6 +5,7 @@
 #include <cstring>
 #include <new>
 
+#include "blas.h"
 #include "handle.h"
 
 namespace lq {
@@ -354,6 +355,36 @@ int dwf_dslash_apply(lq_handle* h, void* out, const void* in, int fmt, int dagge
             return LQ_ERR_CUDA;
     }
     return LQ_OK;
+}
+
+int lq_dot(lq_handle* h, double* result, const void* a, const void* b, int fmt, int subset, int nrhs, int five_d,
+           void* stream) {
+    if (!h || !result || !a || !b || !valid_fmt(fmt)) return LQ_ERR_ARG;
+    if (subset < LQ_FULL || subset > LQ_ODD) return LQ_ERR_ARG;
+    if (!aligned16(a) || !aligned16(b) || (reinterpret_cast<uintptr_t>(result) & 7u)) return LQ_ERR_LAYOUT;
+    long nsites;
+    if (five_d) {
+        if (h->p.Ls < 1) return LQ_ERR_ARG;
+        nrhs = 1;
+        nsites = 2L * h->g.Vh * h->p.Ls;
+    } else {
+        if (nrhs < 1) return LQ_ERR_ARG;
+        nsites = (subset == LQ_FULL ? 2L : 1L) * h->g.Vh;
+    }
+    if (nrhs > 65535) return LQ_ERR_ARG;
+    DeviceGuard dg(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool native = (fmt & LQ_NATIVE) != 0;
+    const int prec = fmt & 0xF;
+    const size_t site_bytes = native ? (size_t)spinor_site_bytes(prec) : (size_t)24 * (prec == LQ_F64 ? 8 : 4);
+    void* ws;
+    const size_t nb = sizeof(double) * 2 * kMaxGrid * (size_t)nrhs + sizeof(unsigned) * nrhs;
+    int rc = ensure_ws(h, WS_DOT, nb, &ws);
+    if (rc) return rc;
+    double* partial = static_cast<double*>(ws);
+    unsigned* tickets = reinterpret_cast<unsigned*>(partial + 2 * kMaxGrid * (size_t)nrhs);
+    if (cudaMemsetAsync(tickets, 0, sizeof(unsigned) * nrhs, st) != cudaSuccess) return LQ_ERR_CUDA;
+    return status_of(launch_cdot(fmt, a, b, site_bytes * nsites, nsites, h->g.Vh, nrhs, partial, tickets, result, st));
 }
 
 const char* lq_status_string(int status) {

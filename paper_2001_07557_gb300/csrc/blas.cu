@@ -62,6 +62,15 @@ __device__ __forceinline__ const char* blk_ptr(const VecRef& v, int rhs, int b, 
 
 __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 
+// Arithmetic type of a vector kernel: FP64 if any operand is stored in FP64, else FP32.
+template <int... Ps>
+struct ComputeT {
+    static constexpr int prec = ((Ps == LQ_F64) || ...) ? LQ_F64 : LQ_F32;
+    using type = typename std::conditional<prec == LQ_F64, double, float>::type;
+};
+template <int... Ps>
+using Compute = typename ComputeT<Ps...>::type;
+
 // ---------------------------------------------------------------- kernels
 
 // sum_re <a, b> per rhs; finalize: FIN_ALPHA (pAp -> alpha) or store into out[rhs]
@@ -70,16 +79,18 @@ __global__ void __launch_bounds__(kThreads) dot_kernel(VecRef a, VecRef b, int V
                                                        unsigned* tickets, CgScalars* st, double* out, int fin) {
     const int rhs = blockIdx.y;
     if (st && st[rhs].done) return;
-    using TA = typename Prec<PA>::real;
+    using T = Compute<PA, PB>;
     double acc = 0;
     const long n = (long)Vh * nblk;
     for (long j = (long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
         const int bk = (int)(j / Vh), i = (int)(j - (long)bk * Vh);
-        cplx<double> sa[12], sb[12];
-        load_spinor<PA, double>(blk_ptr<PA, TA>(a, rhs, bk, Vh), Vh, i, sa);
-        load_spinor<PB, double>(blk_ptr<PB, TA>(b, rhs, bk, Vh), Vh, i, sb);
+        cplx<T> sa[12], sb[12];
+        load_spinor<PA, T>(blk_ptr<PA, T>(a, rhs, bk, Vh), Vh, i, sa);
+        load_spinor<PB, T>(blk_ptr<PB, T>(b, rhs, bk, Vh), Vh, i, sb);
+        T site = 0;
 #pragma unroll
-        for (int k = 0; k < 12; ++k) acc += sa[k].re * sb[k].re + sa[k].im * sb[k].im;
+        for (int k = 0; k < 12; ++k) site += sa[k].re * sb[k].re + sa[k].im * sb[k].im;
+        acc += (double)site;
     }
     double total;
     if (!reduce_last(acc, scratch + (size_t)rhs * gridDim.x, tickets + rhs, gridDim.x, total)) return;
@@ -106,36 +117,29 @@ __global__ void __launch_bounds__(kThreads) cg_update_kernel(VecRef x, VecRef p,
     const int rhs = blockIdx.y;
     CgScalars& s = st[rhs];
     if (s.done) return;
-    const double alpha = s.alpha;
+    using T = Compute<PX, PP, PR, PQ>;
+    const T alpha = (T)s.alpha;
     double acc = 0;
     const long n = (long)Vh * nblk;
     for (long j = (long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
         const int bk = (int)(j / Vh), i = (int)(j - (long)bk * Vh);
-        cplx<double> xs[12], ps[12], rs[12], qs[12];
-        load_spinor<PX, double>(blk_ptr<PX, double>(x, rhs, bk, Vh), Vh, i, xs);
-        load_spinor<PP, double>(blk_ptr<PP, double>(p, rhs, bk, Vh), Vh, i, ps);
-        load_spinor<PR, double>(blk_ptr<PR, double>(r, rhs, bk, Vh), Vh, i, rs);
-        load_spinor<PQ, double>(blk_ptr<PQ, double>(q, rhs, bk, Vh), Vh, i, qs);
+        cplx<T> xs[12], ps[12], rs[12], qs[12];
+        load_spinor<PX, T>(blk_ptr<PX, T>(x, rhs, bk, Vh), Vh, i, xs);
+        load_spinor<PP, T>(blk_ptr<PP, T>(p, rhs, bk, Vh), Vh, i, ps);
+        load_spinor<PR, T>(blk_ptr<PR, T>(r, rhs, bk, Vh), Vh, i, rs);
+        load_spinor<PQ, T>(blk_ptr<PQ, T>(q, rhs, bk, Vh), Vh, i, qs);
+        T site = 0;
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             xs[k].re = fma(alpha, ps[k].re, xs[k].re);
             xs[k].im = fma(alpha, ps[k].im, xs[k].im);
             rs[k].re = fma(-alpha, qs[k].re, rs[k].re);
             rs[k].im = fma(-alpha, qs[k].im, rs[k].im);
+            site += rs[k].re * rs[k].re + rs[k].im * rs[k].im;
         }
-        if constexpr (PR != LQ_F64) {
-            // accumulate the norm of the value as stored
-            cplx<float> rf[12];
-#pragma unroll
-            for (int k = 0; k < 12; ++k) rf[k] = {(float)rs[k].re, (float)rs[k].im};
-#pragma unroll
-            for (int k = 0; k < 12; ++k) acc += (double)rf[k].re * rf[k].re + (double)rf[k].im * rf[k].im;
-        } else {
-#pragma unroll
-            for (int k = 0; k < 12; ++k) acc += rs[k].re * rs[k].re + rs[k].im * rs[k].im;
-        }
-        store_spinor<PX, double>(const_cast<char*>(blk_ptr<PX, double>(x, rhs, bk, Vh)), Vh, i, xs);
-        store_spinor<PR, double>(const_cast<char*>(blk_ptr<PR, double>(r, rhs, bk, Vh)), Vh, i, rs);
+        acc += (double)site;
+        store_spinor<PX, T>(const_cast<char*>(blk_ptr<PX, T>(x, rhs, bk, Vh)), Vh, i, xs);
+        store_spinor<PR, T>(const_cast<char*>(blk_ptr<PR, T>(r, rhs, bk, Vh)), Vh, i, rs);
     }
     double total;
     if (!reduce_last(acc, scratch + (size_t)rhs * gridDim.x, tickets + rhs, gridDim.x, total)) return;
@@ -160,19 +164,20 @@ template <int PP, int PR>
 __global__ void __launch_bounds__(kThreads) cg_xpay_kernel(VecRef p, VecRef r, int Vh, int nblk, const CgScalars* st) {
     const int rhs = blockIdx.y;
     if (st[rhs].done) return;
-    const double beta = st[rhs].beta;
+    using T = Compute<PP, PR>;
+    const T beta = (T)st[rhs].beta;
     const long n = (long)Vh * nblk;
     for (long j = (long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
         const int bk = (int)(j / Vh), i = (int)(j - (long)bk * Vh);
-        cplx<double> ps[12], rs[12];
-        load_spinor<PP, double>(blk_ptr<PP, double>(p, rhs, bk, Vh), Vh, i, ps);
-        load_spinor<PR, double>(blk_ptr<PR, double>(r, rhs, bk, Vh), Vh, i, rs);
+        cplx<T> ps[12], rs[12];
+        load_spinor<PP, T>(blk_ptr<PP, T>(p, rhs, bk, Vh), Vh, i, ps);
+        load_spinor<PR, T>(blk_ptr<PR, T>(r, rhs, bk, Vh), Vh, i, rs);
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             ps[k].re = fma(beta, ps[k].re, rs[k].re);
             ps[k].im = fma(beta, ps[k].im, rs[k].im);
         }
-        store_spinor<PP, double>(const_cast<char*>(blk_ptr<PP, double>(p, rhs, bk, Vh)), Vh, i, ps);
+        store_spinor<PP, T>(const_cast<char*>(blk_ptr<PP, T>(p, rhs, bk, Vh)), Vh, i, ps);
     }
 }
 
@@ -218,6 +223,110 @@ __global__ void cg_init_kernel(CgScalars* st, const double* rr, const double* bb
     }
 }
 
+// Two-component variant of reduce_last (real and imaginary parts).
+__device__ bool reduce_last2(double v0, double v1, double* partial, unsigned* ticket, int nblk_x, double& t0,
+                             double& t1) {
+    __shared__ double ws[2][kThreads / 32];
+    __shared__ bool last;
+    v0 = warp_sum(v0);
+    v1 = warp_sum(v1);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        ws[0][wid] = v0;
+        ws[1][wid] = v1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s0 = 0, s1 = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            s0 += ws[0][w];
+            s1 += ws[1][w];
+        }
+        partial[2 * blockIdx.x] = s0;
+        partial[2 * blockIdx.x + 1] = s1;
+        __threadfence();
+        const unsigned t = atomicAdd(ticket, 1u);
+        last = (t == (unsigned)nblk_x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double s0 = 0, s1 = 0;
+    for (int b = threadIdx.x; b < nblk_x; b += blockDim.x) {
+        s0 += __ldcg(partial + 2 * b);
+        s1 += __ldcg(partial + 2 * b + 1);
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    __syncthreads();
+    if (lane == 0) {
+        ws[0][wid] = s0;
+        ws[1][wid] = s1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a0 = 0, a1 = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a0 += ws[0][w];
+            a1 += ws[1][w];
+        }
+        t0 = a0;
+        t1 = a1;
+        *ticket = 0;
+    }
+    __syncthreads();
+    return true;
+}
+
+// 12 complex numbers of site j of one right-hand side, native or site-major
+template <int P, bool NATIVE>
+__device__ __forceinline__ void load_site(const char* base, size_t rhs_stride, int rhs, long j, int Vh,
+                                          cplx<double> (&s)[12]) {
+    const char* r = base + (size_t)rhs * rhs_stride;
+    if constexpr (NATIVE) {
+        const int bk = (int)(j / Vh), i = (int)(j - (long)bk * Vh);
+        load_spinor<P, double>(r + (size_t)bk * spinor_site_bytes(P) * Vh, Vh, i, s);
+    } else if constexpr (P == LQ_F64) {
+        const double2* q = reinterpret_cast<const double2*>(r) + j * 12;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            double2 v = q[k];
+            s[k] = {v.x, v.y};
+        }
+    } else {
+        const float2* q = reinterpret_cast<const float2*>(r) + j * 12;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            float2 v = q[k];
+            s[k] = {(double)v.x, (double)v.y};
+        }
+    }
+}
+
+// <a, b> = sum conj(a) b per right-hand side, FP64 accumulation; result[2 rhs + {0,1}] = (re, im)
+template <int P, bool NATIVE>
+__global__ void __launch_bounds__(kThreads) cdot_kernel(const char* a, const char* b, size_t rhs_stride, long nsites,
+                                                        int Vh, double* scratch, unsigned* tickets, double* result) {
+    const int rhs = blockIdx.y;
+    double re = 0, im = 0;
+    for (long j = (long)blockIdx.x * blockDim.x + threadIdx.x; j < nsites; j += (long)gridDim.x * blockDim.x) {
+        cplx<double> sa[12], sb[12];
+        load_site<P, NATIVE>(a, rhs_stride, rhs, j, Vh, sa);
+        load_site<P, NATIVE>(b, rhs_stride, rhs, j, Vh, sb);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            re += sa[k].re * sb[k].re + sa[k].im * sb[k].im;
+            im += sa[k].re * sb[k].im - sa[k].im * sb[k].re;
+        }
+    }
+    double t0, t1;
+    if (!reduce_last2(re, im, scratch + (size_t)rhs * 2 * gridDim.x, tickets + rhs, gridDim.x, t0, t1)) return;
+    if (threadIdx.x == 0) {
+        result[2 * rhs] = t0;
+        result[2 * rhs + 1] = t1;
+    }
+}
+
 int grid_x(int Vh, int nblk) {
     static int sms = 0;
     if (!sms) {
@@ -243,6 +352,29 @@ int grid_x(int Vh, int nblk) {
     }
 
 size_t reduce_scratch_doubles(int Vh, int nblk, int nrhs) { return (size_t)grid_x(Vh, nblk) * nrhs; }
+
+int cdot_grid(long nsites) {
+    const long want = (nsites + kThreads - 1) / kThreads;
+    const long cap = (long)kMaxGrid;
+    return (int)(want < cap ? want : cap);
+}
+
+cudaError_t launch_cdot(int fmt, const void* a, const void* b, size_t rhs_stride, long nsites, int Vh, int nrhs,
+                        double* scratch, unsigned* tickets, double* result, cudaStream_t s) {
+    const int prec = fmt & 0xF;
+    const bool native = (fmt & LQ_NATIVE) != 0;
+    dim3 grid(cdot_grid(nsites), nrhs);
+    const char* pa = static_cast<const char*>(a);
+    const char* pb = static_cast<const char*>(b);
+    if (native) {
+        LQ_P_SWITCH(prec, P, (cdot_kernel<P, true><<<grid, kThreads, 0, s>>>(pa, pb, rhs_stride, nsites, Vh, scratch, tickets, result)))
+    } else if (prec == LQ_F64) {
+        cdot_kernel<LQ_F64, false><<<grid, kThreads, 0, s>>>(pa, pb, rhs_stride, nsites, Vh, scratch, tickets, result);
+    } else {
+        cdot_kernel<LQ_F32, false><<<grid, kThreads, 0, s>>>(pa, pb, rhs_stride, nsites, Vh, scratch, tickets, result);
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_dot(const VecRef& a, const VecRef& b, int Vh, int nblk, int nrhs, const Scratch& sc,
                        CgScalars* st, double* out, int fin, cudaStream_t s) {

@@ -49,6 +49,12 @@ cudaError_t launch_cg_xpay(const VecRef& p, const VecRef& r, int Vh, int nblk, i
                            cudaStream_t s);
 cudaError_t launch_axpby(const VecRef& y, const VecRef& x, double a, double b, int Vh, int nblk, int nrhs,
                          cudaStream_t s);
+// Complex dot <a, b> per rhs of nsites sites each (site-major or native fmt);
+// scratch: 2 * kMaxGrid * nrhs doubles, tickets: nrhs zeros; result: 2 * nrhs doubles (device).
+constexpr int kMaxGrid = 152 * 8;
+cudaError_t launch_cdot(int fmt, const void* a, const void* b, size_t rhs_stride, long nsites, int Vh, int nrhs,
+                        double* scratch, unsigned* tickets, double* result, cudaStream_t s);
+
 cudaError_t launch_cg_init(CgScalars* st, const double* rr, const double* bb, double tol, int maxiter, int nrhs,
                            cudaStream_t s);
 

@@ -32,8 +32,8 @@ struct lq_handle {
 namespace lq {
 
 // workspace slots: conversions 0-2; solver vectors 3-7 (inner CG), 8-12 (FP64
-// residuals), 13-15 (defect-correction vectors); 19 solver scalars
-enum { WS_IN = 0, WS_OUT = 1, WS_TMP = 2, WS_CG0 = 3, WS_CTL = 19 };
+// residuals), 13-15 (defect-correction vectors); 18 lq_dot partials; 19 solver scalars
+enum { WS_IN = 0, WS_OUT = 1, WS_TMP = 2, WS_CG0 = 3, WS_DOT = 18, WS_CTL = 19 };
 
 inline int status_of(cudaError_t e) { return e == cudaSuccess ? LQ_OK : LQ_ERR_CUDA; }
 

@@ -26,7 +26,7 @@ STATUS = {0: "LQ_OK", -1: "LQ_ERR_ARG", -2: "LQ_ERR_LAYOUT", -3: "LQ_ERR_CUDA", 
 
 # every function the header declares
 EXPORTS = ["lq_create", "lq_destroy", "lq_field_bytes", "lq_convert", "dslash_apply", "dslash_dag_apply",
-           "dwf_dslash_apply", "cg_solve", "lq_batch_cg_solve", "lq_status_string"]
+           "dwf_dslash_apply", "lq_dot", "cg_solve", "lq_batch_cg_solve", "lq_status_string"]
 
 
 class LqError(RuntimeError):
@@ -70,6 +70,7 @@ def lib():
         L.dslash_apply.argtypes = [vp, vp, vp, i, i, i, vp]
         L.dslash_dag_apply.argtypes = [vp, vp, vp, i, i, i, vp]
         L.dwf_dslash_apply.argtypes = [vp, vp, vp, i, i, vp]
+        L.lq_dot.argtypes = [vp, vp, vp, vp, i, i, i, i, vp]
         L.cg_solve.argtypes = [vp, vp, vp, ctypes.POINTER(lq_cg_params), ctypes.POINTER(lq_cg_stats), vp]
         L.lq_batch_cg_solve.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                         ctypes.POINTER(lq_cg_params), ctypes.POINTER(lq_cg_stats), vp]
@@ -146,6 +147,12 @@ def dslash_dag_apply(h, out, inp, fmt, parity=LQ_FULL, nrhs=1, stream=None):
 
 def dwf_dslash_apply(h, out, inp, fmt, dagger=False, stream=None):
     _check(lib().dwf_dslash_apply(h, _ptr(out), _ptr(inp), fmt, int(dagger), _stream(stream)), "dwf_dslash_apply")
+
+
+def lq_dot(h, result, a, b, fmt, subset=LQ_FULL, nrhs=1, five_d=False, stream=None):
+    """result: device float64 tensor of 2 * nrhs entries, (re, im) per right-hand side."""
+    _check(lib().lq_dot(h, _ptr(result), _ptr(a), _ptr(b), fmt, subset, nrhs, int(five_d), _stream(stream)),
+           "lq_dot")
 
 
 def make_cg_params(op, mode=LQ_CG_PLAIN, fmt=LQ_F64, nrhs=1, tol=1e-10, maxiter=100000, inner=LQ_F32,
