@@ -157,6 +157,30 @@ int dwf_dslash_apply(lq_handle *h, void *out, const void *in, int fmt, int dagge
 int lq_dot(lq_handle *h, double *result, const void *a, const void *b, int fmt, int subset, int nrhs, int five_d,
            void *stream);
 
+/*
+ * lq_dot_noalloc: lq_dot for callers that cannot allocate device memory.
+ * The paper has no counterpart; this is a service of the library.
+ * lq_dot grows handle workspace with cudaMalloc on first use, which some
+ * callers cannot allow: code that manages the whole device memory budget
+ * through its own pool, latency-critical loops in which cudaMalloc/cudaFree
+ * would synchronise the device, and code running while a stream is being
+ * captured, where allocation calls fail.  This call runs the same reduction
+ * with its scratch in a fixed file-scope device array (about 0.6 MB, held by
+ * every GPU that loads the library until the process exits) and calls no
+ * allocating routine.  Arguments and result are those of lq_dot.
+ *   - nrhs (1 for five_d) must be <= LQ_DOT_NOALLOC_MAX_RHS, else LQ_ERR_ARG.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call on a device shares the one array and leaves its contents
+ *     behind (the call clears what must start at zero).  Calls whose work
+ *     overlaps on the GPU -- concurrent streams, or threads sharing a device
+ *     without ordering -- race on the array; order them on one stream.
+ */
+#define LQ_DOT_NOALLOC_MAX_RHS 32
+int lq_dot_noalloc(lq_handle *h, double *result, const void *a, const void *b, int fmt, int subset, int nrhs,
+                   int five_d, void *stream);
+
 /* ------------------------------------------------------------------- CG */
 
 enum {

@@ -26,7 +26,8 @@ STATUS = {0: "LQ_OK", -1: "LQ_ERR_ARG", -2: "LQ_ERR_LAYOUT", -3: "LQ_ERR_CUDA", 
 
 # every function the header declares
 EXPORTS = ["lq_create", "lq_destroy", "lq_field_bytes", "lq_convert", "dslash_apply", "dslash_dag_apply",
-           "dwf_dslash_apply", "lq_dot", "cg_solve", "lq_batch_cg_solve", "lq_status_string"]
+           "dwf_dslash_apply", "lq_dot", "lq_dot_noalloc", "cg_solve", "lq_batch_cg_solve", "lq_status_string"]
+LQ_DOT_NOALLOC_MAX_RHS = 32
 
 
 class LqError(RuntimeError):
@@ -71,6 +72,7 @@ def lib():
         L.dslash_dag_apply.argtypes = [vp, vp, vp, i, i, i, vp]
         L.dwf_dslash_apply.argtypes = [vp, vp, vp, i, i, vp]
         L.lq_dot.argtypes = [vp, vp, vp, vp, i, i, i, i, vp]
+        L.lq_dot_noalloc.argtypes = [vp, vp, vp, vp, i, i, i, i, vp]
         L.cg_solve.argtypes = [vp, vp, vp, ctypes.POINTER(lq_cg_params), ctypes.POINTER(lq_cg_stats), vp]
         L.lq_batch_cg_solve.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                         ctypes.POINTER(lq_cg_params), ctypes.POINTER(lq_cg_stats), vp]
@@ -153,6 +155,13 @@ def lq_dot(h, result, a, b, fmt, subset=LQ_FULL, nrhs=1, five_d=False, stream=No
     """result: device float64 tensor of 2 * nrhs entries, (re, im) per right-hand side."""
     _check(lib().lq_dot(h, _ptr(result), _ptr(a), _ptr(b), fmt, subset, nrhs, int(five_d), _stream(stream)),
            "lq_dot")
+
+
+def lq_dot_noalloc(h, result, a, b, fmt, subset=LQ_FULL, nrhs=1, five_d=False, stream=None):
+    """lq_dot without any device allocation (scratch in a fixed device array);
+    nrhs <= LQ_DOT_NOALLOC_MAX_RHS."""
+    _check(lib().lq_dot_noalloc(h, _ptr(result), _ptr(a), _ptr(b), fmt, subset, nrhs, int(five_d),
+                                _stream(stream)), "lq_dot_noalloc")
 
 
 def make_cg_params(op, mode=LQ_CG_PLAIN, fmt=LQ_F64, nrhs=1, tol=1e-10, maxiter=100000, inner=LQ_F32,
