@@ -212,11 +212,11 @@ int lq_create(lq_handle** hp, const lq_params* p, const void* U, int U_prec, voi
     if (!aligned16(U)) return LQ_ERR_LAYOUT;
     long long V = 1;
     for (int mu = 0; mu < 4; ++mu) {
-        if (p->dims[mu] < 2 || (p->dims[mu] & 1)) return LQ_ERR_LAYOUT;
+        if (p->dims[mu] < 2 || (p->dims[mu] & 1) || p->dims[mu] > 8192) return LQ_ERR_LAYOUT;
         if (p->bc[mu] != 1 && p->bc[mu] != -1) return LQ_ERR_ARG;
         V *= p->dims[mu];
     }
-    if (V / 2 >= (1LL << 31) / 16) return LQ_ERR_LAYOUT;  // plane offsets stay in 32-bit products
+    if (V / 2 >= (1LL << 27)) return LQ_ERR_LAYOUT;  // cb indices < 2^27: exact fast division
     if (p->r != 1.0) return LQ_ERR_ARG;
     if (p->Ls < 0 || p->Ls > 4096) return LQ_ERR_ARG;
     lq_handle* h = new (std::nothrow) lq_handle;
@@ -229,6 +229,9 @@ int lq_create(lq_handle** hp, const lq_params* p, const void* U, int U_prec, voi
     }
     h->g.Lh0 = p->dims[0] / 2;
     h->g.Vh = (int)(V / 2);
+    h->g.mLh0 = div_magic(h->g.Lh0);
+    h->g.mL1 = div_magic(p->dims[1]);
+    h->g.mL2 = div_magic(p->dims[2]);
     for (int k = 0; k < 4; ++k) h->hop_block[k] = 128;
     if (cudaGetDevice(&h->device) != cudaSuccess) {
         delete h;

@@ -70,34 +70,52 @@ __global__ void __launch_bounds__(128) wilson_hop_kernel(const HopArgs a) {
     const char* __restrict__ Lp = a.links + (size_t)(p * 4) * a.link_block;
     const char* __restrict__ Lq = a.links + (size_t)((1 - p) * 4) * a.link_block;
 
-#define LQ_HOP_DIR(MU)                                                   \
-    {                                                                    \
-        cplx<T> s[12], h[6], uh[6], u[9];                                \
-        load_spinor<P, T>(in, g.Vh, nf[MU], s);                          \
-        load_link<P, R12, T>(Lp + (size_t)(MU)*a.link_block, g.Vh, i, u); \
-        project<MU, SF>(s, h);                                           \
-        if (sf[MU]) {                                                    \
-            _Pragma("unroll") for (int k = 0; k < 6; ++k) h[k] = cneg(h[k]); \
-        }                                                                \
-        su3_mul<false>(u, h, uh);                                        \
-        reconstruct_add<MU, SF>(acc, uh);                                \
-    }                                                                    \
-    {                                                                    \
-        cplx<T> s[12], h[6], uh[6], u[9];                                \
-        load_spinor<P, T>(in, g.Vh, nb[MU], s);                          \
-        load_link<P, R12, T>(Lq + (size_t)(MU)*a.link_block, g.Vh, nb[MU], u); \
-        project<MU, SB>(s, h);                                           \
-        if (sb[MU]) {                                                    \
-            _Pragma("unroll") for (int k = 0; k < 6; ++k) h[k] = cneg(h[k]); \
-        }                                                                \
-        su3_mul<true>(u, h, uh);                                         \
-        reconstruct_add<MU, SB>(acc, uh);                                \
+    // The 8 directions D = 2 mu + (0 forward, 1 backward) run as a two-stage
+    // pipeline: the packed spinor and link of direction D+1 are loaded before
+    // direction D is unpacked and computed.  FP16/BF16: the site norm and the
+    // boundary phase multiply the accumulation FMAs; FP32/FP64: a crossing hop
+    // negates its half spinor.
+    constexpr bool NORM = Prec<P>::has_norm;
+    RawSpinor<P> rs[2];
+    RawLink<P, R12> rl[2];
+    auto load_dir = [&](int D, int slot) {
+        const int mu = D >> 1;
+        const bool fwd = (D & 1) == 0;
+        raw_load(rs[slot], in, g.Vh, fwd ? nf[mu] : nb[mu]);
+        raw_load(rl[slot], (fwd ? Lp : Lq) + (size_t)mu * a.link_block, g.Vh, fwd ? i : nb[mu]);
+    };
+#define LQ_HOP_DIR(D)                                                                  \
+    {                                                                                  \
+        constexpr int MU = (D) >> 1;                                                   \
+        constexpr bool FWD = ((D)&1) == 0;                                             \
+        constexpr int S = FWD ? SF : SB;                                               \
+        if constexpr ((D) < 7) load_dir((D) + 1, ((D) + 1) & 1);                      \
+        cplx<T> s[12], h[6], uh[6], u[9];                                              \
+        T nrm;                                                                         \
+        raw_unpack<P, T>(rs[(D)&1], s, nrm);                                           \
+        project<MU, S>(s, h);                                                          \
+        raw_unpack<P, R12, T>(rl[(D)&1], u);                                           \
+        const bool sgn = FWD ? sf[MU] : sb[MU];                                        \
+        if constexpr (NORM) {                                                          \
+            su3_mul<!FWD>(u, h, uh);                                                   \
+            reconstruct_fma<MU, S>(acc, uh, sgn ? -nrm : nrm);                         \
+        } else {                                                                       \
+            if (sgn) {                                                                 \
+                _Pragma("unroll") for (int k = 0; k < 6; ++k) h[k] = cneg(h[k]);       \
+            }                                                                          \
+            su3_mul<!FWD>(u, h, uh);                                                   \
+            reconstruct_add<MU, S>(acc, uh);                                           \
+        }                                                                              \
     }
-
+    load_dir(0, 0);
     LQ_HOP_DIR(0)
     LQ_HOP_DIR(1)
     LQ_HOP_DIR(2)
     LQ_HOP_DIR(3)
+    LQ_HOP_DIR(4)
+    LQ_HOP_DIR(5)
+    LQ_HOP_DIR(6)
+    LQ_HOP_DIR(7)
 #undef LQ_HOP_DIR
 
     const T ch = (T)a.c_hop;

@@ -1,0 +1,341 @@
+// hop_async.cuh -- the Wilson hop for FP32 / FP16 / BF16 storage with its
+// neighbour gathers staged through shared memory by asynchronous copies.
+//
+// The single-right-hand-side hop is a bandwidth-bound gather: per output
+// site it reads 8 neighbour spinors and 8 links.  Holding enough bytes in
+// flight to cover HBM latency with plain loads costs registers (and so
+// occupancy).  Here every thread streams its 8 (spinor, link) pairs through
+// a private S-stage ring in shared memory with cp.async (16/8/4-byte
+// copies that bypass the register file): the copies of directions D+1 ..
+// D+S-1 are in flight while direction D is computed.  A thread reads back
+// only the slots it filled itself, so no block-wide barrier is needed; the
+// per-thread wait on its own copy groups (wait_prior) orders the data.
+//
+// Shared-memory layout of one stage: chunk-major [chunk][thread], 16-byte
+// spinor chunks, then the site norms (FP16/BF16), then the link chunks, so a
+// warp reading chunk k touches one contiguous 512-byte (or 256/128-byte) row.
+#pragma once
+
+#include <cuda_pipeline.h>
+
+#include "lqcd_internal.cuh"
+#include "lqcd_kernels.h"
+
+namespace lq {
+
+template <int P, bool R12>
+struct AsyncLayout {
+    static constexpr bool NORM = Prec<P>::has_norm;
+    static constexpr int SP_CH = (P == LQ_F32) ? 6 : 3;  // 16-byte spinor chunks
+    static constexpr int LK_CH = R12 ? 3 : 9;             // link chunks
+    static constexpr int LK_B = (P == LQ_F32) ? (R12 ? 16 : 8) : (R12 ? 8 : 4);  // bytes per link chunk
+};
+
+template <int P, bool R12, int NT>
+struct AsyncStage {
+    using L = AsyncLayout<P, R12>;
+    static constexpr int SP_OFF = 0;
+    static constexpr int NRM_OFF = SP_OFF + L::SP_CH * 16 * NT;
+    static constexpr int LK_OFF = NRM_OFF + (L::NORM ? 4 * NT : 0);
+    static constexpr int BYTES = ((LK_OFF + L::LK_CH * L::LK_B * NT) + 15) / 16 * 16;
+    static constexpr int SPIN_BYTES = ((L::SP_CH * 16 + (L::NORM ? 4 : 0)) * NT + 15) / 16 * 16;
+};
+
+// issue the copies of one spinor (all chunks + norm) into a spinor slot
+template <int P, bool R12, int NT>
+__device__ __forceinline__ void async_spinor(unsigned char* slot, const char* __restrict__ blk, int Vh, int site,
+                                             int t) {
+    using L = AsyncLayout<P, R12>;
+    using St = AsyncStage<P, R12, NT>;
+#pragma unroll
+    for (int k = 0; k < L::SP_CH; ++k)
+        __pipeline_memcpy_async(slot + St::SP_OFF + (k * NT + t) * 16, blk + ((size_t)k * Vh + site) * 16, 16);
+    if constexpr (L::NORM)
+        __pipeline_memcpy_async(slot + St::NRM_OFF + t * 4, blk + (size_t)48 * Vh + (size_t)site * 4, 4);
+}
+
+template <int P, bool R12, int NT>
+__device__ __forceinline__ void async_link(unsigned char* stage, const char* __restrict__ blk, int Vh, int site,
+                                           int t) {
+    using L = AsyncLayout<P, R12>;
+    using St = AsyncStage<P, R12, NT>;
+#pragma unroll
+    for (int k = 0; k < L::LK_CH; ++k)
+        __pipeline_memcpy_async(stage + St::LK_OFF + (k * NT + t) * L::LK_B,
+                                blk + ((size_t)k * Vh + site) * L::LK_B, L::LK_B);
+}
+
+// read one staged spinor back (unscaled values + norm)
+template <int P, bool R12, int NT>
+__device__ __forceinline__ void smem_spinor(const unsigned char* slot, int t, cplx<float> (&s)[12], float& nrm) {
+    using L = AsyncLayout<P, R12>;
+    using St = AsyncStage<P, R12, NT>;
+    if constexpr (P == LQ_F32) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float4 v = *reinterpret_cast<const float4*>(slot + St::SP_OFF + (k * NT + t) * 16);
+            s[2 * k] = {v.x, v.y};
+            s[2 * k + 1] = {v.z, v.w};
+        }
+        nrm = 1.f;
+    } else {
+        std::integral_constant<int, P> tag;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint4 v = *reinterpret_cast<const uint4*>(slot + St::SP_OFF + (k * NT + t) * 16);
+            float2 a = h2f(v.x, tag), b = h2f(v.y, tag), c = h2f(v.z, tag), d = h2f(v.w, tag);
+            s[4 * k + 0] = {a.x, a.y};
+            s[4 * k + 1] = {b.x, b.y};
+            s[4 * k + 2] = {c.x, c.y};
+            s[4 * k + 3] = {d.x, d.y};
+        }
+        nrm = *reinterpret_cast<const float*>(slot + St::NRM_OFF + t * 4);
+    }
+    (void)sizeof(L);
+}
+
+template <int P, bool R12, int NT>
+__device__ __forceinline__ void smem_link(const unsigned char* stage, int t, cplx<float> (&u)[9]) {
+    using L = AsyncLayout<P, R12>;
+    using St = AsyncStage<P, R12, NT>;
+    const unsigned char* b = stage + St::LK_OFF;
+    if constexpr (P == LQ_F32) {
+        if constexpr (R12) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float4 v = *reinterpret_cast<const float4*>(b + (k * NT + t) * 16);
+                u[2 * k] = {v.x, v.y};
+                u[2 * k + 1] = {v.z, v.w};
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const float2 v = *reinterpret_cast<const float2*>(b + (k * NT + t) * 8);
+                u[k] = {v.x, v.y};
+            }
+        }
+    } else {
+        std::integral_constant<int, P> tag;
+        if constexpr (R12) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const uint2 v = *reinterpret_cast<const uint2*>(b + (k * NT + t) * 8);
+                float2 x = h2f(v.x, tag), y = h2f(v.y, tag);
+                u[2 * k] = {x.x, x.y};
+                u[2 * k + 1] = {y.x, y.y};
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const float2 x = h2f(*reinterpret_cast<const uint32_t*>(b + (k * NT + t) * 4), tag);
+                u[k] = {x.x, x.y};
+            }
+        }
+    }
+    (void)sizeof(L);
+    if constexpr (R12) reconstruct_row2(u);
+}
+
+template <int P, bool R12, int NT, int EPI>
+constexpr int async_smem_bytes(int S) {
+    using St = AsyncStage<P, R12, NT>;
+    return S * St::BYTES + (EPI >= EPI_DIAG ? St::SPIN_BYTES : 0) + (EPI == EPI_DWF ? 2 * St::SPIN_BYTES : 0);
+}
+
+template <int P, bool R12, bool DAG, int EPI, int NT, int S>
+__global__ void __launch_bounds__(NT) wilson_hop_async_kernel(const HopArgs a) {
+    using T = float;
+    using St = AsyncStage<P, R12, NT>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int t = threadIdx.x;
+    const int i = blockIdx.x * NT + t;
+    const Geom& g = a.g;
+    if (i >= g.Vh) return;  // no block barrier below: a finished thread may leave
+    const int yb = blockIdx.y;
+    const int p = a.parity0 + (a.nparity == 2 ? (yb & 1) : 0);
+    const int rhs = a.nparity == 2 ? (yb >> 1) : yb;
+    if (a.skip && a.skip[(EPI == EPI_DWF ? 0 : rhs) * a.skip_stride]) return;
+
+    const char* __restrict__ in = a.in[p] + (size_t)rhs * a.in_rhs;
+    int x[4];
+    cb_coords(g, i, p, x);
+    const int xh = x[0] >> 1;
+    int nf[4], nb[4];
+    bool sf[4], sb[4];
+    {
+        int xf = x[0] + 1, xb = x[0] - 1;
+        sf[0] = (xf == g.L[0]);
+        sb[0] = (xb < 0);
+        if (sf[0]) xf = 0;
+        if (sb[0]) xb = g.L[0] - 1;
+        nf[0] = i - xh + (xf >> 1);
+        nb[0] = i - xh + (xb >> 1);
+        int step = g.Lh0;
+#pragma unroll
+        for (int mu = 1; mu < 4; ++mu) {
+            const bool top = (x[mu] == g.L[mu] - 1), bot = (x[mu] == 0);
+            sf[mu] = top;
+            sb[mu] = bot;
+            nf[mu] = top ? i - (g.L[mu] - 1) * step : i + step;
+            nb[mu] = bot ? i + (g.L[mu] - 1) * step : i - step;
+            step *= g.L[mu];
+        }
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            sf[mu] = sf[mu] && (g.bc[mu] < 0);
+            sb[mu] = sb[mu] && (g.bc[mu] < 0);
+        }
+    }
+    const char* __restrict__ Lp = a.links + (size_t)(p * 4) * a.link_block;
+    const char* __restrict__ Lq = a.links + (size_t)((1 - p) * 4) * a.link_block;
+    unsigned char* extra = smem + S * St::BYTES;  // diagonal / 5th-dimension spinors
+
+    auto issue = [&](int D) {
+        unsigned char* stage = smem + (D % S) * St::BYTES;
+        const int mu = D >> 1;
+        const bool fwd = (D & 1) == 0;
+        async_spinor<P, R12, NT>(stage, in, g.Vh, fwd ? nf[mu] : nb[mu], t);
+        async_link<P, R12, NT>(stage, (fwd ? Lp : Lq) + (size_t)mu * a.link_block, g.Vh, fwd ? i : nb[mu], t);
+    };
+
+    // prologue: the diagonal / 5th-dimension inputs ride with direction 0
+    issue(0);
+    int s_up = 0, s_dn = 0;
+    T c_up = 0, c_dn = 0;
+    if constexpr (EPI >= EPI_DIAG) {
+        async_spinor<P, R12, NT>(extra, a.x[p] + (size_t)rhs * a.x_rhs, g.Vh, i, t);
+    }
+    if constexpr (EPI == EPI_DWF) {
+        const int Ls = a.Ls;
+        const int sl = rhs;
+        s_up = DAG ? (sl + 1 == Ls ? 0 : sl + 1) : (sl == 0 ? Ls - 1 : sl - 1);
+        s_dn = DAG ? (sl == 0 ? Ls - 1 : sl - 1) : (sl + 1 == Ls ? 0 : sl + 1);
+        const bool wrap_up = DAG ? (sl + 1 == Ls) : (sl == 0);
+        const bool wrap_dn = DAG ? (sl == 0) : (sl + 1 == Ls);
+        c_up = wrap_up ? (T)a.mf : (T)-1;
+        c_dn = wrap_dn ? (T)a.mf : (T)-1;
+        async_spinor<P, R12, NT>(extra + St::SPIN_BYTES, a.x[p] + (size_t)s_up * a.x_rhs, g.Vh, i, t);
+        async_spinor<P, R12, NT>(extra + 2 * St::SPIN_BYTES, a.x[p] + (size_t)s_dn * a.x_rhs, g.Vh, i, t);
+    }
+    __pipeline_commit();
+#pragma unroll
+    for (int D = 1; D < S - 1; ++D) {
+        issue(D);
+        __pipeline_commit();
+    }
+
+    constexpr int SF = DAG ? +1 : -1;
+    constexpr int SB = -SF;
+    constexpr bool NORM = Prec<P>::has_norm;
+    cplx<T> acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = {0.f, 0.f};
+
+#define LQ_ASYNC_DIR(D)                                                               \
+    {                                                                                 \
+        constexpr int MU = (D) >> 1;                                                  \
+        constexpr bool FWD = ((D)&1) == 0;                                            \
+        constexpr int SG = FWD ? SF : SB;                                             \
+        if constexpr ((D) + S - 1 < 8) issue((D) + S - 1);                            \
+        __pipeline_commit();                                                          \
+        __pipeline_wait_prior(S - 1);                                                 \
+        const unsigned char* stage = smem + ((D) % S) * St::BYTES;                    \
+        cplx<T> s[12], h[6], uh[6], u[9];                                             \
+        T nrm;                                                                        \
+        smem_spinor<P, R12, NT>(stage, t, s, nrm);                                    \
+        project<MU, SG>(s, h);                                                        \
+        smem_link<P, R12, NT>(stage, t, u);                                           \
+        const bool sgn = FWD ? sf[MU] : sb[MU];                                       \
+        if constexpr (NORM) {                                                         \
+            su3_mul<!FWD>(u, h, uh);                                                  \
+            reconstruct_fma<MU, SG>(acc, uh, sgn ? -nrm : nrm);                       \
+        } else {                                                                      \
+            if (sgn) {                                                                \
+                _Pragma("unroll") for (int k = 0; k < 6; ++k) h[k] = cneg(h[k]);      \
+            }                                                                         \
+            su3_mul<!FWD>(u, h, uh);                                                  \
+            reconstruct_add<MU, SG>(acc, uh);                                         \
+        }                                                                             \
+    }
+    LQ_ASYNC_DIR(0)
+    LQ_ASYNC_DIR(1)
+    LQ_ASYNC_DIR(2)
+    LQ_ASYNC_DIR(3)
+    LQ_ASYNC_DIR(4)
+    LQ_ASYNC_DIR(5)
+    LQ_ASYNC_DIR(6)
+    LQ_ASYNC_DIR(7)
+#undef LQ_ASYNC_DIR
+
+    const T ch = (T)a.c_hop;
+    cplx<T> o[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) o[k] = {ch * acc[k].re, ch * acc[k].im};
+    if constexpr (EPI >= EPI_DIAG) {
+        cplx<T> xs[12];
+        T nx;
+        smem_spinor<P, R12, NT>(extra, t, xs, nx);
+        const T cd = (T)a.c_diag * nx;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            o[k].re = fma(cd, xs[k].re, o[k].re);
+            o[k].im = fma(cd, xs[k].im, o[k].im);
+        }
+    }
+    if constexpr (EPI == EPI_DWF) {
+        cplx<T> su[12], sd[12];
+        T nu, nd;
+        smem_spinor<P, R12, NT>(extra + St::SPIN_BYTES, t, su, nu);
+        smem_spinor<P, R12, NT>(extra + 2 * St::SPIN_BYTES, t, sd, nd);
+        const T cu = c_up * nu, cdn = c_dn * nd;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            o[k].re = fma(cu, su[k].re, o[k].re);
+            o[k].im = fma(cu, su[k].im, o[k].im);
+            o[6 + k].re = fma(cdn, sd[6 + k].re, o[6 + k].re);
+            o[6 + k].im = fma(cdn, sd[6 + k].im, o[6 + k].im);
+        }
+    }
+    store_spinor<P, T>(a.out[p] + (size_t)rhs * a.out_rhs, g.Vh, i, o);
+}
+
+// launch configuration per storage precision: threads per block, stages
+template <int P>
+struct AsyncCfg {
+    static constexpr int NT = 128;
+    static constexpr int S = (P == LQ_F32) ? 3 : 4;
+};
+
+template <int P, bool R12, bool DAG, int EPI>
+cudaError_t launch_async_one(const HopArgs& a, cudaStream_t st) {
+    constexpr int NT = AsyncCfg<P>::NT, S = AsyncCfg<P>::S;
+    constexpr int smem = async_smem_bytes<P, R12, NT, EPI>(S);
+    auto kern = wilson_hop_async_kernel<P, R12, DAG, EPI, NT, S>;
+    static bool configured = false;  // attribute set once per process (per instantiation)
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    dim3 grid((a.g.Vh + NT - 1) / NT, a.nrhs * a.nparity);
+    kern<<<grid, NT, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_hop_async(const HopArgs& a, bool r12, bool dag, int epi, cudaStream_t st) {
+#define LQ_A_EPI(R, D)                                                 \
+    switch (epi) {                                                     \
+    case EPI_HOP: return launch_async_one<P, R, D, EPI_HOP>(a, st);    \
+    case EPI_DIAG: return launch_async_one<P, R, D, EPI_DIAG>(a, st);  \
+    default: return launch_async_one<P, R, D, EPI_DWF>(a, st);         \
+    }
+    if (r12) {
+        if (dag) { LQ_A_EPI(true, true) } else { LQ_A_EPI(true, false) }
+    } else {
+        if (dag) { LQ_A_EPI(false, true) } else { LQ_A_EPI(false, false) }
+    }
+#undef LQ_A_EPI
+}
+
+}  // namespace lq

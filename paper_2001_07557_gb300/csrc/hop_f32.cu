@@ -1,8 +1,10 @@
-// hop_f32.cu -- Wilson hop kernels with F32 storage (one translation unit per precision).
-#include "hop.cuh"
+// hop_f32.cu -- Wilson hop kernels with F32 storage (one translation unit per
+// precision): the shared-memory staged kernel of hop_async.cuh.
+#include "hop_async.cuh"
 
 namespace lq {
 cudaError_t launch_hop_f32(const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st) {
-    return launch_hop_prec<LQ_F32>(a, r12, dag, epi, block, st);
+    (void)block;
+    return launch_hop_async<LQ_F32>(a, r12, dag, epi, st);
 }
 }  // namespace lq

@@ -30,17 +30,25 @@ struct Geom {
     int Lh0;    // L0 / 2
     int Vh;     // sites per parity
     int bc[4];  // +1 / -1 boundary phase per direction
+    // exact division by Lh0, L1, L2: q = (n * m) >> 40 with m = floor(2^40 / d) + 1,
+    // exact for n * d < 2^40 (here n < 2^27 and d <= 2^13)
+    unsigned long long mLh0, mL1, mL2;
 };
+
+__host__ __device__ inline unsigned long long div_magic(int d) { return ((1ULL << 40) / (unsigned)d) + 1ULL; }
+
+__device__ __forceinline__ int fast_div(int n, unsigned long long m) {
+    return (int)(((unsigned long long)(unsigned)n * m) >> 40);
+}
 
 // Coordinates of the site with checkerboard index cb and parity p.
 __device__ __forceinline__ void cb_coords(const Geom& g, int cb, int p, int x[4]) {
-    int t = cb;
-    int xh = t % g.Lh0;
-    t /= g.Lh0;
-    x[1] = t % g.L[1];
-    t /= g.L[1];
-    x[2] = t % g.L[2];
-    x[3] = t / g.L[2];
+    const int t1 = fast_div(cb, g.mLh0);
+    const int xh = cb - t1 * g.Lh0;
+    const int t2 = fast_div(t1, g.mL1);
+    x[1] = t1 - t2 * g.L[1];
+    x[3] = fast_div(t2, g.mL2);
+    x[2] = t2 - x[3] * g.L[2];
     x[0] = 2 * xh + ((p + x[1] + x[2] + x[3]) & 1);
 }
 
@@ -171,6 +179,30 @@ __device__ __forceinline__ void load_spinor(const char* __restrict__ blk, int Vh
             s[4 * k + 1] = {b.x * nrm, b.y * nrm};
             s[4 * k + 2] = {c.x * nrm, c.y * nrm};
             s[4 * k + 3] = {d.x * nrm, d.y * nrm};
+        }
+    }
+}
+
+// As load_spinor, but FP16/BF16 values are returned unscaled with the site
+// norm in `nrm` (1 for FP32/FP64), so that the norm can ride on later FMAs.
+template <int P, typename T>
+__device__ __forceinline__ void load_spinor_raw(const char* __restrict__ blk, int Vh, int i, cplx<T> (&s)[12],
+                                                T& nrm) {
+    if constexpr (P == LQ_F64 || P == LQ_F32) {
+        load_spinor<P, T>(blk, Vh, i, s);
+        nrm = (T)1;
+    } else {
+        const uint4* q = reinterpret_cast<const uint4*>(blk);
+        nrm = __ldg(reinterpret_cast<const float*>(blk + (size_t)48 * Vh) + i);
+        std::integral_constant<int, P> tag;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint4 v = __ldg(q + (size_t)k * Vh + i);
+            float2 a = h2f(v.x, tag), b = h2f(v.y, tag), c = h2f(v.z, tag), d = h2f(v.w, tag);
+            s[4 * k + 0] = {a.x, a.y};
+            s[4 * k + 1] = {b.x, b.y};
+            s[4 * k + 2] = {c.x, c.y};
+            s[4 * k + 3] = {d.x, d.y};
         }
     }
 }
@@ -309,6 +341,137 @@ __device__ __forceinline__ void store_link(char* __restrict__ blk, int Vh, int i
     }
 }
 
+// ----------------------------------------------- raw (packed) neighbour data
+// The hop issues the loads of the next direction before it computes the
+// current one; holding the data in its packed storage form keeps that
+// prefetch cheap in registers (19 words per direction for FP16, 12-real).
+
+template <int P>
+struct RawSpinor;
+template <>
+struct RawSpinor<LQ_F64> {
+    double2 v[12];
+};
+template <>
+struct RawSpinor<LQ_F32> {
+    float4 v[6];
+};
+template <>
+struct RawSpinor<LQ_F16> {
+    uint4 v[3];
+    float n;
+};
+template <>
+struct RawSpinor<LQ_BF16> {
+    uint4 v[3];
+    float n;
+};
+
+template <int P>
+__device__ __forceinline__ void raw_load(RawSpinor<P>& r, const char* __restrict__ blk, int Vh, int i) {
+    if constexpr (P == LQ_F64) {
+        const double2* q = reinterpret_cast<const double2*>(blk);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) r.v[k] = __ldg(q + (size_t)k * Vh + i);
+    } else if constexpr (P == LQ_F32) {
+        const float4* q = reinterpret_cast<const float4*>(blk);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) r.v[k] = __ldg(q + (size_t)k * Vh + i);
+    } else {
+        const uint4* q = reinterpret_cast<const uint4*>(blk);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) r.v[k] = __ldg(q + (size_t)k * Vh + i);
+        r.n = __ldg(reinterpret_cast<const float*>(blk + (size_t)48 * Vh) + i);
+    }
+}
+
+// values (unscaled for FP16/BF16) and the site norm (1 for FP32/FP64)
+template <int P, typename T>
+__device__ __forceinline__ void raw_unpack(const RawSpinor<P>& r, cplx<T> (&s)[12], T& nrm) {
+    if constexpr (P == LQ_F64) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) s[k] = {(T)r.v[k].x, (T)r.v[k].y};
+        nrm = (T)1;
+    } else if constexpr (P == LQ_F32) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            s[2 * k] = {(T)r.v[k].x, (T)r.v[k].y};
+            s[2 * k + 1] = {(T)r.v[k].z, (T)r.v[k].w};
+        }
+        nrm = (T)1;
+    } else {
+        std::integral_constant<int, P> tag;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float2 a = h2f(r.v[k].x, tag), b = h2f(r.v[k].y, tag), c = h2f(r.v[k].z, tag), d = h2f(r.v[k].w, tag);
+            s[4 * k + 0] = {a.x, a.y};
+            s[4 * k + 1] = {b.x, b.y};
+            s[4 * k + 2] = {c.x, c.y};
+            s[4 * k + 3] = {d.x, d.y};
+        }
+        nrm = r.n;
+    }
+}
+
+template <int P, bool R12>
+struct RawLink {
+    // words of one link in its storage form
+    static constexpr int n64 = (P == LQ_F64) ? (R12 ? 6 : 9) : 0;
+    static constexpr int n32x4 = (P == LQ_F32 && R12) ? 3 : 0;
+    static constexpr int n32x2 = (P == LQ_F32 && !R12) ? 9 : 0;
+    static constexpr int n16x4 = (P >= LQ_F16 && R12) ? 3 : 0;
+    static constexpr int n16x2 = (P >= LQ_F16 && !R12) ? 9 : 0;
+    double2 d[n64 ? n64 : 1];
+    float4 f4[n32x4 ? n32x4 : 1];
+    float2 f2[n32x2 ? n32x2 : 1];
+    uint2 h4[n16x4 ? n16x4 : 1];
+    uint32_t h2[n16x2 ? n16x2 : 1];
+};
+
+template <int P, bool R12>
+__device__ __forceinline__ void raw_load(RawLink<P, R12>& r, const char* __restrict__ blk, int Vh, int i) {
+    using RL = RawLink<P, R12>;
+#pragma unroll
+    for (int k = 0; k < RL::n64; ++k) r.d[k] = __ldg(reinterpret_cast<const double2*>(blk) + (size_t)k * Vh + i);
+#pragma unroll
+    for (int k = 0; k < RL::n32x4; ++k) r.f4[k] = __ldg(reinterpret_cast<const float4*>(blk) + (size_t)k * Vh + i);
+#pragma unroll
+    for (int k = 0; k < RL::n32x2; ++k) r.f2[k] = __ldg(reinterpret_cast<const float2*>(blk) + (size_t)k * Vh + i);
+#pragma unroll
+    for (int k = 0; k < RL::n16x4; ++k) r.h4[k] = __ldg(reinterpret_cast<const uint2*>(blk) + (size_t)k * Vh + i);
+#pragma unroll
+    for (int k = 0; k < RL::n16x2; ++k) r.h2[k] = __ldg(reinterpret_cast<const uint32_t*>(blk) + (size_t)k * Vh + i);
+}
+
+template <int P, bool R12, typename T>
+__device__ __forceinline__ void raw_unpack(const RawLink<P, R12>& r, cplx<T> (&u)[9]) {
+    using RL = RawLink<P, R12>;
+#pragma unroll
+    for (int k = 0; k < RL::n64; ++k) u[k] = {(T)r.d[k].x, (T)r.d[k].y};
+#pragma unroll
+    for (int k = 0; k < RL::n32x4; ++k) {
+        u[2 * k] = {(T)r.f4[k].x, (T)r.f4[k].y};
+        u[2 * k + 1] = {(T)r.f4[k].z, (T)r.f4[k].w};
+    }
+#pragma unroll
+    for (int k = 0; k < RL::n32x2; ++k) u[k] = {(T)r.f2[k].x, (T)r.f2[k].y};
+    if constexpr (P >= LQ_F16) {
+        std::integral_constant<int, P> tag;
+#pragma unroll
+        for (int k = 0; k < RL::n16x4; ++k) {
+            float2 a = h2f(r.h4[k].x, tag), b = h2f(r.h4[k].y, tag);
+            u[2 * k] = {a.x, a.y};
+            u[2 * k + 1] = {b.x, b.y};
+        }
+#pragma unroll
+        for (int k = 0; k < RL::n16x2; ++k) {
+            float2 a = h2f(r.h2[k], tag);
+            u[k] = {a.x, a.y};
+        }
+    }
+    if constexpr (R12) reconstruct_row2(u);
+}
+
 // ----------------------------------------------------- spin projection
 // (1 + S gamma_mu) psi = [h; S A_mu^dag h], h = psi_up + S A_mu psi_dn.
 // h[c] = spin 0 colour c, h[3 + c] = spin 1 colour c.
@@ -354,6 +517,42 @@ __device__ __forceinline__ void reconstruct_add(cplx<T> (&acc)[12], const cplx<T
         } else {
             acc[6 + c] = cadds<S>(acc[6 + c], a);
             acc[9 + c] = cadds<S>(acc[9 + c], b);
+        }
+    }
+}
+
+// acc += n [uh; S A_mu^dag uh] with a run-time scale n (site norm x boundary phase):
+// every term is one FMA, so the scale costs nothing over reconstruct_add.
+template <typename T>
+__device__ __forceinline__ void cfma(cplx<T>& acc, T n, cplx<T> b) {
+    acc.re = fma(n, b.re, acc.re);
+    acc.im = fma(n, b.im, acc.im);
+}
+template <typename T>
+__device__ __forceinline__ void cfma_i(cplx<T>& acc, T n, cplx<T> b) {  // acc += n * i b
+    acc.re = fma(-n, b.im, acc.re);
+    acc.im = fma(n, b.re, acc.im);
+}
+template <int MU, int S, typename T>
+__device__ __forceinline__ void reconstruct_fma(cplx<T> (&acc)[12], const cplx<T> (&uh)[6], T n) {
+    const T sn = S > 0 ? n : -n;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const cplx<T> a = uh[c], b = uh[3 + c];
+        cfma(acc[c], n, a);
+        cfma(acc[3 + c], n, b);
+        if constexpr (MU == 0) {
+            cfma_i(acc[6 + c], sn, b);
+            cfma_i(acc[9 + c], sn, a);
+        } else if constexpr (MU == 1) {
+            cfma(acc[6 + c], sn, b);
+            cfma(acc[9 + c], -sn, a);
+        } else if constexpr (MU == 2) {
+            cfma_i(acc[6 + c], sn, a);
+            cfma_i(acc[9 + c], -sn, b);
+        } else {
+            cfma(acc[6 + c], sn, a);
+            cfma(acc[9 + c], sn, b);
         }
     }
 }
