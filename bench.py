@@ -304,10 +304,13 @@ def main():
     }
 
     if rank == 0 and not args.no_extras:
+        lqcd.lq_destroy(h)
+        h = lqcd.lq_create(prm, torch.from_numpy(U).cuda(), lqcd.LQ_F64)
         line["cg"] = cg_compare(h, lqcd, torch, psi_e, prec)
         line["e2e"] = e2e(h, lqcd, torch, dims, psi_e, prec, args, world)
         line["per_precision"] = precision_table(h, lqcd, torch, psi_e, Vh, args, U, dims, mass)
         line["cpu_baseline"] = cpu_baseline(dims, mass, U, psi_e, Vh)
+        line["configs"] = other_configs(lqcd, torch)
     lqcd.lq_destroy(h)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -410,6 +413,120 @@ def cg_compare(h, lqcd, torch, psi_e, prec):
             out[name]["rel_diff_vs_fp64"] = float((x - x64).norm() / x64.norm())
     out["inner_precision"] = {0: "f64", 1: "f32", 2: "f16", 3: "bf16"}[inner]
     out["speedup"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    return out
+
+
+def _time(fn, st, reps, torch):
+    for _ in range(3):
+        fn()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        fn()
+    e1.record(st)
+    st.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def other_configs(lqcd, torch):
+    """The other workloads of the method, one short measurement each."""
+    from paper_2001_07557_gb300 import inputs
+
+    hbm, _ = peaks()
+    out = {}
+    st = torch.cuda.Stream()
+
+    # 4^4, random SU(3), m = 0.1: FP64 CG on D^dag D to 1e-12 (latency bound)
+    dims = (4, 4, 4, 4)
+    U = inputs.gauge_field(dims, "random", seed=1000)
+    h = lqcd.lq_create(lqcd.make_params(dims, mass=0.1), torch.from_numpy(U).cuda())
+    eta = torch.from_numpy(inputs.gaussian_spinor(256, seed=2000)).cuda()
+    b = torch.empty_like(eta)
+    lqcd.dslash_dag_apply(h, b, eta, lqcd.LQ_F64, lqcd.LQ_FULL)
+    x = torch.zeros_like(b)
+    cp = lqcd.make_cg_params(lqcd.LQ_OP_WILSON_NORMAL, lqcd.LQ_CG_PLAIN, lqcd.LQ_F64, tol=1e-12)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, stt = lqcd.cg_solve(h, x, b, cp, check=False)
+    out["c1_4x4_fp64_cg"] = {"status": rc, "seconds": time.perf_counter() - t0, "iters": stt[0].iters,
+                             "true_rel_residual": stt[0].true_rel_residual}
+    lqcd.lq_destroy(h)
+
+    # 16^3x32 even-odd, smooth links, m = 0.05: FP64 and FP32 hops; FP64 and mixed CG to 1e-10
+    dims = (16, 16, 16, 32)
+    V = int(np.prod(dims))
+    U = inputs.gauge_field(dims, "smooth", seed=1001)
+    h = lqcd.lq_create(lqcd.make_params(dims, mass=0.05), torch.from_numpy(U).cuda())
+    src = inputs.gaussian_spinor(V // 2, seed=2001)
+    res = {}
+    for pname, p in (("f64", 0), ("f32", 1)):
+        nat = lqcd.LQ_NATIVE | p
+        nb = lqcd.lq_field_bytes(h, nat, lqcd.LQ_EVEN, 1)
+        a_, b_ = (torch.empty(nb, dtype=torch.uint8, device="cuda") for _ in range(2))
+        lqcd.lq_convert(h, a_, nat, torch.from_numpy(src).cuda(), lqcd.LQ_F64, lqcd.LQ_ODD, stream=st)
+        ms = _time(lambda: lqcd.dslash_apply(h, b_, a_, nat, lqcd.LQ_EVEN, stream=st), st, 50, torch)
+        gbs = (V // 2) * algorithmic_bytes_per_site(p, False, False) / (ms * 1e-3) / 1e9
+        res[f"{pname}_eo_hop"] = {"gflops": FLOP_PER_SITE * (V // 2) / (ms * 1e-3) / 1e9, "ms": ms, "model_gbs": gbs,
+                                  "frac_hbm": gbs / hbm, "note": "working set fits in L2"}
+    bd = torch.from_numpy(src).cuda()
+    for name, mode in (("fp64_cg", lqcd.LQ_CG_PLAIN), ("mixed_cg_f16", lqcd.LQ_CG_MIXED)):
+        x = torch.zeros_like(bd)
+        cp = lqcd.make_cg_params(lqcd.LQ_OP_WILSON_EO_NORMAL, mode, lqcd.LQ_F64, tol=1e-10, inner=lqcd.LQ_F16)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, stt = lqcd.cg_solve(h, x, bd, cp, check=False)
+        res[name] = {"status": rc, "seconds": time.perf_counter() - t0, "iters": stt[0].iters,
+                     "true_rel_residual": stt[0].true_rel_residual}
+    out["c2_16x3x32_eo"] = res
+    lqcd.lq_destroy(h)
+
+    # 24^3x48, m = 0.02, 12 point sources: multi-RHS full-lattice hop (FP32) and solves
+    dims = (24, 24, 24, 48)
+    V = int(np.prod(dims))
+    U = inputs.gauge_field(dims, "smooth", seed=1003)
+    res = {}
+    for r12 in (False, True):
+        h = lqcd.lq_create(lqcd.make_params(dims, mass=0.02, compress12=r12), torch.from_numpy(U).cuda())
+        nat = lqcd.LQ_NATIVE | lqcd.LQ_F32
+        pts = torch.from_numpy(inputs.point_sources(V).astype(np.complex64)).cuda()
+        nb = lqcd.lq_field_bytes(h, nat, lqcd.LQ_FULL, 12)
+        a_, b_ = (torch.empty(nb, dtype=torch.uint8, device="cuda") for _ in range(2))
+        lqcd.lq_convert(h, a_, nat, pts, lqcd.LQ_F32, lqcd.LQ_FULL, 12, stream=st)
+        del pts
+        ms = _time(lambda: lqcd.dslash_apply(h, b_, a_, nat, lqcd.LQ_FULL, nrhs=12, stream=st), st, 10, torch)
+        link = 4 * (48 if r12 else 72)
+        byts = V * (link + 12 * 2 * 96)
+        res[f"hop_f32_12rhs_r{12 if r12 else 18}"] = {
+            "gflops": FLOP_PER_SITE * V * 12 / (ms * 1e-3) / 1e9, "ms": ms,
+            "model_gbs": byts / (ms * 1e-3) / 1e9, "frac_hbm": byts / (ms * 1e-3) / 1e9 / hbm,
+            "bytes_model": "links once per site (4 x link) + 12 x (in + out)"}
+        lqcd.lq_destroy(h)
+        del a_, b_
+    out["c4_24x3x48_multi_rhs"] = res
+
+    # 16^4 x Ls=16 domain wall, FP32
+    dims = (16, 16, 16, 16)
+    Ls = 16
+    V = int(np.prod(dims))
+    U = inputs.gauge_field(dims, "smooth", seed=1004)
+    res = {}
+    for pname, p in (("f32", 1), ("f16", 2)):
+        h = lqcd.lq_create(lqcd.make_params(dims, Ls=Ls, M5=1.8, mf=0.01, compress12=True),
+                           torch.from_numpy(U).cuda())
+        nat = lqcd.LQ_NATIVE | p
+        nb = lqcd.lq_field_bytes(h, nat, five_d=True)
+        a_, b_ = (torch.empty(nb, dtype=torch.uint8, device="cuda") for _ in range(2))
+        lqcd.lq_convert(h, a_, nat, torch.from_numpy(inputs.gaussian_spinor(V, seed=2004, nrhs=Ls)).cuda(),
+                        lqcd.LQ_F64, five_d=True, stream=st)
+        ms = _time(lambda: lqcd.dwf_dslash_apply(h, b_, a_, nat, False, stream=st), st, 20, torch)
+        sp = {1: 96, 2: 52}[p]
+        byts = V * (4 * {1: 48, 2: 24}[p] + Ls * 2 * sp)  # minimum: links once per 4-d site, 5-d in once, out once
+        res[f"dwf_{pname}_r12"] = {"gflops_4d": FLOP_PER_SITE * V * Ls / (ms * 1e-3) / 1e9, "ms": ms,
+                                   "model_gbs": byts / (ms * 1e-3) / 1e9,
+                                   "frac_hbm": byts / (ms * 1e-3) / 1e9 / hbm,
+                                   "extra_5d_flop_per_site": 96}
+        lqcd.lq_destroy(h)
+    out["c5_16x4xLs16_dwf"] = res
     return out
 
 

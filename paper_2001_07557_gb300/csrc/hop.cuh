@@ -19,12 +19,14 @@ namespace lq {
 template <int P, bool R12, bool DAG, int EPI>
 __global__ void __launch_bounds__(128) wilson_hop_kernel(const HopArgs a) {
     using T = typename Prec<P>::real;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    // grid.x = site block x rhs (rhs fastest: the right-hand sides, or 5th-dimension
+    // slices, of one site tile run together and share each link through L2/L1);
+    // grid.y = output parity
+    const int rhs = blockIdx.x % a.nrhs;
+    const int i = (blockIdx.x / a.nrhs) * blockDim.x + threadIdx.x;
     const Geom& g = a.g;
     if (i >= g.Vh) return;
-    const int yb = blockIdx.y;
-    const int p = a.parity0 + (a.nparity == 2 ? (yb & 1) : 0);
-    const int rhs = a.nparity == 2 ? (yb >> 1) : yb;
+    const int p = a.parity0 + blockIdx.y;
     if (a.skip && a.skip[(EPI == EPI_DWF ? 0 : rhs) * a.skip_stride]) return;
 
     const char* __restrict__ in = a.in[p] + (size_t)rhs * a.in_rhs;
@@ -161,7 +163,7 @@ __global__ void __launch_bounds__(128) wilson_hop_kernel(const HopArgs a) {
 
 template <int P>
 cudaError_t launch_hop_prec(const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st) {
-    dim3 grid((a.g.Vh + block - 1) / block, a.nrhs * a.nparity);
+    dim3 grid(((a.g.Vh + block - 1) / block) * a.nrhs, a.nparity);
     dim3 blk(block);
 #define LQ_LAUNCH(R, D, E) wilson_hop_kernel<P, R, D, E><<<grid, blk, 0, st>>>(a)
 #define LQ_EPI(R, D)                       \

@@ -147,13 +147,15 @@ __global__ void __launch_bounds__(NT) wilson_hop_async_kernel(const HopArgs a) {
     using T = float;
     using St = AsyncStage<P, R12, NT>;
     extern __shared__ __align__(16) unsigned char smem[];
+    // grid.x = site block x rhs (rhs fastest: the right-hand sides, or 5th-dimension
+    // slices, of one site tile run together and share each link through L2/L1);
+    // grid.y = output parity
     const int t = threadIdx.x;
-    const int i = blockIdx.x * NT + t;
+    const int rhs = blockIdx.x % a.nrhs;
+    const int i = (blockIdx.x / a.nrhs) * NT + t;
     const Geom& g = a.g;
     if (i >= g.Vh) return;  // no block barrier below: a finished thread may leave
-    const int yb = blockIdx.y;
-    const int p = a.parity0 + (a.nparity == 2 ? (yb & 1) : 0);
-    const int rhs = a.nparity == 2 ? (yb >> 1) : yb;
+    const int p = a.parity0 + blockIdx.y;
     if (a.skip && a.skip[(EPI == EPI_DWF ? 0 : rhs) * a.skip_stride]) return;
 
     const char* __restrict__ in = a.in[p] + (size_t)rhs * a.in_rhs;
@@ -317,7 +319,7 @@ cudaError_t launch_async_one(const HopArgs& a, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    dim3 grid((a.g.Vh + NT - 1) / NT, a.nrhs * a.nparity);
+    dim3 grid(((a.g.Vh + NT - 1) / NT) * a.nrhs, a.nparity);
     kern<<<grid, NT, smem, st>>>(a);
     return cudaGetLastError();
 }
