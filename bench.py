@@ -502,6 +502,27 @@ def other_configs(lqcd, torch):
             "bytes_model": "links once per site (4 x link) + 12 x (in + out)"}
         lqcd.lq_destroy(h)
         del a_, b_
+    # solves to 1e-10 on D^dag D x = D^dag (point source): one FP64 CG, 12 FP64 CGs in one batch,
+    # 12 mixed CGs in one batch (FP16 inner), and block CG over the 12 (FP32 inner)
+    h = lqcd.lq_create(lqcd.make_params(dims, mass=0.02, compress12=True), torch.from_numpy(U).cuda())
+    pts = torch.from_numpy(inputs.point_sources(V)).cuda()
+    b = torch.empty_like(pts)
+    lqcd.dslash_dag_apply(h, b, pts, lqcd.LQ_F64, lqcd.LQ_FULL, nrhs=12)
+    del pts
+    runs = [("fp64_cg_1rhs", lqcd.LQ_CG_PLAIN, 1, lqcd.LQ_F32), ("fp64_cg_12rhs_batched", lqcd.LQ_CG_PLAIN, 12, lqcd.LQ_F32),
+            ("mixed_cg_12rhs_batched_f16", lqcd.LQ_CG_MIXED, 12, lqcd.LQ_F16),
+            ("block_cg_12rhs_f32", lqcd.LQ_CG_BLOCK, 12, lqcd.LQ_F32)]
+    for name, mode, n, inner in runs:
+        x = torch.zeros_like(b[:n])
+        cp = lqcd.make_cg_params(lqcd.LQ_OP_WILSON_NORMAL, mode, lqcd.LQ_F64, nrhs=n, tol=1e-10, inner=inner)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, stt = lqcd.cg_solve(h, x, b[:n].contiguous(), cp, check=False)
+        res[name] = {"status": rc, "seconds": time.perf_counter() - t0, "max_iters": max(z.iters for z in stt),
+                     "max_true_rel_residual": max(z.true_rel_residual for z in stt)}
+        del x
+    lqcd.lq_destroy(h)
+    res["note"] = "full-lattice D^dag D, m = 0.02, smooth links; b = D^dag (point source)"
     out["c4_24x3x48_multi_rhs"] = res
 
     # 16^4 x Ls=16 domain wall, FP32

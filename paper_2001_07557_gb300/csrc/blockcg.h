@@ -1,0 +1,32 @@
+// blockcg.h -- block CG inner solver (FP32 block vectors, FP64 N x N algebra).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+namespace lq {
+
+constexpr int kMaxBlockRhs = 16;
+
+// The operator the block CG iterates: out = A in for all N columns at once.
+struct BlockCgOps {
+    void* ctx;
+    int (*apply)(void* ctx, char* out, const char* in);
+};
+
+// Bytes of device scratch block_cg needs for N columns over nsites sites.
+inline size_t block_cg_scratch_bytes(int N) {
+    return sizeof(double2) * ((size_t)152 * 4 * N * N + (size_t)N * N) + sizeof(float2) * N * N + 256;
+}
+
+// Block CG on A X = B from X = 0 for N columns of FP32 native fields, each
+// `stride` bytes, nsites sites (parity blocks of Vh).  R, Pa, Pb, Q are
+// scratch fields of the same shape; ws: block_cg_scratch_bytes(N) device
+// bytes; hostbuf: N*N pinned double2.  Stops when every column's residual is
+// below tol times its start, when the block loses rank, or after maxiter.
+int block_cg(const BlockCgOps& ops, char* X, const char* B, char* R, char* Pa, char* Pb, char* Q, size_t stride,
+             long nsites, int Vh, int N, double tol, int maxiter, void* ws, double2* hostbuf, cudaStream_t s,
+             int* iters);
+
+}  // namespace lq

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "blas.h"
+#include "blockcg.h"
 #include "handle.h"
 
 namespace lq {
@@ -65,6 +66,20 @@ struct Ctl {
     CgScalars* host;
 };
 
+int ensure_pinned(lq_handle* h, size_t hb) {
+    if (h->pinned_bytes < hb) {
+        if (h->pinned) cudaFreeHost(h->pinned);
+        h->pinned = nullptr;
+        h->pinned_bytes = 0;
+        if (cudaMallocHost(&h->pinned, hb) != cudaSuccess) {
+            cudaGetLastError();
+            return LQ_ERR_NOMEM;
+        }
+        h->pinned_bytes = hb;
+    }
+    return LQ_OK;
+}
+
 int make_ctl(lq_handle* h, const OpGeom& og, Ctl* c, cudaStream_t s) {
     const size_t npart = reduce_scratch_doubles(h->g.Vh, og.nblk, og.nrhs);
     const size_t nb = sizeof(CgScalars) * og.nrhs + sizeof(double) * (2 * og.nrhs + npart) +
@@ -82,16 +97,7 @@ int make_ctl(lq_handle* h, const OpGeom& og, Ctl* c, cudaStream_t s) {
     c->sc.tickets = reinterpret_cast<unsigned*>(q);
     if (cudaMemsetAsync(c->sc.tickets, 0, sizeof(unsigned) * og.nrhs, s) != cudaSuccess) return LQ_ERR_CUDA;
     const size_t hb = sizeof(CgScalars) * og.nrhs + sizeof(double) * 2 * og.nrhs;
-    if (h->pinned_bytes < hb) {
-        if (h->pinned) cudaFreeHost(h->pinned);
-        h->pinned = nullptr;
-        h->pinned_bytes = 0;
-        if (cudaMallocHost(&h->pinned, hb) != cudaSuccess) {
-            cudaGetLastError();
-            return LQ_ERR_NOMEM;
-        }
-        h->pinned_bytes = hb;
-    }
+    if ((rc = ensure_pinned(h, hb))) return rc;
     c->host = static_cast<CgScalars*>(h->pinned);
     return LQ_OK;
 }
@@ -206,6 +212,19 @@ int true_residual(lq_handle* h, const OpGeom& og, const Ctl& c, const VecRef& x6
     return LQ_OK;
 }
 
+struct BlockCtx {
+    lq_handle* h;
+    const OpGeom* og;
+    char* t;
+    char* tmp;
+    cudaStream_t s;
+};
+
+int block_apply(void* ctx, char* out, const char* in) {
+    BlockCtx* c = static_cast<BlockCtx*>(ctx);
+    return apply_normal(c->h, *c->og, LQ_F32, out, in, c->t, c->tmp, c->s);
+}
+
 double default_inner_tol(int prec) {
     switch (prec) {
     case LQ_F32: return 1e-6;
@@ -243,8 +262,9 @@ extern "C" int cg_solve(lq_handle* h, void* x, const void* b, const lq_cg_params
     default: return LQ_ERR_ARG;
     }
     const int mode = cp->mode == LQ_CG_BATCHED ? LQ_CG_MIXED : cp->mode;
-    if (mode != LQ_CG_PLAIN && mode != LQ_CG_MIXED) return LQ_ERR_ARG;
+    if (mode != LQ_CG_PLAIN && mode != LQ_CG_MIXED && mode != LQ_CG_BLOCK) return LQ_ERR_ARG;
     if (mode == LQ_CG_MIXED && (cp->inner < LQ_F32 || cp->inner > LQ_BF16)) return LQ_ERR_ARG;
+    if (mode == LQ_CG_BLOCK && (cp->nrhs > kMaxBlockRhs || cp->op == LQ_OP_DWF_NORMAL)) return LQ_ERR_ARG;
     const int nf = cp->op == LQ_OP_DWF_NORMAL ? h->p.Ls : cp->nrhs;  // fields in the user's buffers
     const size_t ub = field_bytes(h, cp->fmt, subset, nf);
     if (overlap(x, ub, b, ub)) return LQ_ERR_ARG;
@@ -331,9 +351,29 @@ extern "C" int cg_solve(lq_handle* h, void* x, const void* b, const lq_cg_params
             if ((rc = true_residual(h, og, c, X64, B64, WS_CG0 + 5, rel.data(), s))) return rc;
         }
     } else {
-        // FP64 defect correction around a low-precision inner CG
-        const int ip = cp->inner;
-        const double itol = cp->inner_tol > 0 ? cp->inner_tol : default_inner_tol(ip);
+        // FP64 defect correction around a low-precision inner CG (independent
+        // per right-hand side, or one block CG over all of them)
+        const bool block = mode == LQ_CG_BLOCK;
+        const int ip = block ? LQ_F32 : cp->inner;
+        const double itol = cp->inner_tol > 0 ? cp->inner_tol : (block ? 1e-5 : default_inner_tol(ip));
+        BlockCtx bctx{h, &og, nullptr, nullptr, s};
+        void *bws = nullptr, *bR = nullptr, *bPa = nullptr, *bPb = nullptr, *bQ = nullptr;
+        if (block) {
+            void *bt, *btmp;
+            if ((rc = ensure_ws(h, WS_CG0 + 0, og.bytes(h, LQ_F32), &bR)) ||
+                (rc = ensure_ws(h, WS_CG0 + 1, og.bytes(h, LQ_F32), &bPa)) ||
+                (rc = ensure_ws(h, WS_CG0 + 2, og.bytes(h, LQ_F32), &bPb)) ||
+                (rc = ensure_ws(h, WS_CG0 + 3, og.bytes(h, LQ_F32), &bQ)) ||
+                (rc = ensure_ws(h, WS_CG0 + 4, og.bytes(h, LQ_F32), &bt)) ||
+                (rc = ensure_ws(h, 17, block_cg_scratch_bytes(og.nrhs), &bws)) ||
+                (rc = ensure_ws(h, 16, (size_t)spinor_site_bytes(LQ_F32) * h->g.Vh * og.nrhs, &btmp)))
+                return rc;
+            bctx.t = static_cast<char*>(bt);
+            bctx.tmp = static_cast<char*>(btmp);
+            const char* L;
+            size_t lb;
+            if ((rc = get_links(h, LQ_F32, &L, &lb, s))) return rc;
+        }
         void *r64p, *ep, *rinp;
         if ((rc = ensure_ws(h, WS_CG0 + 10, og.bytes(h, LQ_F64), &r64p)) ||
             (rc = ensure_ws(h, WS_CG0 + 11, og.bytes(h, LQ_F32), &ep)) ||
@@ -392,12 +432,28 @@ extern "C" int cg_solve(lq_handle* h, void* x, const void* b, const lq_cg_params
             for (int k = 0; k < og.nrhs; ++k)
                 if (conv[k] && cudaMemsetAsync(RIN.ptr + k * RIN.rhs_stride, 0, RIN.rhs_stride, s) != cudaSuccess)
                     return LQ_ERR_CUDA;
-            if ((rc = run_cg(h, og, c, ip, E, RIN, itol, cp->maxiter - total_inner, WS_CG0, s))) return rc;
             int most = 0;
-            for (int k = 0; k < og.nrhs; ++k) {
-                iters[k] += c.host[k].iter;
-                most = std::max(most, c.host[k].iter);
-                if (!conv[k]) outer[k] += 1;
+            if (block) {
+                if ((rc = ensure_pinned(h, sizeof(double2) * og.nrhs * og.nrhs + 64))) return rc;
+                BlockCgOps ops{&bctx, block_apply};
+                int bit = 0;
+                rc = block_cg(ops, E.ptr, RIN.ptr, static_cast<char*>(bR), static_cast<char*>(bPa),
+                              static_cast<char*>(bPb), static_cast<char*>(bQ), E.rhs_stride,
+                              (long)og.nblk * h->g.Vh, h->g.Vh, og.nrhs, itol, cp->maxiter - total_inner, bws,
+                              static_cast<double2*>(h->pinned), s, &bit);
+                if (rc) return rc;
+                for (int k = 0; k < og.nrhs; ++k) {
+                    iters[k] += conv[k] ? 0 : bit;
+                    if (!conv[k]) outer[k] += 1;
+                }
+                most = bit;
+            } else {
+                if ((rc = run_cg(h, og, c, ip, E, RIN, itol, cp->maxiter - total_inner, WS_CG0, s))) return rc;
+                for (int k = 0; k < og.nrhs; ++k) {
+                    iters[k] += c.host[k].iter;
+                    most = std::max(most, c.host[k].iter);
+                    if (!conv[k]) outer[k] += 1;
+                }
             }
             total_inner += std::max(most, 1);
             if (launch_axpby(X, E, 1.0, 1.0, h->g.Vh, og.nblk, og.nrhs, s) != cudaSuccess) return LQ_ERR_CUDA;
