@@ -67,36 +67,91 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """SM clock and throttle reasons sampled every ~2 ms during the timed region
+    through NVML (libnvidia-ml, read-only queries); nvidia-smi at 200 ms if
+    NVML cannot be loaded."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, index):
-        self.index = index
+    def __init__(self, cuda_index):
+        self.cuda_index = cuda_index
+        self.samples = []
+        self.max_mhz = None
+        self.stop = threading.Event()
+        self.nvml = None
         self.proc = None
         self.lines = []
 
-    def __enter__(self):
-        try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
-        except Exception:
-            self.proc = None
-        time.sleep(0.3)
-        return self
+    def _nvml_handle(self):
+        import ctypes
 
-    def _read(self):
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        handle = ctypes.c_void_p()
+        ok = False
+        try:
+            import torch
+
+            uuid = str(torch.cuda.get_device_properties(self.cuda_index).uuid)
+            u = ("GPU-" + uuid).encode()
+            ok = lib.nvmlDeviceGetHandleByUUID(ctypes.c_char_p(u), ctypes.byref(handle)) == 0
+        except Exception:
+            ok = False
+        if not ok and lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.cuda_index), ctypes.byref(handle)) != 0:
+            raise RuntimeError("no NVML handle")
+        mx = ctypes.c_uint(0)
+        if lib.nvmlDeviceGetMaxClockInfo(handle, ctypes.c_int(1), ctypes.byref(mx)) == 0:
+            self.max_mhz = float(mx.value)
+        return lib, handle
+
+    def _poll_nvml(self):
+        import ctypes
+
+        lib, handle = self.nvml
+        clk = ctypes.c_uint(0)
+        mask = ctypes.c_ulonglong(0)
+        reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self.stop.is_set():
+            if lib.nvmlDeviceGetClockInfo(handle, ctypes.c_int(1), ctypes.byref(clk)) == 0:
+                r = reasons_fn(handle, ctypes.byref(mask))
+                self.samples.append((float(clk.value), int(mask.value) if r == 0 else 0))
+            time.sleep(0.002)
+
+    def _read_smi(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def __enter__(self):
+        try:
+            self.nvml = self._nvml_handle()
+            self.t = threading.Thread(target=self._poll_nvml, daemon=True)
+            self.t.start()
+            time.sleep(0.01)
+        except Exception:
+            self.nvml = None
+            try:
+                self.proc = subprocess.Popen(
+                    ["nvidia-smi", "-i", str(self.cuda_index), "--query-gpu=clocks.sm,clocks.max.sm,"
+                     "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                     "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                     "--format=csv,noheader,nounits", "-lms", "200"],
+                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                self.t = threading.Thread(target=self._read_smi, daemon=True)
+                self.t.start()
+                time.sleep(0.3)
+            except Exception:
+                self.proc = None
+        return self
+
     def __exit__(self, *a):
-        time.sleep(0.3)
+        if self.nvml:
+            self.stop.set()
+            self.t.join(timeout=1)
         if self.proc:
+            time.sleep(0.3)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -104,24 +159,32 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx = float(f[2])
-            except ValueError:
-                continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
+        reasons = set()
+        if self.nvml:
+            sm = [c for c, _ in self.samples]
+            for _, m in self.samples:
+                for bit, name in self.REASONS.items():
+                    if m & bit:
+                        reasons.add(name)
+            src = "nvml"
+        else:
+            sm = []
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for line in self.lines:
+                f = [x.strip() for x in line.split(",")]
+                try:
+                    sm.append(float(f[0]))
+                    self.max_mhz = float(f[1])
+                except (ValueError, IndexError):
+                    continue
+                for n, v in zip(names, f[2:6]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+            src = "nvidia-smi"
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unsampled"], "source": src}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": self.max_mhz, "reasons": sorted(reasons),
+                "samples": len(sm), "source": src}
 
 
 def algorithmic_bytes_per_site(prec, r12, diag):
@@ -547,6 +610,30 @@ def other_configs(lqcd, torch):
                                    "frac_hbm": byts / (ms * 1e-3) / 1e9 / hbm,
                                    "extra_5d_flop_per_site": 96}
         lqcd.lq_destroy(h)
+    # CG on D_dw^dag D_dw: FP32 alone to 1e-8, and FP64 refinement around FP32 inner solves to 1e-10
+    h = lqcd.lq_create(lqcd.make_params(dims, Ls=Ls, M5=1.8, mf=0.01, compress12=True), torch.from_numpy(U).cuda())
+    eta = torch.from_numpy(inputs.gaussian_spinor(V, seed=2004, nrhs=Ls)).cuda()
+    b = torch.empty_like(eta)
+    lqcd.dwf_dslash_apply(h, b, eta, lqcd.LQ_F64, True)
+    del eta
+    b32 = b.to(torch.complex64)
+    x32 = torch.zeros_like(b32)
+    cp = lqcd.make_cg_params(lqcd.LQ_OP_DWF_NORMAL, lqcd.LQ_CG_PLAIN, lqcd.LQ_F32, tol=1e-8, maxiter=20000)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, stt = lqcd.cg_solve(h, x32, b32, cp, check=False)
+    res["fp32_cg_1e-8"] = {"status": rc, "seconds": time.perf_counter() - t0, "iters": stt[0].iters,
+                           "true_rel_residual_fp64": stt[0].true_rel_residual}
+    x = torch.zeros_like(b)
+    cp = lqcd.make_cg_params(lqcd.LQ_OP_DWF_NORMAL, lqcd.LQ_CG_MIXED, lqcd.LQ_F64, tol=1e-10, maxiter=40000,
+                             inner=lqcd.LQ_F32, inner_tol=1e-6)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, stt = lqcd.cg_solve(h, x, b, cp, check=False)
+    res["fp64_refined_fp32_inner_1e-10"] = {"status": rc, "seconds": time.perf_counter() - t0,
+                                            "iters": stt[0].iters, "outer": stt[0].outer_iters,
+                                            "true_rel_residual": stt[0].true_rel_residual}
+    lqcd.lq_destroy(h)
     out["c5_16x4xLs16_dwf"] = res
     return out
 

@@ -54,6 +54,13 @@ int get_links(lq_handle* h, int prec, const char** links, size_t* link_block, cu
     return LQ_OK;
 }
 
+// the fused output norm applies to operator outputs (diagonal / domain-wall epilogues) only
+static void set_red(HopArgs& a, const lq_handle* h) {
+    a.red_partial = h->red_partial;
+    a.red_ticket = h->red_ticket;
+    a.red_st = h->red_st;
+}
+
 static HopArgs base_args(lq_handle* h, const char* links, size_t lb) {
     HopArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -83,6 +90,7 @@ int native_wilson_full(lq_handle* h, int prec, char* out, const char* in, int nr
     a.nrhs = nrhs;
     a.c_hop = -0.5;
     a.c_diag = h->p.mass + 4.0;
+    set_red(a, h);
     return status_of(launch_hop(prec, a, h->p.compress12 != 0, dag, EPI_DIAG, h->hop_block[prec], st));
 }
 
@@ -125,6 +133,7 @@ int native_wilson_schur(lq_handle* h, int prec, char* out, const char* in, char*
     a.nrhs = nrhs;
     a.c_hop = -1.0 / (4.0 * am);
     a.c_diag = am;
+    set_red(a, h);
     return status_of(launch_hop(prec, a, h->p.compress12 != 0, dag, EPI_DIAG, h->hop_block[prec], st));
 }
 
@@ -148,6 +157,7 @@ int native_dwf(lq_handle* h, int prec, char* out, const char* in, bool dag, cuda
     a.mf = h->p.mf;
     a.c_hop = -0.5;
     a.c_diag = 5.0 - h->p.M5;
+    set_red(a, h);
     return status_of(launch_hop(prec, a, h->p.compress12 != 0, dag, EPI_DWF, h->hop_block[prec], st));
 }
 
@@ -232,7 +242,7 @@ int lq_create(lq_handle** hp, const lq_params* p, const void* U, int U_prec, voi
     h->g.mLh0 = div_magic(h->g.Lh0);
     h->g.mL1 = div_magic(p->dims[1]);
     h->g.mL2 = div_magic(p->dims[2]);
-    for (int k = 0; k < 4; ++k) h->hop_block[k] = 128;
+    for (int k = 0; k < 4; ++k) h->hop_block[k] = kHopThreads;
     if (cudaGetDevice(&h->device) != cudaSuccess) {
         delete h;
         return LQ_ERR_CUDA;

@@ -327,6 +327,31 @@ __global__ void __launch_bounds__(kThreads) cdot_kernel(const char* a, const cha
     }
 }
 
+__global__ void hop_norm_finalize_kernel(const double* partial, int nwarps, CgScalars* st) {
+    const int g = blockIdx.x;
+    CgScalars& s = st[g];
+    if (s.done) return;
+    double t = 0;
+    for (int w = threadIdx.x; w < nwarps; w += blockDim.x) t += partial[(size_t)g * nwarps + w];
+    __shared__ double ws[kThreads / 32];
+    t = warp_sum(t);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) ws[wid] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += ws[k];
+        s.pAp = tot;
+        if (!(tot > 0.0) || !isfinite(tot)) {
+            s.done = 1;
+            s.status = LQ_ERR_BREAKDOWN;
+            s.alpha = 0;
+        } else {
+            s.alpha = s.rr / tot;
+        }
+    }
+}
+
 int grid_x(int Vh, int nblk) {
     static int sms = 0;
     if (!sms) {
@@ -350,6 +375,11 @@ int grid_x(int Vh, int nblk) {
     case LQ_F16: { constexpr int NAME = LQ_F16; BODY; } break;    \
     default: { constexpr int NAME = LQ_BF16; BODY; } break;       \
     }
+
+cudaError_t launch_hop_norm_finalize(const double* partial, int nwarps, int ngroups, CgScalars* st, cudaStream_t s) {
+    hop_norm_finalize_kernel<<<ngroups, kThreads, 0, s>>>(partial, nwarps, st);
+    return cudaGetLastError();
+}
 
 size_t reduce_scratch_doubles(int Vh, int nblk, int nrhs) { return (size_t)grid_x(Vh, nblk) * nrhs; }
 

@@ -18,20 +18,6 @@ struct VecRef {
     size_t rhs_stride;
 };
 
-// Device-resident CG scalars of one right-hand side.
-struct CgScalars {
-    double rr;     // |r|^2
-    double bb;     // |b|^2
-    double stop2;  // tol^2 |b|^2
-    double pAp;
-    double alpha;
-    double beta;
-    int iter;
-    int maxiter;
-    int done;      // converged, broke down, or out of iterations
-    int status;    // LQ_OK / LQ_ERR_BREAKDOWN / LQ_ERR_NOT_CONVERGED / LQ_ERR_NAN
-};
-
 struct Scratch {
     double* partial;    // reduce_scratch_doubles() entries
     unsigned* tickets;  // one per rhs, zero before the first launch (each launch leaves them zero)

@@ -40,23 +40,12 @@ struct OpGeom {
     VecRef ref(const lq_handle* h, void* p, int prec) const { return VecRef{static_cast<char*>(p), prec, stride(h, prec)}; }
 };
 
-// out = K^dag K in;  t: intermediate of in's size, tmp: odd half (even-odd only)
+// out = K^dag K in;  t: intermediate of in's size, tmp: odd half (even-odd only).
+// With c given, the launch that writes t = K in also sums |t|^2 = <in, K^dag K in>
+// per right-hand side and sets the CG step length alpha on the device.
+struct Ctl;
 int apply_normal(lq_handle* h, const OpGeom& og, int prec, char* out, const char* in, char* t, char* tmp,
-                 cudaStream_t st) {
-    int rc;
-    switch (og.op) {
-    case LQ_OP_WILSON_NORMAL:
-        if ((rc = native_wilson_full(h, prec, t, in, og.nrhs, false, st))) return rc;
-        return native_wilson_full(h, prec, out, t, og.nrhs, true, st);
-    case LQ_OP_WILSON_EO_NORMAL:
-        if ((rc = native_wilson_schur(h, prec, t, in, tmp, og.nrhs, false, st))) return rc;
-        return native_wilson_schur(h, prec, out, t, tmp, og.nrhs, true, st);
-    case LQ_OP_DWF_NORMAL:
-        if ((rc = native_dwf(h, prec, t, in, false, st))) return rc;
-        return native_dwf(h, prec, out, t, true, st);
-    }
-    return LQ_ERR_ARG;
-}
+                 cudaStream_t st, const Ctl* c = nullptr);
 
 // Solver scratch: scalars, norms, reduction partials, tickets (one workspace slot)
 struct Ctl {
@@ -64,6 +53,8 @@ struct Ctl {
     double* red;  // 2 * nrhs doubles
     Scratch sc;
     CgScalars* host;
+    double* hop_partial;  // fused |K p|^2 partials of the hop launches
+    unsigned* hop_tickets;
 };
 
 int ensure_pinned(lq_handle* h, size_t hb) {
@@ -82,8 +73,9 @@ int ensure_pinned(lq_handle* h, size_t hb) {
 
 int make_ctl(lq_handle* h, const OpGeom& og, Ctl* c, cudaStream_t s) {
     const size_t npart = reduce_scratch_doubles(h->g.Vh, og.nblk, og.nrhs);
-    const size_t nb = sizeof(CgScalars) * og.nrhs + sizeof(double) * (2 * og.nrhs + npart) +
-                      sizeof(unsigned) * og.nrhs + 256;
+    const size_t nhop = hop_red_warps(h->g.Vh, 2, std::max(h->p.Ls, 1)) * (size_t)og.nrhs;
+    const size_t nb = sizeof(CgScalars) * og.nrhs + sizeof(double) * (2 * og.nrhs + npart + nhop) +
+                      2 * sizeof(unsigned) * og.nrhs + 256;
     void* p;
     int rc = ensure_ws(h, WS_CTL, nb, &p);
     if (rc) return rc;
@@ -94,12 +86,49 @@ int make_ctl(lq_handle* h, const OpGeom& og, Ctl* c, cudaStream_t s) {
     q += sizeof(double) * 2 * og.nrhs;
     c->sc.partial = reinterpret_cast<double*>(q);
     q += sizeof(double) * npart;
+    c->hop_partial = reinterpret_cast<double*>(q);
+    q += sizeof(double) * nhop;
     c->sc.tickets = reinterpret_cast<unsigned*>(q);
-    if (cudaMemsetAsync(c->sc.tickets, 0, sizeof(unsigned) * og.nrhs, s) != cudaSuccess) return LQ_ERR_CUDA;
+    c->hop_tickets = c->sc.tickets + og.nrhs;
+    if (cudaMemsetAsync(c->sc.tickets, 0, 2 * sizeof(unsigned) * og.nrhs, s) != cudaSuccess) return LQ_ERR_CUDA;
     const size_t hb = sizeof(CgScalars) * og.nrhs + sizeof(double) * 2 * og.nrhs;
     if ((rc = ensure_pinned(h, hb))) return rc;
     c->host = static_cast<CgScalars*>(h->pinned);
     return LQ_OK;
+}
+
+int apply_normal(lq_handle* h, const OpGeom& og, int prec, char* out, const char* in, char* t, char* tmp,
+                 cudaStream_t st, const Ctl* c) {
+    int rc;
+    if (c) {
+        h->red_partial = c->hop_partial;
+        h->red_ticket = c->hop_tickets;
+        h->red_st = c->st;
+    }
+    switch (og.op) {
+    case LQ_OP_WILSON_NORMAL: rc = native_wilson_full(h, prec, t, in, og.nrhs, false, st); break;
+    case LQ_OP_WILSON_EO_NORMAL: rc = native_wilson_schur(h, prec, t, in, tmp, og.nrhs, false, st); break;
+    case LQ_OP_DWF_NORMAL: rc = native_dwf(h, prec, t, in, false, st); break;
+    default: rc = LQ_ERR_ARG;
+    }
+    h->red_partial = nullptr;
+    h->red_ticket = nullptr;
+    h->red_st = nullptr;
+    if (rc) return rc;
+    switch (og.op) {
+    case LQ_OP_WILSON_NORMAL: return native_wilson_full(h, prec, out, t, og.nrhs, true, st);
+    case LQ_OP_WILSON_EO_NORMAL: return native_wilson_schur(h, prec, out, t, tmp, og.nrhs, true, st);
+    default: return native_dwf(h, prec, out, t, true, st);
+    }
+}
+
+// warp partials per group written by the fused-norm launch of apply_normal
+int hop_warps(const lq_handle* h, const OpGeom& og) {
+    switch (og.op) {
+    case LQ_OP_WILSON_NORMAL: return (int)hop_red_warps(h->g.Vh, 2, 1);
+    case LQ_OP_WILSON_EO_NORMAL: return (int)hop_red_warps(h->g.Vh, 1, 1);
+    default: return (int)hop_red_warps(h->g.Vh, 2, h->p.Ls);
+    }
 }
 
 double* host_red(lq_handle* h, const OpGeom& og) {
@@ -167,10 +196,15 @@ int run_cg(lq_handle* h, const OpGeom& og, const Ctl& c, int pp, const VecRef& e
     rc = LQ_OK;
     if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = LQ_ERR_CUDA;
     for (int k = 0; k < kItersPerGraph && rc == LQ_OK; ++k) {
-        rc = apply_normal(h, og, pp, v.q.ptr, v.p.ptr, v.t.ptr, v.tmp.ptr, s);
+        // q = K^dag K p, with <p, q> = |K p|^2 and alpha fused into the launch that writes K p
+        rc = apply_normal(h, og, pp, v.q.ptr, v.p.ptr, v.t.ptr, v.tmp.ptr, s, &c);
         if (rc) break;
-        if (launch_dot(v.p, v.q, Vh, og.nblk, og.nrhs, c.sc, c.st, nullptr, FIN_ALPHA, s) != cudaSuccess ||
-            launch_cg_update(e, v.p, v.r, v.q, Vh, og.nblk, og.nrhs, c.sc, c.st, s) != cudaSuccess ||
+        if (launch_hop_norm_finalize(c.hop_partial, hop_warps(h, og), og.op == LQ_OP_DWF_NORMAL ? 1 : og.nrhs, c.st,
+                                     s) != cudaSuccess) {
+            rc = LQ_ERR_CUDA;
+            break;
+        }
+        if (launch_cg_update(e, v.p, v.r, v.q, Vh, og.nblk, og.nrhs, c.sc, c.st, s) != cudaSuccess ||
             launch_cg_xpay(v.p, v.r, Vh, og.nblk, og.nrhs, c.st, s) != cudaSuccess)
             rc = LQ_ERR_CUDA;
     }

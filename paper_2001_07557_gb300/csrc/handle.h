@@ -24,6 +24,10 @@ struct lq_handle {
     int hop_block[4]; // threads per block of the hop kernels, per precision
     const int* skip;  // per-rhs early-exit flags the solvers hand to the hop launches (else null)
     int skip_stride;
+    // fused |K p|^2 for the next operator output (the K of K^dag K), else null
+    double* red_partial;
+    unsigned* red_ticket;
+    lq::CgScalars* red_st;
     cudaStream_t solver_stream;  // private non-blocking stream the solvers capture into graphs
     void* pinned;                // pinned host buffer the solvers poll their scalars into
     size_t pinned_bytes;

@@ -16,16 +16,20 @@
 
 namespace lq {
 
-template <int P, bool R12, bool DAG, int EPI>
+template <int P, bool R12, bool DAG, int EPI, bool RED>
 __global__ void __launch_bounds__(128) wilson_hop_kernel(const HopArgs a) {
     using T = typename Prec<P>::real;
     // grid.x = site block x rhs (rhs fastest: the right-hand sides, or 5th-dimension
     // slices, of one site tile run together and share each link through L2/L1);
     // grid.y = output parity
     const int rhs = blockIdx.x % a.nrhs;
-    const int i = (blockIdx.x / a.nrhs) * blockDim.x + threadIdx.x;
     const Geom& g = a.g;
-    if (i >= g.Vh) return;
+    const int i0 = (blockIdx.x / a.nrhs) * blockDim.x + threadIdx.x;
+    const bool active = i0 < g.Vh;
+    if constexpr (!RED) {
+        if (!active) return;
+    }
+    const int i = active ? i0 : g.Vh - 1;  // (fused norm: a thread past the end stores nothing)
     const int p = a.parity0 + blockIdx.y;
     if (a.skip && a.skip[(EPI == EPI_DWF ? 0 : rhs) * a.skip_stride]) return;
 
@@ -158,19 +162,35 @@ __global__ void __launch_bounds__(128) wilson_hop_kernel(const HopArgs a) {
             o[6 + k].im = fma(c_dn, sd[6 + k].im, o[6 + k].im);
         }
     }
-    store_spinor<P, T>(a.out[p] + (size_t)rhs * a.out_rhs, g.Vh, i, o);
+    if (active) store_spinor<P, T>(a.out[p] + (size_t)rhs * a.out_rhs, g.Vh, i, o);
+    if constexpr (RED) {
+        double v = 0;
+        if (active) {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) v += (double)(o[k].re * o[k].re + o[k].im * o[k].im);
+        }
+        // warp partials, group-major: [group][warp of the group's blocks]
+        const int wpb = blockDim.x >> 5;
+        const int grp = EPI == EPI_DWF ? 0 : rhs;
+        const int nblk = EPI == EPI_DWF ? gridDim.x * gridDim.y : (gridDim.x / a.nrhs) * gridDim.y;
+        const int bidx = EPI == EPI_DWF ? blockIdx.x * gridDim.y + blockIdx.y
+                                        : (blockIdx.x / a.nrhs) * gridDim.y + blockIdx.y;
+        hop_norm_warp(v, a.red_partial + (size_t)grp * nblk * wpb, bidx * wpb + (threadIdx.x >> 5));
+    }
 }
 
 template <int P>
 cudaError_t launch_hop_prec(const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st) {
     dim3 grid(((a.g.Vh + block - 1) / block) * a.nrhs, a.nparity);
     dim3 blk(block);
-#define LQ_LAUNCH(R, D, E) wilson_hop_kernel<P, R, D, E><<<grid, blk, 0, st>>>(a)
-#define LQ_EPI(R, D)                       \
-    switch (epi) {                         \
-    case EPI_HOP: LQ_LAUNCH(R, D, EPI_HOP); break;   \
-    case EPI_DIAG: LQ_LAUNCH(R, D, EPI_DIAG); break; \
-    default: LQ_LAUNCH(R, D, EPI_DWF); break;        \
+    const bool red = a.red_partial != nullptr;
+    if (red && epi == EPI_HOP) return cudaErrorInvalidValue;
+#define LQ_LAUNCH(R, D, E, RD) wilson_hop_kernel<P, R, D, E, RD><<<grid, blk, 0, st>>>(a)
+#define LQ_EPI(R, D)                                                                           \
+    switch (epi) {                                                                             \
+    case EPI_HOP: LQ_LAUNCH(R, D, EPI_HOP, false); break;                                      \
+    case EPI_DIAG: if (red) LQ_LAUNCH(R, D, EPI_DIAG, true); else LQ_LAUNCH(R, D, EPI_DIAG, false); break; \
+    default: if (red) LQ_LAUNCH(R, D, EPI_DWF, true); else LQ_LAUNCH(R, D, EPI_DWF, false); break;         \
     }
     if (r12) {
         if (dag) { LQ_EPI(true, true) } else { LQ_EPI(true, false) }

@@ -142,7 +142,7 @@ constexpr int async_smem_bytes(int S) {
     return S * St::BYTES + (EPI >= EPI_DIAG ? St::SPIN_BYTES : 0) + (EPI == EPI_DWF ? 2 * St::SPIN_BYTES : 0);
 }
 
-template <int P, bool R12, bool DAG, int EPI, int NT, int S>
+template <int P, bool R12, bool DAG, int EPI, int NT, int S, bool RED>
 __global__ void __launch_bounds__(NT) wilson_hop_async_kernel(const HopArgs a) {
     using T = float;
     using St = AsyncStage<P, R12, NT>;
@@ -152,11 +152,17 @@ __global__ void __launch_bounds__(NT) wilson_hop_async_kernel(const HopArgs a) {
     // grid.y = output parity
     const int t = threadIdx.x;
     const int rhs = blockIdx.x % a.nrhs;
-    const int i = (blockIdx.x / a.nrhs) * NT + t;
     const Geom& g = a.g;
-    if (i >= g.Vh) return;  // no block barrier below: a finished thread may leave
+    const int i0 = (blockIdx.x / a.nrhs) * NT + t;
+    const bool active = i0 < g.Vh;
+    // without the fused norm there is no block barrier: a thread past the end leaves;
+    // with it, such a thread recomputes the last site and stores nothing
+    if constexpr (!RED) {
+        if (!active) return;
+    }
+    const int i = active ? i0 : g.Vh - 1;
     const int p = a.parity0 + blockIdx.y;
-    if (a.skip && a.skip[(EPI == EPI_DWF ? 0 : rhs) * a.skip_stride]) return;
+    if (a.skip && a.skip[(EPI == EPI_DWF ? 0 : rhs) * a.skip_stride]) return;  // uniform per block
 
     const char* __restrict__ in = a.in[p] + (size_t)rhs * a.in_rhs;
     int x[4];
@@ -298,21 +304,37 @@ __global__ void __launch_bounds__(NT) wilson_hop_async_kernel(const HopArgs a) {
             o[6 + k].im = fma(cdn, sd[6 + k].im, o[6 + k].im);
         }
     }
-    store_spinor<P, T>(a.out[p] + (size_t)rhs * a.out_rhs, g.Vh, i, o);
+    if (active) store_spinor<P, T>(a.out[p] + (size_t)rhs * a.out_rhs, g.Vh, i, o);
+    if constexpr (RED) {
+        double v = 0;
+        if (active) {
+            T q = 0;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) q += o[k].re * o[k].re + o[k].im * o[k].im;
+            v = (double)q;
+        }
+        // warp partials, group-major: [group][warp of the group's blocks]
+        const int wpb = blockDim.x >> 5;
+        const int grp = EPI == EPI_DWF ? 0 : rhs;
+        const int nblk = EPI == EPI_DWF ? gridDim.x * gridDim.y : (gridDim.x / a.nrhs) * gridDim.y;
+        const int bidx = EPI == EPI_DWF ? blockIdx.x * gridDim.y + blockIdx.y
+                                        : (blockIdx.x / a.nrhs) * gridDim.y + blockIdx.y;
+        hop_norm_warp(v, a.red_partial + (size_t)grp * nblk * wpb, bidx * wpb + (threadIdx.x >> 5));
+    }
 }
 
 // launch configuration per storage precision: threads per block, stages
 template <int P>
 struct AsyncCfg {
-    static constexpr int NT = 128;
+    static constexpr int NT = kHopThreads;
     static constexpr int S = (P == LQ_F32) ? 3 : 4;
 };
 
-template <int P, bool R12, bool DAG, int EPI>
+template <int P, bool R12, bool DAG, int EPI, bool RED>
 cudaError_t launch_async_one(const HopArgs& a, cudaStream_t st) {
     constexpr int NT = AsyncCfg<P>::NT, S = AsyncCfg<P>::S;
     constexpr int smem = async_smem_bytes<P, R12, NT, EPI>(S);
-    auto kern = wilson_hop_async_kernel<P, R12, DAG, EPI, NT, S>;
+    auto kern = wilson_hop_async_kernel<P, R12, DAG, EPI, NT, S, RED>;
     static bool configured = false;  // attribute set once per process (per instantiation)
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -326,11 +348,15 @@ cudaError_t launch_async_one(const HopArgs& a, cudaStream_t st) {
 
 template <int P>
 cudaError_t launch_hop_async(const HopArgs& a, bool r12, bool dag, int epi, cudaStream_t st) {
-#define LQ_A_EPI(R, D)                                                 \
-    switch (epi) {                                                     \
-    case EPI_HOP: return launch_async_one<P, R, D, EPI_HOP>(a, st);    \
-    case EPI_DIAG: return launch_async_one<P, R, D, EPI_DIAG>(a, st);  \
-    default: return launch_async_one<P, R, D, EPI_DWF>(a, st);         \
+    const bool red = a.red_partial != nullptr;
+    if (red && epi == EPI_HOP) return cudaErrorInvalidValue;
+#define LQ_A_EPI(R, D)                                                                       \
+    switch (epi) {                                                                           \
+    case EPI_HOP: return launch_async_one<P, R, D, EPI_HOP, false>(a, st);                   \
+    case EPI_DIAG: return red ? launch_async_one<P, R, D, EPI_DIAG, true>(a, st)             \
+                              : launch_async_one<P, R, D, EPI_DIAG, false>(a, st);           \
+    default: return red ? launch_async_one<P, R, D, EPI_DWF, true>(a, st)                    \
+                        : launch_async_one<P, R, D, EPI_DWF, false>(a, st);                  \
     }
     if (r12) {
         if (dag) { LQ_A_EPI(true, true) } else { LQ_A_EPI(true, false) }

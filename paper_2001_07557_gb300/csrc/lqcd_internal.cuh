@@ -52,6 +52,20 @@ __device__ __forceinline__ void cb_coords(const Geom& g, int cb, int p, int x[4]
     x[0] = 2 * xh + ((p + x[1] + x[2] + x[3]) & 1);
 }
 
+// Device-resident CG scalars of one right-hand side.
+struct CgScalars {
+    double rr;     // |r|^2
+    double bb;     // |b|^2
+    double stop2;  // tol^2 |b|^2
+    double pAp;
+    double alpha;
+    double beta;
+    int iter;
+    int maxiter;
+    int done;      // converged, broke down, or out of iterations
+    int status;    // LQ_OK / LQ_ERR_BREAKDOWN / LQ_ERR_NOT_CONVERGED / LQ_ERR_NAN
+};
+
 // ------------------------------------------------------------------ complex
 
 template <typename T>
@@ -573,6 +587,16 @@ __device__ __forceinline__ void su3_mul(const cplx<T> (&u)[9], const cplx<T> (&h
             uh[3 * sp + i] = acc;
         }
     }
+}
+
+// Fused |out|^2 of a hop launch: each warp writes one FP64 partial (no block
+// barrier, no fence -- the async pipeline of the hop stays undisturbed); a
+// separate one-block-per-group launch sums them in a fixed order and sets the
+// CG step length (hop_norm_finalize).
+__device__ __forceinline__ void hop_norm_warp(double v, double* partial, int warp_index) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) partial[warp_index] = v;
 }
 
 }  // namespace lq

@@ -31,7 +31,27 @@ struct HopArgs {
     double mf;
     const int* skip;  // optional per-rhs flags (skip[rhs * skip_stride]): a set flag ends the block at once
     int skip_stride;
+    // optional fused |out|^2 per right-hand side (one group for the domain wall):
+    // one FP64 partial per warp; hop_norm_finalize sums them and sets
+    // st.pAp = |out|^2 = <p, K^dag K p> and st.alpha = st.rr / st.pAp
+    double* red_partial;
+    unsigned* red_ticket;  // unused by the hop (kept for the layout of callers)
+    CgScalars* red_st;
 };
+
+// Every hop launch uses blocks of this many threads (the fused-norm partial
+// count depends on it).
+constexpr int kHopThreads = 128;
+
+// Warp partials per reduction group of a fused-norm hop launch over nparity
+// parities and `slices` 5th-dimension slices (1 for Wilson).
+inline size_t hop_red_warps(int Vh, int nparity, int slices) {
+    return (size_t)((Vh + kHopThreads - 1) / kHopThreads) * (kHopThreads / 32) * nparity * slices;
+}
+
+// Sum the warp partials of the last fused-norm hop (ngroups groups of
+// nwarps each) in a fixed order and set pAp and alpha of each group.
+cudaError_t launch_hop_norm_finalize(const double* partial, int nwarps, int ngroups, CgScalars* st, cudaStream_t s);
 
 cudaError_t launch_hop(int prec, const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st);
 cudaError_t launch_hop_f64(const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st);
