@@ -10,6 +10,16 @@
 
 namespace lq {
 
+cudaError_t launch_hop_batch(int prec, const HopArgs* args, const int* lat_off, int nlat, bool r12, bool dag, int epi,
+                             int mult, int grid, cudaStream_t st, int* occ) {
+    switch (prec) {
+    case LQ_F32: return launch_hop_batch_f32(args, lat_off, nlat, r12, dag, epi, mult, grid, st, occ);
+    case LQ_F16: return launch_hop_batch_f16(args, lat_off, nlat, r12, dag, epi, mult, grid, st, occ);
+    case LQ_BF16: return launch_hop_batch_bf16(args, lat_off, nlat, r12, dag, epi, mult, grid, st, occ);
+    default: return cudaErrorInvalidValue;  // the FP64 hop has no batched form
+    }
+}
+
 cudaError_t launch_hop(int prec, const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st) {
     switch (prec) {
     case LQ_F64: return launch_hop_f64(a, r12, dag, epi, block, st);
@@ -72,7 +82,7 @@ static HopArgs base_args(lq_handle* h, const char* links, size_t lb) {
     return a;
 }
 
-int native_wilson_full(lq_handle* h, int prec, char* out, const char* in, int nrhs, bool dag, cudaStream_t st) {
+int prep_wilson_full(lq_handle* h, int prec, char* out, const char* in, int nrhs, HopArgs* ap, cudaStream_t st) {
     const char* L;
     size_t lb;
     int rc = get_links(h, prec, &L, &lb, st);
@@ -91,11 +101,12 @@ int native_wilson_full(lq_handle* h, int prec, char* out, const char* in, int nr
     a.c_hop = -0.5;
     a.c_diag = h->p.mass + 4.0;
     set_red(a, h);
-    return status_of(launch_hop(prec, a, h->p.compress12 != 0, dag, EPI_DIAG, h->hop_block[prec], st));
+    *ap = a;
+    return LQ_OK;
 }
 
-int native_wilson_block(lq_handle* h, int prec, char* out, const char* in, int out_parity, int nrhs, bool dag,
-                        double c_hop, cudaStream_t st) {
+int prep_wilson_block(lq_handle* h, int prec, char* out, const char* in, int out_parity, int nrhs, double c_hop,
+                      HopArgs* ap, cudaStream_t st) {
     const char* L;
     size_t lb;
     int rc = get_links(h, prec, &L, &lb, st);
@@ -109,18 +120,17 @@ int native_wilson_block(lq_handle* h, int prec, char* out, const char* in, int o
     a.nparity = 1;
     a.nrhs = nrhs;
     a.c_hop = c_hop;
-    return status_of(launch_hop(prec, a, h->p.compress12 != 0, dag, EPI_HOP, h->hop_block[prec], st));
+    *ap = a;
+    return LQ_OK;
 }
 
-int native_wilson_schur(lq_handle* h, int prec, char* out, const char* in, char* tmp, int nrhs, bool dag,
-                        cudaStream_t st) {
-    // out = a in - 1/(4a) H_eo H_oe in
+// second half of the Schur complement: out = a in - 1/(4a) H_eo tmp
+int prep_wilson_schur2(lq_handle* h, int prec, char* out, const char* tmp, const char* in, int nrhs, HopArgs* ap,
+                       cudaStream_t st) {
     const double am = h->p.mass + 4.0;
-    int rc = native_wilson_block(h, prec, tmp, in, 1, nrhs, dag, 1.0, st);
-    if (rc) return rc;
     const char* L;
     size_t lb;
-    rc = get_links(h, prec, &L, &lb, st);
+    int rc = get_links(h, prec, &L, &lb, st);
     if (rc) return rc;
     const size_t blk = native_block_bytes(h, prec);
     HopArgs a = base_args(h, L, lb);
@@ -134,6 +144,32 @@ int native_wilson_schur(lq_handle* h, int prec, char* out, const char* in, char*
     a.c_hop = -1.0 / (4.0 * am);
     a.c_diag = am;
     set_red(a, h);
+    *ap = a;
+    return LQ_OK;
+}
+
+int native_wilson_full(lq_handle* h, int prec, char* out, const char* in, int nrhs, bool dag, cudaStream_t st) {
+    HopArgs a;
+    int rc = prep_wilson_full(h, prec, out, in, nrhs, &a, st);
+    if (rc) return rc;
+    return status_of(launch_hop(prec, a, h->p.compress12 != 0, dag, EPI_DIAG, h->hop_block[prec], st));
+}
+
+int native_wilson_block(lq_handle* h, int prec, char* out, const char* in, int out_parity, int nrhs, bool dag,
+                        double c_hop, cudaStream_t st) {
+    HopArgs a;
+    int rc = prep_wilson_block(h, prec, out, in, out_parity, nrhs, c_hop, &a, st);
+    if (rc) return rc;
+    return status_of(launch_hop(prec, a, h->p.compress12 != 0, dag, EPI_HOP, h->hop_block[prec], st));
+}
+
+int native_wilson_schur(lq_handle* h, int prec, char* out, const char* in, char* tmp, int nrhs, bool dag,
+                        cudaStream_t st) {
+    // out = a in - 1/(4a) H_eo H_oe in
+    int rc = native_wilson_block(h, prec, tmp, in, 1, nrhs, dag, 1.0, st);
+    if (rc) return rc;
+    HopArgs a;
+    if ((rc = prep_wilson_schur2(h, prec, out, tmp, in, nrhs, &a, st))) return rc;
     return status_of(launch_hop(prec, a, h->p.compress12 != 0, dag, EPI_DIAG, h->hop_block[prec], st));
 }
 

@@ -352,6 +352,112 @@ __global__ void hop_norm_finalize_kernel(const double* partial, int nwarps, CgSc
     }
 }
 
+// ------------------------------------------------------- batched segments
+
+template <int P>
+__device__ __forceinline__ const char* seg_blk(const char* base, int b, int Vh) {
+    return base + (size_t)b * spinor_site_bytes(P) * Vh;
+}
+
+template <int PP>
+__global__ void __launch_bounds__(kThreads) bdot_alpha_kernel(const BSeg* __restrict__ segs) {
+    const BSeg& sg = segs[blockIdx.y];
+    if (sg.st->done) return;
+    using T = Compute<PP>;
+    double acc = 0;
+    const long n = (long)sg.Vh * sg.nblk;
+    for (long j = (long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
+        const int bk = (int)(j / sg.Vh), i = (int)(j - (long)bk * sg.Vh);
+        cplx<T> a[12], b[12];
+        load_spinor<PP, T>(seg_blk<PP>(sg.p, bk, sg.Vh), sg.Vh, i, a);
+        load_spinor<PP, T>(seg_blk<PP>(sg.q, bk, sg.Vh), sg.Vh, i, b);
+        T site = 0;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) site += a[k].re * b[k].re + a[k].im * b[k].im;
+        acc += (double)site;
+    }
+    double total;
+    if (!reduce_last(acc, sg.partial, sg.ticket, gridDim.x, total)) return;
+    if (threadIdx.x != 0) return;
+    CgScalars& s = *sg.st;
+    s.pAp = total;
+    if (!(total > 0.0) || !finite(total)) {
+        s.done = 1;
+        s.status = LQ_ERR_BREAKDOWN;
+        s.alpha = 0;
+    } else {
+        s.alpha = s.rr / total;
+    }
+}
+
+template <int PX, int PP>
+__global__ void __launch_bounds__(kThreads) bupdate_kernel(const BSeg* __restrict__ segs) {
+    const BSeg& sg = segs[blockIdx.y];
+    CgScalars& s = *sg.st;
+    if (s.done) return;
+    using T = Compute<PX, PP>;
+    const T alpha = (T)s.alpha;
+    double acc = 0;
+    const long n = (long)sg.Vh * sg.nblk;
+    for (long j = (long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
+        const int bk = (int)(j / sg.Vh), i = (int)(j - (long)bk * sg.Vh);
+        cplx<T> xs[12], ps[12], rs[12], qs[12];
+        load_spinor<PX, T>(seg_blk<PX>(sg.x, bk, sg.Vh), sg.Vh, i, xs);
+        load_spinor<PP, T>(seg_blk<PP>(sg.p, bk, sg.Vh), sg.Vh, i, ps);
+        load_spinor<PX, T>(seg_blk<PX>(sg.r, bk, sg.Vh), sg.Vh, i, rs);
+        load_spinor<PP, T>(seg_blk<PP>(sg.q, bk, sg.Vh), sg.Vh, i, qs);
+        T site = 0;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            xs[k].re = fma(alpha, ps[k].re, xs[k].re);
+            xs[k].im = fma(alpha, ps[k].im, xs[k].im);
+            rs[k].re = fma(-alpha, qs[k].re, rs[k].re);
+            rs[k].im = fma(-alpha, qs[k].im, rs[k].im);
+            site += rs[k].re * rs[k].re + rs[k].im * rs[k].im;
+        }
+        acc += (double)site;
+        store_spinor<PX, T>(const_cast<char*>(seg_blk<PX>(sg.x, bk, sg.Vh)), sg.Vh, i, xs);
+        store_spinor<PX, T>(const_cast<char*>(seg_blk<PX>(sg.r, bk, sg.Vh)), sg.Vh, i, rs);
+    }
+    double total;
+    if (!reduce_last(acc, sg.partial, sg.ticket, gridDim.x, total)) return;
+    if (threadIdx.x != 0) return;
+    s.iter += 1;
+    if (!finite(total)) {
+        s.done = 1;
+        s.status = LQ_ERR_NAN;
+        return;
+    }
+    s.beta = total / s.rr;
+    s.rr = total;
+    if (total <= s.stop2) s.done = 1;
+    else if (s.iter >= s.maxiter) {
+        s.done = 1;
+        s.status = LQ_ERR_NOT_CONVERGED;
+    }
+}
+
+template <int PP, int PR>
+__global__ void __launch_bounds__(kThreads) bxpay_kernel(const BSeg* __restrict__ segs) {
+    const BSeg& sg = segs[blockIdx.y];
+    if (sg.st->done) return;
+    using T = Compute<PP, PR>;
+    const T beta = (T)sg.st->beta;
+    const long n = (long)sg.Vh * sg.nblk;
+    for (long j = (long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
+        const int bk = (int)(j / sg.Vh), i = (int)(j - (long)bk * sg.Vh);
+        cplx<T> ps[12], rs[12];
+        load_spinor<PP, T>(seg_blk<PP>(sg.p, bk, sg.Vh), sg.Vh, i, ps);
+        load_spinor<PR, T>(seg_blk<PR>(sg.r, bk, sg.Vh), sg.Vh, i, rs);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            ps[k].re = fma(beta, ps[k].re, rs[k].re);
+            ps[k].im = fma(beta, ps[k].im, rs[k].im);
+        }
+        store_spinor<PP, T>(const_cast<char*>(seg_blk<PP>(sg.p, bk, sg.Vh)), sg.Vh, i, ps);
+    }
+}
+
 int grid_x(int Vh, int nblk) {
     static int sms = 0;
     if (!sms) {
@@ -446,6 +552,35 @@ cudaError_t launch_axpby(const VecRef& y, const VecRef& x, double a, double b, i
     dim3 grid(grid_x(Vh, nblk), nrhs);
     LQ_P_SWITCH(y.prec, PY, LQ_P_SWITCH(x.prec, PX,
         (axpby_kernel<PY, PX><<<grid, kThreads, 0, s>>>(y, x, a, b, Vh, nblk))))
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bdot_alpha(const BSeg* segs, int nseg, int gx, int pp, cudaStream_t s) {
+    dim3 grid(gx, nseg);
+    LQ_P_SWITCH(pp, PP, (bdot_alpha_kernel<PP><<<grid, kThreads, 0, s>>>(segs)))
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bupdate(const BSeg* segs, int nseg, int gx, int px, int pp, cudaStream_t s) {
+    dim3 grid(gx, nseg);
+    if (px != LQ_F32 && px != LQ_F64) return cudaErrorInvalidValue;
+    if (px == LQ_F64) {
+        if (pp != LQ_F64) return cudaErrorInvalidValue;
+        bupdate_kernel<LQ_F64, LQ_F64><<<grid, kThreads, 0, s>>>(segs);
+    } else {
+        switch (pp) {
+        case LQ_F32: bupdate_kernel<LQ_F32, LQ_F32><<<grid, kThreads, 0, s>>>(segs); break;
+        case LQ_F16: bupdate_kernel<LQ_F32, LQ_F16><<<grid, kThreads, 0, s>>>(segs); break;
+        case LQ_BF16: bupdate_kernel<LQ_F32, LQ_BF16><<<grid, kThreads, 0, s>>>(segs); break;
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bxpay(const BSeg* segs, int nseg, int gx, int pp, int pr, cudaStream_t s) {
+    dim3 grid(gx, nseg);
+    LQ_P_SWITCH(pp, PP, LQ_P_SWITCH(pr, PR, (bxpay_kernel<PP, PR><<<grid, kThreads, 0, s>>>(segs))))
     return cudaGetLastError();
 }
 

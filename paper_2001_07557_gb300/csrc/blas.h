@@ -27,6 +27,26 @@ enum { FIN_STORE = 0, FIN_ALPHA = 1 };
 
 size_t reduce_scratch_doubles(int Vh, int nblk, int nrhs);
 
+// One (lattice, right-hand side) segment of a batched CG over lattices of
+// different sizes: base pointers of its x, p, r, q vectors (nblk parity blocks
+// of Vh sites each), its scalars, and its reduction partials (gx) and ticket.
+struct BSeg {
+    char* x;
+    char* p;
+    char* r;
+    char* q;
+    int Vh;
+    int nblk;
+    CgScalars* st;
+    double* partial;
+    unsigned* ticket;
+};
+
+// Batched CG steps over nseg segments, gx blocks per segment (grid = gx x nseg).
+cudaError_t launch_bdot_alpha(const BSeg* segs, int nseg, int gx, int pp, cudaStream_t s);
+cudaError_t launch_bupdate(const BSeg* segs, int nseg, int gx, int px, int pp, cudaStream_t s);
+cudaError_t launch_bxpay(const BSeg* segs, int nseg, int gx, int pp, int pr, cudaStream_t s);
+
 cudaError_t launch_dot(const VecRef& a, const VecRef& b, int Vh, int nblk, int nrhs, const Scratch& sc,
                        CgScalars* st, double* out, int fin, cudaStream_t s);
 cudaError_t launch_cg_update(const VecRef& x, const VecRef& p, const VecRef& r, const VecRef& q, int Vh, int nblk,

@@ -511,8 +511,3 @@ extern "C" int cg_solve(lq_handle* h, void* x, const void* b, const lq_cg_params
     return ret;
 }
 
-extern "C" int lq_batch_cg_solve(lq_handle** hs, int nlat, void** xs, const void** bs, const lq_cg_params* cp,
-                                 lq_cg_stats* stats, void* stream) {
-    (void)hs; (void)nlat; (void)xs; (void)bs; (void)cp; (void)stats; (void)stream;
-    return LQ_ERR_ARG;
-}

@@ -61,6 +61,13 @@ int native_wilson_schur(lq_handle* h, int prec, char* out, const char* in, char*
                         cudaStream_t st);
 int native_dwf(lq_handle* h, int prec, char* out, const char* in, bool dag, cudaStream_t st);
 
+// Launch descriptors of the Wilson operator pieces (links packed on demand).
+int prep_wilson_full(lq_handle* h, int prec, char* out, const char* in, int nrhs, HopArgs* a, cudaStream_t st);
+int prep_wilson_block(lq_handle* h, int prec, char* out, const char* in, int out_parity, int nrhs, double c_hop,
+                      HopArgs* a, cudaStream_t st);
+int prep_wilson_schur2(lq_handle* h, int prec, char* out, const char* tmp, const char* in, int nrhs, HopArgs* a,
+                       cudaStream_t st);
+
 // ---------------------------------------------------------- argument checks
 
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }

@@ -142,28 +142,21 @@ constexpr int async_smem_bytes(int S) {
     return S * St::BYTES + (EPI >= EPI_DIAG ? St::SPIN_BYTES : 0) + (EPI == EPI_DWF ? 2 * St::SPIN_BYTES : 0);
 }
 
-template <int P, bool R12, bool DAG, int EPI, int NT, int S, bool RED>
-__global__ void __launch_bounds__(NT) wilson_hop_async_kernel(const HopArgs a) {
+// launch configuration per storage precision: threads per block, stages
+template <int P>
+struct AsyncCfg {
+    static constexpr int NT = kHopThreads;
+    static constexpr int S = (P == LQ_F32) ? 3 : 4;
+};
+
+// One output site (checkerboard index i < Vh, right-hand side rhs, parity p):
+// the staged 8-direction gather and the epilogue, result in o (not stored).
+template <int P, bool R12, bool DAG, int EPI, int NT, int S>
+__device__ __forceinline__ void hop_async_site(const HopArgs& a, int i, int rhs, int p, unsigned char* smem, int t,
+                                               cplx<float> (&o)[12]) {
     using T = float;
     using St = AsyncStage<P, R12, NT>;
-    extern __shared__ __align__(16) unsigned char smem[];
-    // grid.x = site block x rhs (rhs fastest: the right-hand sides, or 5th-dimension
-    // slices, of one site tile run together and share each link through L2/L1);
-    // grid.y = output parity
-    const int t = threadIdx.x;
-    const int rhs = blockIdx.x % a.nrhs;
     const Geom& g = a.g;
-    const int i0 = (blockIdx.x / a.nrhs) * NT + t;
-    const bool active = i0 < g.Vh;
-    // without the fused norm there is no block barrier: a thread past the end leaves;
-    // with it, such a thread recomputes the last site and stores nothing
-    if constexpr (!RED) {
-        if (!active) return;
-    }
-    const int i = active ? i0 : g.Vh - 1;
-    const int p = a.parity0 + blockIdx.y;
-    if (a.skip && a.skip[(EPI == EPI_DWF ? 0 : rhs) * a.skip_stride]) return;  // uniform per block
-
     const char* __restrict__ in = a.in[p] + (size_t)rhs * a.in_rhs;
     int x[4];
     cb_coords(g, i, p, x);
@@ -276,7 +269,6 @@ __global__ void __launch_bounds__(NT) wilson_hop_async_kernel(const HopArgs a) {
 #undef LQ_ASYNC_DIR
 
     const T ch = (T)a.c_hop;
-    cplx<T> o[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) o[k] = {ch * acc[k].re, ch * acc[k].im};
     if constexpr (EPI >= EPI_DIAG) {
@@ -304,6 +296,30 @@ __global__ void __launch_bounds__(NT) wilson_hop_async_kernel(const HopArgs a) {
             o[6 + k].im = fma(cdn, sd[6 + k].im, o[6 + k].im);
         }
     }
+}
+
+template <int P, bool R12, bool DAG, int EPI, int NT, int S, bool RED>
+__global__ void __launch_bounds__(NT) wilson_hop_async_kernel(const HopArgs a) {
+    using T = float;
+    extern __shared__ __align__(16) unsigned char smem[];
+    // grid.x = site block x rhs (rhs fastest: the right-hand sides, or 5th-dimension
+    // slices, of one site tile run together and share each link through L2/L1);
+    // grid.y = output parity
+    const int t = threadIdx.x;
+    const int rhs = blockIdx.x % a.nrhs;
+    const Geom& g = a.g;
+    const int i0 = (blockIdx.x / a.nrhs) * NT + t;
+    const bool active = i0 < g.Vh;
+    // without the fused norm there is no block barrier: a thread past the end leaves;
+    // with it, such a thread recomputes the last site and stores nothing
+    if constexpr (!RED) {
+        if (!active) return;
+    }
+    const int i = active ? i0 : g.Vh - 1;
+    const int p = a.parity0 + blockIdx.y;
+    if (a.skip && a.skip[(EPI == EPI_DWF ? 0 : rhs) * a.skip_stride]) return;  // uniform per block
+    cplx<T> o[12];
+    hop_async_site<P, R12, DAG, EPI, NT, S>(a, i, rhs, p, smem, t, o);
     if (active) store_spinor<P, T>(a.out[p] + (size_t)rhs * a.out_rhs, g.Vh, i, o);
     if constexpr (RED) {
         double v = 0;
@@ -323,13 +339,6 @@ __global__ void __launch_bounds__(NT) wilson_hop_async_kernel(const HopArgs a) {
     }
 }
 
-// launch configuration per storage precision: threads per block, stages
-template <int P>
-struct AsyncCfg {
-    static constexpr int NT = kHopThreads;
-    static constexpr int S = (P == LQ_F32) ? 3 : 4;
-};
-
 template <int P, bool R12, bool DAG, int EPI, bool RED>
 cudaError_t launch_async_one(const HopArgs& a, cudaStream_t st) {
     constexpr int NT = AsyncCfg<P>::NT, S = AsyncCfg<P>::S;
@@ -344,6 +353,73 @@ cudaError_t launch_async_one(const HopArgs& a, cudaStream_t st) {
     dim3 grid(((a.g.Vh + NT - 1) / NT) * a.nrhs, a.nparity);
     kern<<<grid, NT, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Persistent hop over a batch of lattices of different sizes: one launch of
+// `grid` blocks walks the flattened work list of every lattice's
+// (site tile, right-hand side, parity) items, tile = mult x NT sites, item k
+// of lattice l at lat_off[l] + k.  The per-lattice launch descriptors
+// (pointers, geometry, links, skip flags) live in device memory.
+template <int P, bool R12, bool DAG, int EPI, int NT, int S>
+__global__ void __launch_bounds__(NT) wilson_hop_batch_kernel(const HopArgs* __restrict__ args,
+                                                              const int* __restrict__ lat_off, int nlat, int mult) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int t = threadIdx.x;
+    const int total = lat_off[nlat];
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        int l = 0;
+        while (l + 1 < nlat && item >= lat_off[l + 1]) ++l;
+        const HopArgs& a = args[l];
+        int local = item - lat_off[l];
+        const int pidx = local % a.nparity;
+        local /= a.nparity;
+        const int rhs = local % a.nrhs;
+        const int tile = local / a.nrhs;
+        if (a.skip && a.skip[rhs * a.skip_stride]) continue;
+        const int p = a.parity0 + pidx;
+        for (int m = 0; m < mult; ++m) {
+            const int i = (tile * mult + m) * NT + t;
+            if (i < a.g.Vh) {
+                cplx<float> o[12];
+                hop_async_site<P, R12, DAG, EPI, NT, S>(a, i, rhs, p, smem, t, o);
+                store_spinor<P, float>(a.out[p] + (size_t)rhs * a.out_rhs, a.g.Vh, i, o);
+            }
+        }
+    }
+}
+
+template <int P, bool R12, bool DAG, int EPI>
+cudaError_t launch_batch_one(const HopArgs* args, const int* lat_off, int nlat, int mult, int grid, cudaStream_t st,
+                             int* max_blocks_per_sm) {
+    constexpr int NT = AsyncCfg<P>::NT, S = AsyncCfg<P>::S;
+    constexpr int smem = async_smem_bytes<P, R12, NT, EPI>(S);
+    auto kern = wilson_hop_batch_kernel<P, R12, DAG, EPI, NT, S>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    if (max_blocks_per_sm) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, kern, NT, smem);
+    kern<<<grid, NT, smem, st>>>(args, lat_off, nlat, mult);
+    return cudaGetLastError();
+}
+
+// Batched hop launch (grid = 0: report the occupancy in *max_blocks_per_sm instead).
+template <int P>
+cudaError_t launch_hop_batch_prec(const HopArgs* args, const int* lat_off, int nlat, bool r12, bool dag, int epi,
+                                  int mult, int grid, cudaStream_t st, int* max_blocks_per_sm) {
+    if (epi == EPI_DWF) return cudaErrorInvalidValue;
+#define LQ_B_EPI(R, D)                                                                                       \
+    return epi == EPI_HOP ? launch_batch_one<P, R, D, EPI_HOP>(args, lat_off, nlat, mult, grid, st, max_blocks_per_sm) \
+                          : launch_batch_one<P, R, D, EPI_DIAG>(args, lat_off, nlat, mult, grid, st, max_blocks_per_sm);
+    if (r12) {
+        if (dag) { LQ_B_EPI(true, true) } else { LQ_B_EPI(true, false) }
+    } else {
+        if (dag) { LQ_B_EPI(false, true) } else { LQ_B_EPI(false, false) }
+    }
+#undef LQ_B_EPI
 }
 
 template <int P>

@@ -59,6 +59,16 @@ cudaError_t launch_hop_f32(const HopArgs& a, bool r12, bool dag, int epi, int bl
 cudaError_t launch_hop_f16(const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st);
 cudaError_t launch_hop_bf16(const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st);
 
+// Persistent hop over a batch of lattices (FP32 / FP16 / BF16 storage):
+// args[nlat] device launch descriptors, lat_off[nlat + 1] device prefix sums
+// of each lattice's work items (ceil(Vh / (128 mult)) x nrhs x nparity).
+// grid == 0: *occ receives the resident blocks per SM (nothing is launched).
+cudaError_t launch_hop_batch(int prec, const HopArgs* args, const int* lat_off, int nlat, bool r12, bool dag, int epi,
+                             int mult, int grid, cudaStream_t st, int* occ);
+cudaError_t launch_hop_batch_f32(const HopArgs*, const int*, int, bool, bool, int, int, int, cudaStream_t, int*);
+cudaError_t launch_hop_batch_f16(const HopArgs*, const int*, int, bool, bool, int, int, int, cudaStream_t, int*);
+cudaError_t launch_hop_batch_bf16(const HopArgs*, const int*, int, bool, bool, int, int, int, cudaStream_t, int*);
+
 // ----------------------------------------------------------- conversions
 // Spinor fields.  "site-major" = [rhs][site][4][3][2] in F64/F32, sites either
 // the full lattice in lexicographic order (full = true) or one parity in cb
