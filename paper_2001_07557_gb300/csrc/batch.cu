@@ -484,7 +484,12 @@ extern "C" int lq_batch_cg_solve(lq_handle** hs, int nlat, void** xs, const void
                     if (conv[l * nr + k] && cudaMemsetAsync(L.RIN + k * s32, 0, s32, s) != cudaSuccess)
                         rc = LQ_ERR_CUDA;
             }
-            if (rc || (rc = inner(itol, cp->maxiter - total_inner))) break;
+            // inner tolerance: the precision's floor, or less work once the outer target is within reach
+            double reach = 0.5;  // the smallest reduction every unfinished right-hand side still needs
+            for (int g = 0; g < nseg; ++g)
+                if (!conv[g] && rel[g] > 0) reach = std::min(reach, 0.5 * cp->tol / rel[g]);
+            const double need = std::max(itol, reach);
+            if (rc || (rc = inner(need, cp->maxiter - total_inner))) break;
             int most = 0;
             for (int g = 0; g < nseg; ++g) {
                 iters[g] += host_st[g].iter;

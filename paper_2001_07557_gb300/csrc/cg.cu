@@ -482,7 +482,13 @@ extern "C" int cg_solve(lq_handle* h, void* x, const void* b, const lq_cg_params
                 }
                 most = bit;
             } else {
-                if ((rc = run_cg(h, og, c, ip, E, RIN, itol, cp->maxiter - total_inner, WS_CG0, s))) return rc;
+                // inner tolerance: the precision's floor itol, or less work when the outer
+            // target is already within reach (relative to the current residual, with margin)
+            double reach = 0.5;  // the smallest reduction every unfinished right-hand side still needs
+            for (int k = 0; k < og.nrhs; ++k)
+                if (!conv[k] && rel[k] > 0) reach = std::min(reach, 0.5 * cp->tol / rel[k]);
+            const double need = std::max(itol, reach);
+            if ((rc = run_cg(h, og, c, ip, E, RIN, need, cp->maxiter - total_inner, WS_CG0, s))) return rc;
                 for (int k = 0; k < og.nrhs; ++k) {
                     iters[k] += c.host[k].iter;
                     most = std::max(most, c.host[k].iter);
