@@ -47,7 +47,7 @@ int ensure_ws(lq_handle* h, int k, size_t bytes, void** out) {
 }
 
 int get_links(lq_handle* h, int prec, const char** links, size_t* link_block, cudaStream_t st) {
-    const bool r12 = h->p.compress12 != 0;
+    const bool r12 = link_r12(h, prec);
     void*& L = h->links[prec][r12];
     const size_t lb = (size_t)link_site_bytes(prec, r12) * h->g.Vh;
     if (!L) {
@@ -152,7 +152,7 @@ int native_wilson_full(lq_handle* h, int prec, char* out, const char* in, int nr
     HopArgs a;
     int rc = prep_wilson_full(h, prec, out, in, nrhs, &a, st);
     if (rc) return rc;
-    return status_of(launch_hop(prec, a, h->p.compress12 != 0, dag, EPI_DIAG, h->hop_block[prec], st));
+    return status_of(launch_hop(prec, a, link_r12(h, prec), dag, EPI_DIAG, h->hop_block[prec], st));
 }
 
 int native_wilson_block(lq_handle* h, int prec, char* out, const char* in, int out_parity, int nrhs, bool dag,
@@ -160,7 +160,7 @@ int native_wilson_block(lq_handle* h, int prec, char* out, const char* in, int o
     HopArgs a;
     int rc = prep_wilson_block(h, prec, out, in, out_parity, nrhs, c_hop, &a, st);
     if (rc) return rc;
-    return status_of(launch_hop(prec, a, h->p.compress12 != 0, dag, EPI_HOP, h->hop_block[prec], st));
+    return status_of(launch_hop(prec, a, link_r12(h, prec), dag, EPI_HOP, h->hop_block[prec], st));
 }
 
 int native_wilson_schur(lq_handle* h, int prec, char* out, const char* in, char* tmp, int nrhs, bool dag,
@@ -170,7 +170,7 @@ int native_wilson_schur(lq_handle* h, int prec, char* out, const char* in, char*
     if (rc) return rc;
     HopArgs a;
     if ((rc = prep_wilson_schur2(h, prec, out, tmp, in, nrhs, &a, st))) return rc;
-    return status_of(launch_hop(prec, a, h->p.compress12 != 0, dag, EPI_DIAG, h->hop_block[prec], st));
+    return status_of(launch_hop(prec, a, link_r12(h, prec), dag, EPI_DIAG, h->hop_block[prec], st));
 }
 
 int native_dwf(lq_handle* h, int prec, char* out, const char* in, bool dag, cudaStream_t st) {
@@ -194,7 +194,7 @@ int native_dwf(lq_handle* h, int prec, char* out, const char* in, bool dag, cuda
     a.c_hop = -0.5;
     a.c_diag = 5.0 - h->p.M5;
     set_red(a, h);
-    return status_of(launch_hop(prec, a, h->p.compress12 != 0, dag, EPI_DWF, h->hop_block[prec], st));
+    return status_of(launch_hop(prec, a, link_r12(h, prec), dag, EPI_DWF, h->hop_block[prec], st));
 }
 
 }  // namespace lq

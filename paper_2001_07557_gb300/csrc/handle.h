@@ -47,6 +47,10 @@ int ensure_ws(lq_handle* h, int k, size_t bytes, void** out);
 // Native links of a precision (packed from the saved gauge copy on first use).
 int get_links(lq_handle* h, int prec, const char** links, size_t* link_block, cudaStream_t st);
 
+// Links of this precision stored as 2 rows?  FP64 hops are bound by FP64
+// arithmetic, so FP64 always keeps all 3 rows (rebuilding row 3 costs FMAs).
+inline bool link_r12(const lq_handle* h, int prec) { return h->p.compress12 != 0 && prec != LQ_F64; }
+
 // Bytes of one native parity block of one field.
 inline size_t native_block_bytes(const lq_handle* h, int prec) {
     return (size_t)spinor_site_bytes(prec) * (size_t)h->g.Vh;

@@ -27,8 +27,8 @@ template <int P, bool R12>
 struct AsyncLayout {
     static constexpr bool NORM = Prec<P>::has_norm;
     static constexpr int SP_CH = (P == LQ_F32) ? 6 : 3;  // 16-byte spinor chunks
-    static constexpr int LK_CH = R12 ? 3 : 9;             // link chunks
-    static constexpr int LK_B = (P == LQ_F32) ? (R12 ? 16 : 8) : (R12 ? 8 : 4);  // bytes per link chunk
+    static constexpr int LK16 = LinkLayout<P, R12>::NFULL;  // 16-byte link chunks
+    static constexpr int LKT = LinkLayout<P, R12>::TAIL;    // bytes of the link's tail chunk (0, 4, 8)
 };
 
 template <int P, bool R12, int NT>
@@ -37,7 +37,8 @@ struct AsyncStage {
     static constexpr int SP_OFF = 0;
     static constexpr int NRM_OFF = SP_OFF + L::SP_CH * 16 * NT;
     static constexpr int LK_OFF = NRM_OFF + (L::NORM ? 4 * NT : 0);
-    static constexpr int BYTES = ((LK_OFF + L::LK_CH * L::LK_B * NT) + 15) / 16 * 16;
+    static constexpr int LKT_OFF = LK_OFF + L::LK16 * 16 * NT;
+    static constexpr int BYTES = ((LKT_OFF + L::LKT * NT) + 15) / 16 * 16;
     static constexpr int SPIN_BYTES = ((L::SP_CH * 16 + (L::NORM ? 4 : 0)) * NT + 15) / 16 * 16;
 };
 
@@ -60,9 +61,11 @@ __device__ __forceinline__ void async_link(unsigned char* stage, const char* __r
     using L = AsyncLayout<P, R12>;
     using St = AsyncStage<P, R12, NT>;
 #pragma unroll
-    for (int k = 0; k < L::LK_CH; ++k)
-        __pipeline_memcpy_async(stage + St::LK_OFF + (k * NT + t) * L::LK_B,
-                                blk + ((size_t)k * Vh + site) * L::LK_B, L::LK_B);
+    for (int c = 0; c < L::LK16; ++c)
+        __pipeline_memcpy_async(stage + St::LK_OFF + (c * NT + t) * 16, blk + ((size_t)c * Vh + site) * 16, 16);
+    if constexpr (L::LKT > 0)
+        __pipeline_memcpy_async(stage + St::LKT_OFF + t * L::LKT,
+                                blk + (size_t)L::LK16 * 16 * Vh + (size_t)site * L::LKT, L::LKT);
 }
 
 // read one staged spinor back (unscaled values + norm)
@@ -98,42 +101,23 @@ template <int P, bool R12, int NT>
 __device__ __forceinline__ void smem_link(const unsigned char* stage, int t, cplx<float> (&u)[9]) {
     using L = AsyncLayout<P, R12>;
     using St = AsyncStage<P, R12, NT>;
-    const unsigned char* b = stage + St::LK_OFF;
-    if constexpr (P == LQ_F32) {
-        if constexpr (R12) {
+    RawLink<P, R12> r;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const float4 v = *reinterpret_cast<const float4*>(b + (k * NT + t) * 16);
-                u[2 * k] = {v.x, v.y};
-                u[2 * k + 1] = {v.z, v.w};
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                const float2 v = *reinterpret_cast<const float2*>(b + (k * NT + t) * 8);
-                u[k] = {v.x, v.y};
-            }
-        }
-    } else {
-        std::integral_constant<int, P> tag;
-        if constexpr (R12) {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const uint2 v = *reinterpret_cast<const uint2*>(b + (k * NT + t) * 8);
-                float2 x = h2f(v.x, tag), y = h2f(v.y, tag);
-                u[2 * k] = {x.x, x.y};
-                u[2 * k + 1] = {y.x, y.y};
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                const float2 x = h2f(*reinterpret_cast<const uint32_t*>(b + (k * NT + t) * 4), tag);
-                u[k] = {x.x, x.y};
-            }
-        }
+    for (int c = 0; c < L::LK16; ++c) {
+        const uint4 v = *reinterpret_cast<const uint4*>(stage + St::LK_OFF + (c * NT + t) * 16);
+        r.w[4 * c] = v.x;
+        r.w[4 * c + 1] = v.y;
+        r.w[4 * c + 2] = v.z;
+        r.w[4 * c + 3] = v.w;
     }
-    (void)sizeof(L);
-    if constexpr (R12) reconstruct_row2(u);
+    if constexpr (L::LKT == 8) {
+        const uint2 v = *reinterpret_cast<const uint2*>(stage + St::LKT_OFF + t * 8);
+        r.w[4 * L::LK16] = v.x;
+        r.w[4 * L::LK16 + 1] = v.y;
+    } else if constexpr (L::LKT == 4) {
+        r.w[4 * L::LK16] = *reinterpret_cast<const uint32_t*>(stage + St::LKT_OFF + t * 4);
+    }
+    raw_unpack<P, R12, float>(r, u);
 }
 
 template <int P, bool R12, int NT, int EPI>

@@ -267,91 +267,102 @@ __device__ __forceinline__ void reconstruct_row2(cplx<T> (&u)[9]) {
             -(u[0].re * u[4].im + u[0].im * u[4].re - (u[1].re * u[3].im + u[1].im * u[3].re))};
 }
 
+// Link record of one site: NC complex numbers (9, or the first two rows = 6
+// with compression) of ESZ bytes each, stored as NFULL 16-byte planes and,
+// when the record is not a multiple of 16 bytes, one TAIL-byte plane:
+//   FP64 18: 9 x 16 B     FP64 12: 6 x 16 B
+//   FP32 18: 4 x 16 B + 8 B      FP32 12: 3 x 16 B
+//   FP16 18: 2 x 16 B + 4 B      FP16 12: 1 x 16 B + 8 B
+// Plane c of a (parity, mu) block starts at c * 16 * Vh, the tail plane at
+// NFULL * 16 * Vh; a site's bytes sit at index i within each plane.
+template <int P, bool R12>
+struct LinkLayout {
+    static constexpr int ESZ = P == LQ_F64 ? 16 : P == LQ_F32 ? 8 : 4;
+    static constexpr int NC = R12 ? 6 : 9;
+    static constexpr int BYTES = NC * ESZ;
+    static constexpr int NFULL = BYTES / 16;
+    static constexpr int TAIL = BYTES % 16;  // 0, 4 or 8
+    static constexpr int WORDS = BYTES / 4;
+};
+
+template <int P, bool R12>
+struct RawLink {
+    uint32_t w[LinkLayout<P, R12>::WORDS];
+};
+
+template <int P, bool R12>
+__device__ __forceinline__ void raw_load(RawLink<P, R12>& r, const char* __restrict__ blk, int Vh, int i) {
+    using LL = LinkLayout<P, R12>;
+#pragma unroll
+    for (int c = 0; c < LL::NFULL; ++c) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(blk) + (size_t)c * Vh + i);
+        r.w[4 * c] = v.x;
+        r.w[4 * c + 1] = v.y;
+        r.w[4 * c + 2] = v.z;
+        r.w[4 * c + 3] = v.w;
+    }
+    const char* tail = blk + (size_t)LL::NFULL * 16 * Vh;
+    if constexpr (LL::TAIL == 8) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2*>(tail) + i);
+        r.w[4 * LL::NFULL] = v.x;
+        r.w[4 * LL::NFULL + 1] = v.y;
+    } else if constexpr (LL::TAIL == 4) {
+        r.w[4 * LL::NFULL] = __ldg(reinterpret_cast<const uint32_t*>(tail) + i);
+    }
+}
+
 template <int P, bool R12, typename T>
-__device__ __forceinline__ void load_link(const char* __restrict__ blk, int Vh, int i, cplx<T> (&u)[9]) {
-    if constexpr (P == LQ_F64) {
-        const double2* q = reinterpret_cast<const double2*>(blk);
-        constexpr int n = R12 ? 6 : 9;
+__device__ __forceinline__ void raw_unpack(const RawLink<P, R12>& r, cplx<T> (&u)[9]) {
+    using LL = LinkLayout<P, R12>;
 #pragma unroll
-        for (int k = 0; k < n; ++k) {
-            double2 v = __ldg(q + (size_t)k * Vh + i);
+    for (int k = 0; k < LL::NC; ++k) {
+        if constexpr (P == LQ_F64) {
+            u[k] = {(T)__hiloint2double((int)r.w[4 * k + 1], (int)r.w[4 * k]),
+                    (T)__hiloint2double((int)r.w[4 * k + 3], (int)r.w[4 * k + 2])};
+        } else if constexpr (P == LQ_F32) {
+            u[k] = {(T)__uint_as_float(r.w[2 * k]), (T)__uint_as_float(r.w[2 * k + 1])};
+        } else {
+            const float2 v = h2f(r.w[k], std::integral_constant<int, P>());
             u[k] = {(T)v.x, (T)v.y};
-        }
-    } else if constexpr (P == LQ_F32) {
-        if constexpr (R12) {
-            const float4* q = reinterpret_cast<const float4*>(blk);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                float4 v = __ldg(q + (size_t)k * Vh + i);
-                u[2 * k] = {(T)v.x, (T)v.y};
-                u[2 * k + 1] = {(T)v.z, (T)v.w};
-            }
-        } else {
-            const float2* q = reinterpret_cast<const float2*>(blk);
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                float2 v = __ldg(q + (size_t)k * Vh + i);
-                u[k] = {(T)v.x, (T)v.y};
-            }
-        }
-    } else {
-        std::integral_constant<int, P> tag;
-        if constexpr (R12) {
-            const uint2* q = reinterpret_cast<const uint2*>(blk);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                uint2 v = __ldg(q + (size_t)k * Vh + i);
-                float2 a = h2f(v.x, tag), b = h2f(v.y, tag);
-                u[2 * k] = {a.x, a.y};
-                u[2 * k + 1] = {b.x, b.y};
-            }
-        } else {
-            const uint32_t* q = reinterpret_cast<const uint32_t*>(blk);
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                float2 a = h2f(__ldg(q + (size_t)k * Vh + i), tag);
-                u[k] = {a.x, a.y};
-            }
         }
     }
     if constexpr (R12) reconstruct_row2(u);
 }
 
+template <int P, bool R12, typename T>
+__device__ __forceinline__ void load_link(const char* __restrict__ blk, int Vh, int i, cplx<T> (&u)[9]) {
+    RawLink<P, R12> r;
+    raw_load(r, blk, Vh, i);
+    raw_unpack<P, R12, T>(r, u);
+}
+
 template <int P, bool R12>
 __device__ __forceinline__ void store_link(char* __restrict__ blk, int Vh, int i, const cplx<double> (&u)[9]) {
-    if constexpr (P == LQ_F64) {
-        double2* q = reinterpret_cast<double2*>(blk);
-        constexpr int n = R12 ? 6 : 9;
+    using LL = LinkLayout<P, R12>;
+    RawLink<P, R12> r;
 #pragma unroll
-        for (int k = 0; k < n; ++k) q[(size_t)k * Vh + i] = make_double2(u[k].re, u[k].im);
-    } else if constexpr (P == LQ_F32) {
-        if constexpr (R12) {
-            float4* q = reinterpret_cast<float4*>(blk);
-#pragma unroll
-            for (int k = 0; k < 3; ++k)
-                q[(size_t)k * Vh + i] = make_float4((float)u[2 * k].re, (float)u[2 * k].im, (float)u[2 * k + 1].re,
-                                                    (float)u[2 * k + 1].im);
+    for (int k = 0; k < LL::NC; ++k) {
+        if constexpr (P == LQ_F64) {
+            r.w[4 * k] = (uint32_t)__double2loint(u[k].re);
+            r.w[4 * k + 1] = (uint32_t)__double2hiint(u[k].re);
+            r.w[4 * k + 2] = (uint32_t)__double2loint(u[k].im);
+            r.w[4 * k + 3] = (uint32_t)__double2hiint(u[k].im);
+        } else if constexpr (P == LQ_F32) {
+            r.w[2 * k] = __float_as_uint((float)u[k].re);
+            r.w[2 * k + 1] = __float_as_uint((float)u[k].im);
         } else {
-            float2* q = reinterpret_cast<float2*>(blk);
-#pragma unroll
-            for (int k = 0; k < 9; ++k) q[(size_t)k * Vh + i] = make_float2((float)u[k].re, (float)u[k].im);
+            r.w[k] = f2h((float)u[k].re, (float)u[k].im, std::integral_constant<int, P>());
         }
-    } else {
-        std::integral_constant<int, P> tag;
-        if constexpr (R12) {
-            uint2* q = reinterpret_cast<uint2*>(blk);
+    }
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                uint2 v;
-                v.x = f2h((float)u[2 * k].re, (float)u[2 * k].im, tag);
-                v.y = f2h((float)u[2 * k + 1].re, (float)u[2 * k + 1].im, tag);
-                q[(size_t)k * Vh + i] = v;
-            }
-        } else {
-            uint32_t* q = reinterpret_cast<uint32_t*>(blk);
-#pragma unroll
-            for (int k = 0; k < 9; ++k) q[(size_t)k * Vh + i] = f2h((float)u[k].re, (float)u[k].im, tag);
-        }
+    for (int c = 0; c < LL::NFULL; ++c)
+        reinterpret_cast<uint4*>(blk)[(size_t)c * Vh + i] =
+            make_uint4(r.w[4 * c], r.w[4 * c + 1], r.w[4 * c + 2], r.w[4 * c + 3]);
+    char* tail = blk + (size_t)LL::NFULL * 16 * Vh;
+    if constexpr (LL::TAIL == 8) {
+        reinterpret_cast<uint2*>(tail)[i] = make_uint2(r.w[4 * LL::NFULL], r.w[4 * LL::NFULL + 1]);
+    } else if constexpr (LL::TAIL == 4) {
+        reinterpret_cast<uint32_t*>(tail)[i] = r.w[4 * LL::NFULL];
     }
 }
 
@@ -425,65 +436,6 @@ __device__ __forceinline__ void raw_unpack(const RawSpinor<P>& r, cplx<T> (&s)[1
         }
         nrm = r.n;
     }
-}
-
-template <int P, bool R12>
-struct RawLink {
-    // words of one link in its storage form
-    static constexpr int n64 = (P == LQ_F64) ? (R12 ? 6 : 9) : 0;
-    static constexpr int n32x4 = (P == LQ_F32 && R12) ? 3 : 0;
-    static constexpr int n32x2 = (P == LQ_F32 && !R12) ? 9 : 0;
-    static constexpr int n16x4 = (P >= LQ_F16 && R12) ? 3 : 0;
-    static constexpr int n16x2 = (P >= LQ_F16 && !R12) ? 9 : 0;
-    double2 d[n64 ? n64 : 1];
-    float4 f4[n32x4 ? n32x4 : 1];
-    float2 f2[n32x2 ? n32x2 : 1];
-    uint2 h4[n16x4 ? n16x4 : 1];
-    uint32_t h2[n16x2 ? n16x2 : 1];
-};
-
-template <int P, bool R12>
-__device__ __forceinline__ void raw_load(RawLink<P, R12>& r, const char* __restrict__ blk, int Vh, int i) {
-    using RL = RawLink<P, R12>;
-#pragma unroll
-    for (int k = 0; k < RL::n64; ++k) r.d[k] = __ldg(reinterpret_cast<const double2*>(blk) + (size_t)k * Vh + i);
-#pragma unroll
-    for (int k = 0; k < RL::n32x4; ++k) r.f4[k] = __ldg(reinterpret_cast<const float4*>(blk) + (size_t)k * Vh + i);
-#pragma unroll
-    for (int k = 0; k < RL::n32x2; ++k) r.f2[k] = __ldg(reinterpret_cast<const float2*>(blk) + (size_t)k * Vh + i);
-#pragma unroll
-    for (int k = 0; k < RL::n16x4; ++k) r.h4[k] = __ldg(reinterpret_cast<const uint2*>(blk) + (size_t)k * Vh + i);
-#pragma unroll
-    for (int k = 0; k < RL::n16x2; ++k) r.h2[k] = __ldg(reinterpret_cast<const uint32_t*>(blk) + (size_t)k * Vh + i);
-}
-
-template <int P, bool R12, typename T>
-__device__ __forceinline__ void raw_unpack(const RawLink<P, R12>& r, cplx<T> (&u)[9]) {
-    using RL = RawLink<P, R12>;
-#pragma unroll
-    for (int k = 0; k < RL::n64; ++k) u[k] = {(T)r.d[k].x, (T)r.d[k].y};
-#pragma unroll
-    for (int k = 0; k < RL::n32x4; ++k) {
-        u[2 * k] = {(T)r.f4[k].x, (T)r.f4[k].y};
-        u[2 * k + 1] = {(T)r.f4[k].z, (T)r.f4[k].w};
-    }
-#pragma unroll
-    for (int k = 0; k < RL::n32x2; ++k) u[k] = {(T)r.f2[k].x, (T)r.f2[k].y};
-    if constexpr (P >= LQ_F16) {
-        std::integral_constant<int, P> tag;
-#pragma unroll
-        for (int k = 0; k < RL::n16x4; ++k) {
-            float2 a = h2f(r.h4[k].x, tag), b = h2f(r.h4[k].y, tag);
-            u[2 * k] = {a.x, a.y};
-            u[2 * k + 1] = {b.x, b.y};
-        }
-#pragma unroll
-        for (int k = 0; k < RL::n16x2; ++k) {
-            float2 a = h2f(r.h2[k], tag);
-            u[k] = {a.x, a.y};
-        }
-    }
-    if constexpr (R12) reconstruct_row2(u);
 }
 
 // ----------------------------------------------------- spin projection
