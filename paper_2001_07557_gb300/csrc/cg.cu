@@ -259,6 +259,62 @@ int block_apply(void* ctx, char* out, const char* in) {
     return apply_normal(c->h, *c->og, LQ_F32, out, in, c->t, c->tmp, c->s);
 }
 
+// FP32 residuals of the middle level are accurate to roughly this relative size.
+constexpr double kMiddleTol = 1e-5;
+
+// A e = rhs to relative tolerance `target` with an FP32 defect correction:
+// e, rhs FP32; each pass solves A d = r with the low-precision inner CG to
+// max(itol, what is still needed), adds d to e, and recomputes r = rhs - A e
+// with FP32 hops.  iters[k] accumulates operator applications.
+int solve_fp32_middle(lq_handle* h, const OpGeom& og, const Ctl& c, int ip, const VecRef& e, const VecRef& rhs,
+                      double target, double itol, int maxiter, cudaStream_t s, int* iters, int* most_out) {
+    const int Vh = h->g.Vh, nr = og.nrhs;
+    void *rp, *dp, *qp, *tp, *tmpp;
+    int rc;
+    if ((rc = ensure_ws(h, 20, og.bytes(h, LQ_F32), &rp)) || (rc = ensure_ws(h, 21, og.bytes(h, LQ_F32), &dp)) ||
+        (rc = ensure_ws(h, 22, og.bytes(h, LQ_F32), &qp)) || (rc = ensure_ws(h, 23, og.bytes(h, LQ_F32), &tp)) ||
+        (rc = ensure_ws(h, 16, (size_t)spinor_site_bytes(LQ_F32) * Vh * nr, &tmpp)))
+        return rc;
+    const VecRef R = og.ref(h, rp, LQ_F32), Dv = og.ref(h, dp, LQ_F32), Q = og.ref(h, qp, LQ_F32);
+    std::vector<double> bb(nr), rr(nr);
+    if ((rc = norms_to_host(h, og, c, rhs, bb.data(), s))) return rc;
+    if (cudaMemsetAsync(e.ptr, 0, og.bytes(h, LQ_F32), s) != cudaSuccess ||
+        cudaMemcpyAsync(R.ptr, rhs.ptr, og.bytes(h, LQ_F32), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return LQ_ERR_CUDA;
+    int used = 0, most = 0;
+    std::vector<double> rel(nr, 1.0);
+    for (int pass = 0; pass < 8 && used < maxiter; ++pass) {
+        double reach = 0.5;
+        for (int k = 0; k < nr; ++k)
+            if (rel[k] > target && rel[k] > 0) reach = std::min(reach, 0.5 * target / rel[k]);
+        if ((rc = run_cg(h, og, c, ip, Dv, R, std::max(itol, reach), maxiter - used, WS_CG0, s))) return rc;
+        int m = 0;
+        for (int k = 0; k < nr; ++k) {
+            iters[k] += c.host[k].iter;
+            m = std::max(m, c.host[k].iter);
+        }
+        used += std::max(m, 1);
+        most += m;
+        if (launch_axpby(e, Dv, 1.0, 1.0, Vh, og.nblk, nr, s) != cudaSuccess) return LQ_ERR_CUDA;
+        // r = rhs - A e in FP32
+        if ((rc = apply_normal(h, og, LQ_F32, Q.ptr, e.ptr, static_cast<char*>(tp), static_cast<char*>(tmpp), s)))
+            return rc;
+        if (launch_axpby(R, rhs, 1.0, 0.0, Vh, og.nblk, nr, s) != cudaSuccess ||
+            launch_axpby(R, Q, -1.0, 1.0, Vh, og.nblk, nr, s) != cudaSuccess)
+            return LQ_ERR_CUDA;
+        if ((rc = norms_to_host(h, og, c, R, rr.data(), s))) return rc;
+        bool done = true;
+        for (int k = 0; k < nr; ++k) {
+            iters[k] += 1;
+            rel[k] = bb[k] > 0 ? std::sqrt(rr[k] / bb[k]) : 0.0;
+            done = done && (rel[k] <= target || !std::isfinite(rel[k]));
+        }
+        if (done) break;
+    }
+    *most_out = most;
+    return LQ_OK;
+}
+
 double default_inner_tol(int prec) {
     switch (prec) {
     case LQ_F32: return 1e-6;
@@ -482,18 +538,29 @@ extern "C" int cg_solve(lq_handle* h, void* x, const void* b, const lq_cg_params
                 }
                 most = bit;
             } else {
-                // inner tolerance: the precision's floor itol, or less work when the outer
-            // target is already within reach (relative to the current residual, with margin)
-            double reach = 0.5;  // the smallest reduction every unfinished right-hand side still needs
-            for (int k = 0; k < og.nrhs; ++k)
-                if (!conv[k] && rel[k] > 0) reach = std::min(reach, 0.5 * cp->tol / rel[k]);
-            const double need = std::max(itol, reach);
-            if ((rc = run_cg(h, og, c, ip, E, RIN, need, cp->maxiter - total_inner, WS_CG0, s))) return rc;
-                for (int k = 0; k < og.nrhs; ++k) {
-                    iters[k] += c.host[k].iter;
-                    most = std::max(most, c.host[k].iter);
-                    if (!conv[k]) outer[k] += 1;
+                // inner tolerance: the precision's floor itol, or less work once the outer
+                // target is within reach (relative to the current residual, with margin)
+                double reach = 0.5;  // the smallest reduction every unfinished right-hand side still needs
+                for (int k = 0; k < og.nrhs; ++k)
+                    if (!conv[k] && rel[k] > 0) reach = std::min(reach, 0.5 * cp->tol / rel[k]);
+                if (ip == LQ_F32) {
+                    const double need = std::max(itol, reach);
+                    if ((rc = run_cg(h, og, c, ip, E, RIN, need, cp->maxiter - total_inner, WS_CG0, s))) return rc;
+                    for (int k = 0; k < og.nrhs; ++k) {
+                        iters[k] += c.host[k].iter;
+                        most = std::max(most, c.host[k].iter);
+                    }
+                } else {
+                    // three precisions: an FP32 defect correction (cheap FP32 residuals) around
+                    // the FP16/BF16 inner CG takes the correction to FP32's reach, so FP64
+                    // residuals are needed only about twice per solve
+                    const double need = std::max(kMiddleTol, reach);
+                    if ((rc = solve_fp32_middle(h, og, c, ip, E, RIN, need, itol, cp->maxiter - total_inner, s,
+                                                iters.data(), &most)))
+                        return rc;
                 }
+                for (int k = 0; k < og.nrhs; ++k)
+                    if (!conv[k]) outer[k] += 1;
             }
             total_inner += std::max(most, 1);
             if (launch_axpby(X, E, 1.0, 1.0, h->g.Vh, og.nblk, og.nrhs, s) != cudaSuccess) return LQ_ERR_CUDA;
