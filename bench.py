@@ -548,18 +548,19 @@ def other_configs(lqcd, torch):
     V = int(np.prod(dims))
     U = inputs.gauge_field(dims, "smooth", seed=1003)
     res = {}
-    for r12 in (False, True):
+    for r12, hp in ((False, 1), (True, 1), (False, 2)):
         h = lqcd.lq_create(lqcd.make_params(dims, mass=0.02, compress12=r12), torch.from_numpy(U).cuda())
-        nat = lqcd.LQ_NATIVE | lqcd.LQ_F32
+        nat = lqcd.LQ_NATIVE | hp
         pts = torch.from_numpy(inputs.point_sources(V).astype(np.complex64)).cuda()
         nb = lqcd.lq_field_bytes(h, nat, lqcd.LQ_FULL, 12)
         a_, b_ = (torch.empty(nb, dtype=torch.uint8, device="cuda") for _ in range(2))
         lqcd.lq_convert(h, a_, nat, pts, lqcd.LQ_F32, lqcd.LQ_FULL, 12, stream=st)
+        pname = {1: "f32", 2: "f16"}[hp]
         del pts
         ms = _time(lambda: lqcd.dslash_apply(h, b_, a_, nat, lqcd.LQ_FULL, nrhs=12, stream=st), st, 10, torch)
-        link = 4 * (48 if r12 else 72)
-        byts = V * (link + 12 * 2 * 96)
-        res[f"hop_f32_12rhs_r{12 if r12 else 18}"] = {
+        link = 4 * {(1, True): 48, (1, False): 72, (2, False): 36}[(hp, r12)]
+        byts = V * (link + 12 * 2 * {1: 96, 2: 52}[hp])
+        res[f"hop_{pname}_12rhs_r{12 if r12 else 18}"] = {
             "gflops": FLOP_PER_SITE * V * 12 / (ms * 1e-3) / 1e9, "ms": ms,
             "model_gbs": byts / (ms * 1e-3) / 1e9, "frac_hbm": byts / (ms * 1e-3) / 1e9 / hbm,
             "bytes_model": "links once per site (4 x link) + 12 x (in + out)"}
@@ -649,8 +650,9 @@ def other_configs(lqcd, torch):
     V = int(np.prod(dims))
     U = inputs.gauge_field(dims, "smooth", seed=1004)
     res = {}
-    for pname, p in (("f32", 1), ("f16", 2)):
-        h = lqcd.lq_create(lqcd.make_params(dims, Ls=Ls, M5=1.8, mf=0.01, compress12=True),
+    for pname, p in (("f32", 1), ("f16", 2), ("bf16", 3)):
+        # 18-real links: the Ls = 16 slices share every link load
+        h = lqcd.lq_create(lqcd.make_params(dims, Ls=Ls, M5=1.8, mf=0.01, compress12=False),
                            torch.from_numpy(U).cuda())
         nat = lqcd.LQ_NATIVE | p
         nb = lqcd.lq_field_bytes(h, nat, five_d=True)
@@ -658,15 +660,15 @@ def other_configs(lqcd, torch):
         lqcd.lq_convert(h, a_, nat, torch.from_numpy(inputs.gaussian_spinor(V, seed=2004, nrhs=Ls)).cuda(),
                         lqcd.LQ_F64, five_d=True, stream=st)
         ms = _time(lambda: lqcd.dwf_dslash_apply(h, b_, a_, nat, False, stream=st), st, 20, torch)
-        sp = {1: 96, 2: 52}[p]
-        byts = V * (4 * {1: 48, 2: 24}[p] + Ls * 2 * sp)  # minimum: links once per 4-d site, 5-d in once, out once
-        res[f"dwf_{pname}_r12"] = {"gflops_4d": FLOP_PER_SITE * V * Ls / (ms * 1e-3) / 1e9, "ms": ms,
+        sp = {1: 96, 2: 52, 3: 52}[p]
+        byts = V * (4 * {1: 72, 2: 36, 3: 36}[p] + Ls * 2 * sp)  # minimum: links once per 4-d site, 5-d in once, out once
+        res[f"dwf_{pname}_r18"] = {"gflops_4d": FLOP_PER_SITE * V * Ls / (ms * 1e-3) / 1e9, "ms": ms,
                                    "model_gbs": byts / (ms * 1e-3) / 1e9,
                                    "frac_hbm": byts / (ms * 1e-3) / 1e9 / hbm,
                                    "extra_5d_flop_per_site": 96}
         lqcd.lq_destroy(h)
     # CG on D_dw^dag D_dw: FP32 alone to 1e-8, and FP64 refinement around FP32 inner solves to 1e-10
-    h = lqcd.lq_create(lqcd.make_params(dims, Ls=Ls, M5=1.8, mf=0.01, compress12=True), torch.from_numpy(U).cuda())
+    h = lqcd.lq_create(lqcd.make_params(dims, Ls=Ls, M5=1.8, mf=0.01, compress12=False), torch.from_numpy(U).cuda())
     eta = torch.from_numpy(inputs.gaussian_spinor(V, seed=2004, nrhs=Ls)).cuda()
     b = torch.empty_like(eta)
     lqcd.dwf_dslash_apply(h, b, eta, lqcd.LQ_F64, True)

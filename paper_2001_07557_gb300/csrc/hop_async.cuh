@@ -120,6 +120,36 @@ __device__ __forceinline__ void smem_link(const unsigned char* stage, int t, cpl
     raw_unpack<P, R12, float>(r, u);
 }
 
+// staged FP16/BF16 spinor as 12 packed complex words + norm
+template <int P, int NT>
+__device__ __forceinline__ void smem_words_spinor(const unsigned char* slot, int t, uint32_t (&w)[12], float& nrm) {
+    using St = AsyncStage<P, false, NT>;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const uint4 v = *reinterpret_cast<const uint4*>(slot + St::SP_OFF + (k * NT + t) * 16);
+        w[4 * k] = v.x;
+        w[4 * k + 1] = v.y;
+        w[4 * k + 2] = v.z;
+        w[4 * k + 3] = v.w;
+    }
+    nrm = *reinterpret_cast<const float*>(slot + St::NRM_OFF + t * 4);
+}
+
+// staged FP16/BF16 18-real link as 9 packed complex words
+template <int P, int NT>
+__device__ __forceinline__ void smem_words_link(const unsigned char* stage, int t, uint32_t (&w)[9]) {
+    using St = AsyncStage<P, false, NT>;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const uint4 v = *reinterpret_cast<const uint4*>(stage + St::LK_OFF + (c * NT + t) * 16);
+        w[4 * c] = v.x;
+        w[4 * c + 1] = v.y;
+        w[4 * c + 2] = v.z;
+        w[4 * c + 3] = v.w;
+    }
+    w[8] = *reinterpret_cast<const uint32_t*>(stage + St::LKT_OFF + t * 4);
+}
+
 template <int P, bool R12, int NT, int EPI>
 constexpr int async_smem_bytes(int S) {
     using St = AsyncStage<P, R12, NT>;
@@ -212,6 +242,8 @@ __device__ __forceinline__ void hop_async_site(const HopArgs& a, int i, int rhs,
     constexpr int SF = DAG ? +1 : -1;
     constexpr int SB = -SF;
     constexpr bool NORM = Prec<P>::has_norm;
+    // FP16/BF16 with 18-real links: packed projection and mixed-precision FMAs
+    constexpr bool PACKED = NORM && !R12;
     cplx<T> acc[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = {0.f, 0.f};
@@ -227,14 +259,24 @@ __device__ __forceinline__ void hop_async_site(const HopArgs& a, int i, int rhs,
         const unsigned char* stage = smem + ((D) % S) * St::BYTES;                    \
         cplx<T> s[12], h[6], uh[6], u[9];                                             \
         T nrm;                                                                        \
-        smem_spinor<P, R12, NT>(stage, t, s, nrm);                                    \
-        project<MU, SG>(s, h);                                                        \
-        smem_link<P, R12, NT>(stage, t, u);                                           \
         const bool sgn = FWD ? sf[MU] : sb[MU];                                       \
-        if constexpr (NORM) {                                                         \
+        if constexpr (PACKED) {                                                       \
+            uint32_t sw[12], hw[6], uw[9];                                            \
+            smem_words_spinor<P, NT>(stage, t, sw, nrm);                              \
+            project_h2<P, MU, SG>(sw, hw);                                            \
+            smem_words_link<P, NT>(stage, t, uw);                                     \
+            su3_mul_h2<P, !FWD>(uw, hw, uh);                                          \
+            reconstruct_fma<MU, SG>(acc, uh, sgn ? -nrm : nrm);                       \
+        } else if constexpr (NORM) {                                                  \
+            smem_spinor<P, R12, NT>(stage, t, s, nrm);                                \
+            project<MU, SG>(s, h);                                                    \
+            smem_link<P, R12, NT>(stage, t, u);                                       \
             su3_mul<!FWD>(u, h, uh);                                                  \
             reconstruct_fma<MU, SG>(acc, uh, sgn ? -nrm : nrm);                       \
         } else {                                                                      \
+            smem_spinor<P, R12, NT>(stage, t, s, nrm);                                \
+            project<MU, SG>(s, h);                                                    \
+            smem_link<P, R12, NT>(stage, t, u);                                       \
             if (sgn) {                                                                \
                 _Pragma("unroll") for (int k = 0; k < 6; ++k) h[k] = cneg(h[k]);      \
             }                                                                         \

@@ -523,6 +523,111 @@ __device__ __forceinline__ void reconstruct_fma(cplx<T> (&acc)[12], const cplx<T
     }
 }
 
+// ------------------------------------------ FP16 / BF16 packed arithmetic
+// A complex number held as one 32-bit word: (re, im) = (low, high) 16-bit half.
+// The spin projection of an FP16/BF16 spinor is done on packed halves (one
+// add per component, rounded to 11 / 8 significant bits like the stored
+// inputs), and the SU(3) products multiply the packed halves with the
+// mixed-precision FMA (16-bit inputs, FP32 accumulator): no conversion
+// instructions, all sums in FP32.
+
+template <int P>
+__device__ __forceinline__ uint32_t h2_add(uint32_t a, uint32_t b) {
+    if constexpr (P == LQ_F16) {
+        __half2 r = __hadd2(*reinterpret_cast<__half2*>(&a), *reinterpret_cast<__half2*>(&b));
+        return *reinterpret_cast<uint32_t*>(&r);
+    } else {
+        __nv_bfloat162 r = __hadd2(*reinterpret_cast<__nv_bfloat162*>(&a), *reinterpret_cast<__nv_bfloat162*>(&b));
+        return *reinterpret_cast<uint32_t*>(&r);
+    }
+}
+template <int P>
+__device__ __forceinline__ uint32_t h2_sub(uint32_t a, uint32_t b) {
+    if constexpr (P == LQ_F16) {
+        __half2 r = __hsub2(*reinterpret_cast<__half2*>(&a), *reinterpret_cast<__half2*>(&b));
+        return *reinterpret_cast<uint32_t*>(&r);
+    } else {
+        __nv_bfloat162 r = __hsub2(*reinterpret_cast<__nv_bfloat162*>(&a), *reinterpret_cast<__nv_bfloat162*>(&b));
+        return *reinterpret_cast<uint32_t*>(&r);
+    }
+}
+// i z = (-im, re): swap the halves, flip the sign bit of the new low half
+__device__ __forceinline__ uint32_t h2_mul_i(uint32_t z) { return __byte_perm(z, 0, 0x1032) ^ 0x00008000u; }
+template <int P, int S>
+__device__ __forceinline__ uint32_t h2_adds(uint32_t a, uint32_t b) {
+    if constexpr (S > 0) return h2_add<P>(a, b);
+    else return h2_sub<P>(a, b);
+}
+
+// (1 + S gamma_mu) psi projected on packed halves; same algebra as project()
+template <int P, int MU, int S>
+__device__ __forceinline__ void project_h2(const uint32_t (&s)[12], uint32_t (&h)[6]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const uint32_t p0 = s[c], p1 = s[3 + c], p2 = s[6 + c], p3 = s[9 + c];
+        if constexpr (MU == 0) {
+            h[c] = h2_adds<P, -S>(p0, h2_mul_i(p3));
+            h[3 + c] = h2_adds<P, -S>(p1, h2_mul_i(p2));
+        } else if constexpr (MU == 1) {
+            h[c] = h2_adds<P, -S>(p0, p3);
+            h[3 + c] = h2_adds<P, S>(p1, p2);
+        } else if constexpr (MU == 2) {
+            h[c] = h2_adds<P, -S>(p0, h2_mul_i(p2));
+            h[3 + c] = h2_adds<P, S>(p1, h2_mul_i(p3));
+        } else {
+            h[c] = h2_adds<P, S>(p0, p2);
+            h[3 + c] = h2_adds<P, S>(p1, p3);
+        }
+    }
+}
+
+// c + a * b with 16-bit a, b (packed halves selected by the caller) and FP32 c
+template <int P>
+__device__ __forceinline__ float fma_h(unsigned short a, unsigned short b, float c) {
+    float d;
+    if constexpr (P == LQ_F16) asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(d) : "h"(a), "h"(b), "f"(c));
+    else asm("fma.rn.f32.bf16 %0, %1, %2, %3;" : "=f"(d) : "h"(a), "h"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned short lo16(uint32_t w) { return (unsigned short)(w & 0xffffu); }
+__device__ __forceinline__ unsigned short hi16(uint32_t w) { return (unsigned short)(w >> 16); }
+
+// uh = U h (ADJ: U^dag h) with U (9 packed complex) and h (6 packed complex) in
+// FP16/BF16 and uh in FP32
+template <int P, bool ADJ>
+__device__ __forceinline__ void su3_mul_h2(const uint32_t (&u)[9], const uint32_t (&h)[6], cplx<float> (&uh)[6]) {
+    // copies of h with one part negated: -im (for U h) or -re (for U^dag h)
+    uint32_t hn[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) hn[k] = h[k] ^ (ADJ ? 0x00008000u : 0x80000000u);
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            float re = 0.f, im = 0.f;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const uint32_t w = ADJ ? u[3 * j + i] : u[3 * i + j];
+                const uint32_t x = h[3 * sp + j], xn = hn[3 * sp + j];
+                if constexpr (!ADJ) {
+                    // (a + ib)(c + id) = ac - bd + i(ad + bc)
+                    re = fma_h<P>(lo16(w), lo16(x), re);
+                    re = fma_h<P>(hi16(w), hi16(xn), re);
+                    im = fma_h<P>(lo16(w), hi16(x), im);
+                    im = fma_h<P>(hi16(w), lo16(x), im);
+                } else {
+                    // (a - ib)(c + id) = ac + bd + i(ad - bc)
+                    re = fma_h<P>(lo16(w), lo16(x), re);
+                    re = fma_h<P>(hi16(w), hi16(x), re);
+                    im = fma_h<P>(lo16(w), hi16(x), im);
+                    im = fma_h<P>(hi16(w), lo16(xn), im);
+                }
+            }
+            uh[3 * sp + i] = {re, im};
+        }
+    }
+}
+
 // uh = U h (ADJ: U^dag h), per spin component
 template <bool ADJ, typename T>
 __device__ __forceinline__ void su3_mul(const cplx<T> (&u)[9], const cplx<T> (&h)[6], cplx<T> (&uh)[6]) {
