@@ -187,6 +187,31 @@ class ClockSampler:
                 "samples": len(sm), "source": src}
 
 
+def hop_source_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("hop_async.cuh", "lqcd_internal.cuh", "hop.cuh"):
+        with open(os.path.join(ROOT, "paper_2001_07557_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(config, prec, r12):
+    """DRAM bytes per hop launch from profiles/traffic.txt, if measured on the current kernel sources."""
+    try:
+        cur = hop_source_hash()
+        with open(os.path.join(ROOT, "profiles", "traffic.txt")) as f:
+            for line in f:
+                p = line.split()
+                if len(p) == 5 and not line.startswith("#") and p[0] == config and p[1] == prec and \
+                        int(p[2]) == r12 and p[3] == cur:
+                    return float(p[4])
+    except Exception:
+        return None
+    return None
+
+
 def algorithmic_bytes_per_site(prec, r12, diag):
     """Minimum DRAM bytes of one even-odd hop per output site: 8 links, the
     input spinor once, the output once (+ the diagonal input)."""
@@ -341,14 +366,7 @@ def main():
     launch_ms = statistics.median(step_ms) / 4
     hbm, peak_kind = peaks()
     achieved = bytes_launch / (launch_ms * 1e-3) / 1e9
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", f"traffic_{args.config}_{args.prec}_r{int(r12)}.json")
-    if os.path.exists(tfile):
-        try:
-            traffic = json.load(open(tfile)).get("bytes_per_launch")
-        except Exception:
-            traffic = None
-
+    traffic = measured_traffic(args.config, args.prec, int(r12))
     line = {
         "metric": METRIC, "value": value, "unit": "GFlop/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
