@@ -10,7 +10,7 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA device (GB300, sm_103a)")
-    config.addinivalue_line("markers", "slow: long CPU-side test")
+    config.addinivalue_line("markers", "slow: long test (full-size workloads)")
 
 
 @pytest.fixture(scope="session")

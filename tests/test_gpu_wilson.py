@@ -236,3 +236,73 @@ def test_full_size_32x4_eo_f32_native_sampled():
         got = host(y)[sample]
     want = (-0.5 * oracle.wilson_hop_eo(psi, U, dims, 0))[sample]
     check(got, want, lqcd.LQ_F32)
+
+
+@pytest.mark.slow
+def test_full_size_bench_step_fp16_normal_operator():
+    """The benchmark's step in its launch configuration: 32^4, smooth links,
+    m = 0.01, FP16 storage with per-site norms, 18-real links, Mhat^dag Mhat on
+    a Gaussian even field -- against the oracle on the whole lattice."""
+    dims = (32, 32, 32, 32)
+    V = int(np.prod(dims))
+    U = field(dims, "smooth", 1002)
+    psi = inputs.gaussian_spinor(V // 2, seed=2002)
+    with Handle(dims, U, mass=0.01) as H:
+        nat = lqcd.LQ_NATIVE | lqcd.LQ_F16
+        x = dev(psi)
+        xn, yn, zn = (native_buffer(H.h, lqcd.LQ_F16, lqcd.LQ_EVEN) for _ in range(3))
+        lqcd.lq_convert(H.h, xn, nat, x, lqcd.LQ_F64, lqcd.LQ_EVEN)
+        lqcd.dslash_apply(H.h, yn, xn, nat, lqcd.LQ_SCHUR_EVEN)
+        lqcd.dslash_dag_apply(H.h, zn, yn, nat, lqcd.LQ_SCHUR_EVEN)
+        z = torch.empty_like(x)
+        lqcd.lq_convert(H.h, z, lqcd.LQ_F64, zn, nat, lqcd.LQ_EVEN)
+        got = host(z)
+    want = oracle.apply_normal(oracle.OP_WILSON_EO, psi, U, oracle.params(dims, mass=0.01))
+    # two FP16 operator applications: twice the single-hop tolerance
+    assert rel_err(got, want) < 4e-3
+    assert max_err(got, want) < 1e-2
+
+
+@pytest.mark.slow
+def test_full_size_multi_rhs_fp16_point_sources():
+    """24^3x48, smooth links, m = 0.02, 12 point sources, FP16 full-lattice D in
+    one 12-right-hand-side launch; three of the twelve checked against the oracle."""
+    dims = (24, 24, 24, 48)
+    V = int(np.prod(dims))
+    U = field(dims, "smooth", 1003)
+    src = inputs.point_sources(V)
+    with Handle(dims, U, mass=0.02) as H:
+        nat = lqcd.LQ_NATIVE | lqcd.LQ_F16
+        x = dev(src)
+        xn = native_buffer(H.h, lqcd.LQ_F16, lqcd.LQ_FULL, 12)
+        yn = native_buffer(H.h, lqcd.LQ_F16, lqcd.LQ_FULL, 12)
+        lqcd.lq_convert(H.h, xn, nat, x, lqcd.LQ_F64, lqcd.LQ_FULL, 12)
+        lqcd.dslash_apply(H.h, yn, xn, nat, lqcd.LQ_FULL, nrhs=12)
+        y = torch.empty_like(x)
+        lqcd.lq_convert(H.h, y, lqcd.LQ_F64, yn, nat, lqcd.LQ_FULL, 12)
+        got = host(y)
+    for k in (0, 5, 11):
+        check(got[k], oracle.wilson_dslash(src[k], U, dims, 0.02), lqcd.LQ_F16)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", [lqcd.LQ_F32, lqcd.LQ_F16])
+def test_full_size_domain_wall(prec):
+    """16^4 x Ls = 16, M5 = 1.8, mf = 0.01, smooth links, Gaussian 5-d field,
+    18-real links: the benchmark's domain-wall launch against the oracle."""
+    dims = (16, 16, 16, 16)
+    Ls = 16
+    V = int(np.prod(dims))
+    U = field(dims, "smooth", 1004)
+    psi = inputs.gaussian_spinor(V, seed=2004, nrhs=Ls)
+    with Handle(dims, U, Ls=Ls, M5=1.8, mf=0.01) as H:
+        nat = lqcd.LQ_NATIVE | prec
+        x = dev(psi)
+        xn = native_buffer(H.h, prec, five_d=True)
+        yn = native_buffer(H.h, prec, five_d=True)
+        lqcd.lq_convert(H.h, xn, nat, x, lqcd.LQ_F64, five_d=True)
+        lqcd.dwf_dslash_apply(H.h, yn, xn, nat, False)
+        y = torch.empty_like(x)
+        lqcd.lq_convert(H.h, y, lqcd.LQ_F64, yn, nat, five_d=True)
+        got = host(y)
+    check(got, oracle.dwf_dslash(psi, U, dims, Ls, 1.8, 0.01), prec)
