@@ -616,6 +616,7 @@ def other_configs(lqcd, torch):
         t0 = time.perf_counter()
         rc, stt = lqcd.cg_solve(h, x, b[:n].contiguous(), cp, check=False)
         res[name] = {"status": rc, "seconds": time.perf_counter() - t0, "max_iters": max(z.iters for z in stt),
+                     "max_outer": max(z.outer_iters for z in stt),
                      "max_true_rel_residual": max(z.true_rel_residual for z in stt)}
         del x
     # the same comparison on the even-odd preconditioned system: the point sources sit on an
@@ -625,13 +626,15 @@ def other_configs(lqcd, torch):
     lqcd.dslash_dag_apply(h, be, pts_e, lqcd.LQ_F64, lqcd.LQ_SCHUR_EVEN, nrhs=12)
     del pts_e
     for name, mode, n, inner in [("eo_fp64_cg_1rhs", lqcd.LQ_CG_PLAIN, 1, lqcd.LQ_F32),
-                                 ("eo_mixed_cg_12rhs_batched_f16", lqcd.LQ_CG_MIXED, 12, lqcd.LQ_F16)]:
+                                 ("eo_mixed_cg_12rhs_batched_f16", lqcd.LQ_CG_MIXED, 12, lqcd.LQ_F16),
+                                 ("eo_block_cg_12rhs_f32", lqcd.LQ_CG_BLOCK, 12, lqcd.LQ_F32)]:
         x = torch.zeros_like(be[:n])
         cp = lqcd.make_cg_params(lqcd.LQ_OP_WILSON_EO_NORMAL, mode, lqcd.LQ_F64, nrhs=n, tol=1e-10, inner=inner)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         rc, stt = lqcd.cg_solve(h, x, be[:n].contiguous(), cp, check=False)
         res[name] = {"status": rc, "seconds": time.perf_counter() - t0, "max_iters": max(z.iters for z in stt),
+                     "max_outer": max(z.outer_iters for z in stt),
                      "max_true_rel_residual": max(z.true_rel_residual for z in stt)}
         del x
     lqcd.lq_destroy(h)

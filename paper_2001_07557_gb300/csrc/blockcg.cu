@@ -9,9 +9,11 @@
 //            beta = rho^{-1} (R^dag R)_new,  P = R + P beta
 //
 // The block vectors live in FP32 storage (FP32 arithmetic); the N x N Gram
-// matrices are summed in FP64 on the device (per-thread FP64 accumulators,
-// per-block partials, a fixed-order second pass) and the N x N algebra
-// (Cholesky solves) runs in FP64 on the host.  As a mixed-precision solver
+// matrices are summed on the device (FP32 per-thread sums, FP64 lane, warp
+// and block reductions in a fixed order) and the N x N algebra (Cholesky
+// solves) runs in FP64 on the host.  Every block kernel reads each column
+// once per call (tiles of all N columns staged in shared memory); P is
+// updated in place.  As a mixed-precision solver
 // the block CG is the inner solve of the FP64 defect-correction loop in
 // cg.cu: it stops when every column's residual has dropped by the inner
 // tolerance, or when Delta stops being numerically positive definite (the
@@ -29,125 +31,316 @@ namespace lq {
 
 namespace {
 
-constexpr int kGT = 128;  // threads per block of the block kernels
+// Block vectors are N columns of FP32 native fields; column j is a contiguous
+// array of M float4 (2 complex numbers each) at base + j * stride4 float4s.
+// Every block kernel below walks tiles of kTE consecutive float4 of all N
+// columns: the CTA stages the tile of each input matrix in shared memory with
+// cp.async (one read of every column from memory), then warp w < ceil(N/2)
+// works on the output columns w and N-1-w, lane l on the tile elements l and
+// l + 32.  Blocks have a whole number of kTE-thread groups (see block_threads).
+constexpr int kTE = 64;
+constexpr int kGrid = 152 * 4;  // grid of the block kernels (partials sized for it)
+constexpr int kGramStages = 3;
 
-// G[i][j] partials: sum over the block's sites of <A_i(x), B_j(x)>.
-// grid = (site blocks, N); thread = (site, i); the N B-spinors of a site are
-// re-read from L1 by the N threads that share the site.
-template <int P>
-__global__ void __launch_bounds__(kGT) gram_partial_kernel(const char* A, const char* B, size_t stride, long nsites,
-                                                           int Vh, int N, double2* partial) {
-    const int i = blockIdx.y;
-    double2 acc[kMaxBlockRhs];
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    const int n = valid ? 16 : 0;  // 0: zero-fill, nothing read
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gsrc), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// s[j * pitch + e] = column j, element e0 + e (zero past M)
+__device__ __forceinline__ void stage_tile(float4* s, const float4* __restrict__ base, size_t stride4, long e0,
+                                           long M, int N, int pitch = kTE) {
+    const int e = threadIdx.x & (kTE - 1);  // blockDim.x is a multiple of kTE
+    const bool ok = e0 + e < M;
+    const float4* src = base + (ok ? e0 + e : 0);
+    for (int j = threadIdx.x / kTE; j < N; j += blockDim.x / kTE)
+        cp_async16(s + j * pitch + e, src + (size_t)j * stride4, ok);
+}
+
+// the output columns of this warp: c0 = w and c1 = N-1-w (if different)
+struct WarpCols {
+    int c0, c1;
+    bool has0, has1;
+};
+__device__ __forceinline__ WarpCols warp_cols(int N) {
+    const int w = threadIdx.x >> 5;
+    WarpCols c;
+    c.c0 = w;
+    c.c1 = N - 1 - w;
+    c.has0 = w < (N + 1) / 2;
+    c.has1 = c.has0 && c.c1 > c.c0;
+    return c;
+}
+
+// for the update kernels: c0 = w, c1 = w + ceil(N/2)
+__device__ __forceinline__ WarpCols warp_cols_split(int N) {
+    const int w = threadIdx.x >> 5, h = (N + 1) / 2;
+    WarpCols c;
+    c.c0 = w;
+    c.c1 = w + h;
+    c.has0 = w < h;
+    c.has1 = c.has0 && c.c1 < N;
+    return c;
+}
+
+// acc += conj(a) * b over the two complex numbers of a float4
+__device__ __forceinline__ void cdot4(float2& acc, const float4 a, const float4 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(a.y, b.y, acc.x);
+    acc.x = fmaf(a.z, b.z, acc.x);
+    acc.x = fmaf(a.w, b.w, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(-a.y, b.x, acc.y);
+    acc.y = fmaf(a.z, b.w, acc.y);
+    acc.y = fmaf(-a.w, b.z, acc.y);
+}
+
+// y += c * x for the two complex numbers of a float4 (c complex)
+__device__ __forceinline__ void cmac4(float4& y, const float2 c, const float4 x) {
+    y.x = fmaf(c.x, x.x, y.x);
+    y.x = fmaf(-c.y, x.y, y.x);
+    y.y = fmaf(c.x, x.y, y.y);
+    y.y = fmaf(c.y, x.x, y.y);
+    y.z = fmaf(c.x, x.z, y.z);
+    y.z = fmaf(-c.y, x.w, y.z);
+    y.w = fmaf(c.x, x.w, y.w);
+    y.w = fmaf(c.y, x.z, y.w);
+}
+
+// partial[blk][i][j] = sum over the block's tiles of <A_i, B_j> (conj on A).
+// The tile of column j sits in shared memory at row j with a pitch of kPad
+// float4 (one float4 of padding spreads the rows over the banks).  Lane
+// (j = l & 15, h = l >> 4) of a warp owns column j and the elements of parity
+// h of each element pair the warp takes; it reads B_j once per element and
+// the N row values A_i as broadcasts, and keeps one complex sum per row.
+// kGramStages tile buffers: the copies of the next tiles are in flight while
+// the current one is multiplied.  Sums in FP32 per thread; the reductions
+// over lanes, warps and blocks in FP64.  The kernel is issue-bound: one
+// shared-memory load per 8 FMA, about 40% of the issue slots used.
+constexpr int kPad = kTE + 1;
+constexpr int kGramThreads = 256;
+
+template <bool SAME>
+__global__ void __launch_bounds__(kGramThreads) block_gram_kernel(const float4* __restrict__ A,
+                                                                  const float4* __restrict__ B, size_t stride4,
+                                                                  long M, int N, double2* partial) {
+    extern __shared__ float4 sm[];
+    const size_t buf = (size_t)(SAME ? 1 : 2) * N * kPad;  // float4 per tile buffer
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int j = lane & 15, h = lane >> 4;
+    const bool act = j < N;
+    float2 acc[kMaxBlockRhs];
 #pragma unroll
-    for (int j = 0; j < kMaxBlockRhs; ++j) acc[j] = make_double2(0.0, 0.0);
-    for (long s = (long)blockIdx.x * kGT + threadIdx.x; s < nsites; s += (long)gridDim.x * kGT) {
-        const int bk = (int)(s / Vh), x = (int)(s - (long)bk * Vh);
-        const size_t blk = (size_t)bk * spinor_site_bytes(P) * Vh;
-        cplx<float> a[12];
-        load_spinor<P, float>(A + (size_t)i * stride + blk, Vh, x, a);
+    for (int i = 0; i < kMaxBlockRhs; ++i) acc[i] = make_float2(0.f, 0.f);
+    const long step = (long)gridDim.x * kTE;
+    auto stage = [&](long e0, int k) {
+        if (e0 < M) {
+            float4* sA = sm + k * buf;
+            stage_tile(sA, A, stride4, e0, M, N, kPad);
+            if (!SAME) stage_tile(sA + (size_t)N * kPad, B, stride4, e0, M, N, kPad);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");  // one group per tile (maybe empty)
+    };
 #pragma unroll
-        for (int j = 0; j < kMaxBlockRhs; ++j) {
-            if (j < N) {
-                cplx<float> b[12];
-                load_spinor<P, float>(B + (size_t)j * stride + blk, Vh, x, b);
-                float re = 0.f, im = 0.f;
+    for (int k = 0; k < kGramStages - 1; ++k) stage((long)blockIdx.x * kTE + k * step, k);
+    int k = 0;
+    for (long e0 = (long)blockIdx.x * kTE; e0 < M; e0 += step) {
+        stage(e0 + (kGramStages - 1) * step, (k + kGramStages - 1) % kGramStages);
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(kGramStages - 1) : "memory");  // tile e0 has landed
+        __syncthreads();
+        const float4* sA = sm + k * buf;
+        const float4* sB = SAME ? sA : sA + (size_t)N * kPad;
+        for (int q = w; q < kTE / 2; q += nw) {
+            const int e = 2 * q + h;
+            const float4 bv = act ? sB[j * kPad + e] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                for (int k = 0; k < 12; ++k) {
-                    re = fmaf(a[k].re, b[k].re, re);
-                    re = fmaf(a[k].im, b[k].im, re);
-                    im = fmaf(a[k].re, b[k].im, im);
-                    im = fmaf(-a[k].im, b[k].re, im);
-                }
-                acc[j].x += re;
-                acc[j].y += im;
+            for (int i = 0; i < kMaxBlockRhs; ++i) {
+                if (i < N) cdot4(acc[i], sA[i * kPad + e], bv);
             }
         }
+        __syncthreads();  // buffer k is refilled by a later iteration's copies
+        k = (k + 1) % kGramStages;
     }
-    // block reduction of the N accumulators: warps, then shared memory
-    __shared__ double2 red[kGT / 32][kMaxBlockRhs];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    // lanes j and j + 16 -> warp sums in shared memory -> fixed-order sum over warps
+    double2* red = reinterpret_cast<double2*>(sm);  // [warp][i][16]
 #pragma unroll
-    for (int j = 0; j < kMaxBlockRhs; ++j) {
-        if (j < N) {
-            double x = acc[j].x, y = acc[j].y;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                x += __shfl_xor_sync(0xffffffffu, x, o);
-                y += __shfl_xor_sync(0xffffffffu, y, o);
-            }
-            if (lane == 0) red[w][j] = make_double2(x, y);
+    for (int i = 0; i < kMaxBlockRhs; ++i) {
+        if (i < N) {
+            double x = acc[i].x, y = acc[i].y;
+            x += __shfl_xor_sync(0xffffffffu, x, 16);
+            y += __shfl_xor_sync(0xffffffffu, y, 16);
+            if (h == 0) red[((size_t)w * N + i) * 16 + j] = make_double2(x, y);
         }
     }
     __syncthreads();
-    if (threadIdx.x < N) {
-        const int j = threadIdx.x;
-        double2 t = make_double2(0.0, 0.0);
-        for (int q = 0; q < kGT / 32; ++q) {
-            t.x += red[q][j].x;
-            t.y += red[q][j].y;
+    for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
+        const int i = t / N, jj = t - i * N;
+        double2 v = make_double2(0.0, 0.0);
+        for (int q = 0; q < nw; ++q) {
+            const double2 r = red[((size_t)q * N + i) * 16 + jj];
+            v.x += r.x;
+            v.y += r.y;
         }
-        partial[((size_t)blockIdx.x * N + i) * N + j] = t;
+        partial[(size_t)blockIdx.x * N * N + t] = v;
     }
 }
 
-// G = sum over blocks of the partials (fixed order); one thread per entry.
+// G = sum over blocks of the partials: one warp per entry, lanes stride over
+// the blocks, then a fixed shuffle tree (the same order on every call).
 __global__ void gram_final_kernel(const double2* partial, int nblk, int N, double2* G) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (e >= N * N) return;
-    double2 t = make_double2(0.0, 0.0);
-    for (int b = 0; b < nblk; ++b) {
+    double x = 0.0, y = 0.0;
+    for (int b = lane; b < nblk; b += 32) {
         const double2 v = partial[(size_t)b * N * N + e];
-        t.x += v.x;
-        t.y += v.y;
+        x += v.x;
+        y += v.y;
     }
-    G[e] = t;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
+    }
+    if (lane == 0) G[e] = make_double2(x, y);
 }
 
-// Y_j = cy * Y_j + sum_k M[k][j] X_k  and, if X2/Y2 are given, Y2_j = Y2_j + sum_k M2[k][j] X2_k
-// with the same matrix (M2 = -M handled by sign2).  thread = (site, j).
-template <int P>
-__global__ void __launch_bounds__(kGT) block_axpy_kernel(char* Y, const char* X, float cy, char* Y2, const char* X2,
-                                                         float sign2, const float2* M, size_t stride, long nsites,
-                                                         int Vh, int N) {
-    const int j = blockIdx.y;
-    __shared__ float2 m[kMaxBlockRhs];
-    if (threadIdx.x < N) m[threadIdx.x] = M[threadIdx.x * N + j];
-    __syncthreads();
-    for (long s = (long)blockIdx.x * kGT + threadIdx.x; s < nsites; s += (long)gridDim.x * kGT) {
-        const int bk = (int)(s / Vh), x = (int)(s - (long)bk * Vh);
-        const size_t blk = (size_t)bk * spinor_site_bytes(P) * Vh;
-        cplx<float> y[12], y2[12];
-        if (cy != 0.f) {
-            load_spinor<P, float>(Y + (size_t)j * stride + blk, Vh, x, y);
+// X_j += sum_k P_k a[k][j],  R_j -= sum_k Q_k a[k][j]   (a: N x N, row-major, complex)
+__global__ void __launch_bounds__(32 * ((kMaxBlockRhs + 1) / 2)) block_update_kernel(
+    float4* __restrict__ X, const float4* __restrict__ P, float4* __restrict__ R, const float4* __restrict__ Q,
+    size_t stride4, long M, int N, const float2* __restrict__ a) {
+    extern __shared__ float4 sm[];
+    float4* sP = sm;
+    float4* sQ = sm + (size_t)N * kTE;
+    float2* sa = reinterpret_cast<float2*>(sm + (size_t)2 * N * kTE);
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) sa[e] = a[e];
+    const int lane = threadIdx.x & 31;
+    const WarpCols wc = warp_cols_split(N);
+    const int j0 = wc.c0, j1 = wc.c1;
+    const bool has0 = wc.has0, has1 = wc.has1;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (long e0 = (long)blockIdx.x * kTE; e0 < M; e0 += (long)gridDim.x * kTE) {
+        stage_tile(sP, P, stride4, e0, M, N);
+        stage_tile(sQ, Q, stride4, e0, M, N);
+        float4 x[2][2], r[2][2];
 #pragma unroll
-            for (int c = 0; c < 12; ++c) y[c] = {cy * y[c].re, cy * y[c].im};
-        } else {
-#pragma unroll
-            for (int c = 0; c < 12; ++c) y[c] = {0.f, 0.f};
+        for (int u = 0; u < 2; ++u) {
+            const long ge = e0 + lane + 32 * u;
+            const bool ok = has0 && ge < M;
+            x[0][u] = ok ? X[(size_t)j0 * stride4 + ge] : z4;
+            r[0][u] = ok ? R[(size_t)j0 * stride4 + ge] : z4;
+            x[1][u] = ok && has1 ? X[(size_t)j1 * stride4 + ge] : z4;
+            r[1][u] = ok && has1 ? R[(size_t)j1 * stride4 + ge] : z4;
         }
-        if (Y2) load_spinor<P, float>(Y2 + (size_t)j * stride + blk, Vh, x, y2);
-        for (int k = 0; k < N; ++k) {
-            const float2 mk = m[k];
-            cplx<float> v[12];
-            load_spinor<P, float>(X + (size_t)k * stride + blk, Vh, x, v);
+        cp_async_wait_all();
+        __syncthreads();
 #pragma unroll
-            for (int c = 0; c < 12; ++c) cmac(y[c], cplx<float>{mk.x, mk.y}, v[c]);
-            if (Y2) {
-                load_spinor<P, float>(X2 + (size_t)k * stride + blk, Vh, x, v);
-                const cplx<float> m2 = {sign2 * mk.x, sign2 * mk.y};
+        for (int k = 0; k < kMaxBlockRhs; ++k) {
+            if (k < N && has0) {
+                const float2 c0 = sa[k * N + j0];
+                const float2 c1 = has1 ? sa[k * N + j1] : make_float2(0.f, 0.f);
+                const float2 m0 = make_float2(-c0.x, -c0.y), m1 = make_float2(-c1.x, -c1.y);
 #pragma unroll
-                for (int c = 0; c < 12; ++c) cmac(y2[c], m2, v[c]);
+                for (int u = 0; u < 2; ++u) {
+                    const float4 p = sP[k * kTE + lane + 32 * u];
+                    const float4 q = sQ[k * kTE + lane + 32 * u];
+                    cmac4(x[0][u], c0, p);
+                    cmac4(x[1][u], c1, p);
+                    cmac4(r[0][u], m0, q);
+                    cmac4(r[1][u], m1, q);
+                }
             }
         }
-        store_spinor<P, float>(Y + (size_t)j * stride + blk, Vh, x, y);
-        if (Y2) store_spinor<P, float>(Y2 + (size_t)j * stride + blk, Vh, x, y2);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const long ge = e0 + lane + 32 * u;
+            if (has0 && ge < M) {
+                X[(size_t)j0 * stride4 + ge] = x[0][u];
+                R[(size_t)j0 * stride4 + ge] = r[0][u];
+                if (has1) {
+                    X[(size_t)j1 * stride4 + ge] = x[1][u];
+                    R[(size_t)j1 * stride4 + ge] = r[1][u];
+                }
+            }
+        }
+        __syncthreads();
     }
 }
 
-int block_grid(long nsites) {
-    const long want = (nsites + kGT - 1) / kGT;
-    return (int)std::min<long>(want, 152L * 4);
+// P_j = R_j + sum_k P_k b[k][j], in place: a tile of every column of P is in
+// shared memory before any of it is overwritten, and tiles are disjoint.
+__global__ void __launch_bounds__(32 * ((kMaxBlockRhs + 1) / 2)) block_pupdate_kernel(
+    float4* __restrict__ P, const float4* __restrict__ R, size_t stride4, long M, int N, const float2* __restrict__ b) {
+    extern __shared__ float4 sm[];
+    float4* sP = sm;
+    float2* sb = reinterpret_cast<float2*>(sm + (size_t)N * kTE);
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) sb[e] = b[e];
+    const int lane = threadIdx.x & 31;
+    const WarpCols wc = warp_cols_split(N);
+    const int j0 = wc.c0, j1 = wc.c1;
+    const bool has0 = wc.has0, has1 = wc.has1;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (long e0 = (long)blockIdx.x * kTE; e0 < M; e0 += (long)gridDim.x * kTE) {
+        stage_tile(sP, P, stride4, e0, M, N);
+        float4 y[2][2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const long ge = e0 + lane + 32 * u;
+            const bool ok = has0 && ge < M;
+            y[0][u] = ok ? R[(size_t)j0 * stride4 + ge] : z4;
+            y[1][u] = ok && has1 ? R[(size_t)j1 * stride4 + ge] : z4;
+        }
+        cp_async_wait_all();
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kMaxBlockRhs; ++k) {
+            if (k < N && has0) {
+                const float2 c0 = sb[k * N + j0];
+                const float2 c1 = has1 ? sb[k * N + j1] : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const float4 p = sP[k * kTE + lane + 32 * u];
+                    cmac4(y[0][u], c0, p);
+                    cmac4(y[1][u], c1, p);
+                }
+            }
+        }
+        __syncthreads();  // every warp has read the tile of P before it is overwritten
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const long ge = e0 + lane + 32 * u;
+            if (has0 && ge < M) {
+                P[(size_t)j0 * stride4 + ge] = y[0][u];
+                if (has1) P[(size_t)j1 * stride4 + ge] = y[1][u];
+            }
+        }
+    }
+}
+
+// grid of a block kernel: every SM gets the same number of resident blocks
+// (a partial second wave would leave most SMs idle at the end), at most kGrid
+template <typename K>
+int block_grid(long M, K kern, int threads, size_t smem) {
+    const long want = (M + kTE - 1) / kTE;
+    int per_sm = 0, dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1, sms = 152;
+    const long resident = std::min<long>((long)per_sm * sms, kGrid);
+    return (int)std::min<long>(want, resident);
+}
+
+// threads of the block kernels: one warp per pair of columns, rounded up to
+// whole kTE-thread groups (the staging loop assigns one tile element per thread)
+int block_threads(int N) {
+    const int warps = (N + 1) / 2;
+    return kTE * ((32 * warps + kTE - 1) / kTE);
 }
 
 using cd = std::complex<double>;
@@ -189,48 +382,68 @@ bool chol_solve(const std::vector<cd>& H, const std::vector<cd>& Y, std::vector<
 
 }  // namespace
 
-int block_cg(const BlockCgOps& ops, char* X, const char* Bv, char* R, char* Pa, char* Pb, char* Q, size_t stride,
-             long nsites, int Vh, int N, double tol, int maxiter, void* ws, double2* hostbuf, cudaStream_t s,
-             int* iters) {
-    if (N < 1 || N > kMaxBlockRhs) return LQ_ERR_ARG;
-    const int nblk = block_grid(nsites);
+int block_cg(const BlockCgOps& ops, char* X, const char* Bv, char* R, char* P, char* Q, size_t stride, long nsites,
+             int N, double tol, int maxiter, void* ws, double2* hostbuf, cudaStream_t s, int* iters) {
+    if (N < 1 || N > kMaxBlockRhs || stride % 16 != 0) return LQ_ERR_ARG;
+    const long M = nsites * (spinor_site_bytes(LQ_F32) / 16);  // float4 per column
+    const size_t stride4 = stride / 16;
+    const int nthr = block_threads(N);
+    const size_t tile = sizeof(float4) * N * kTE, mat = sizeof(float2) * N * N;
+    const size_t gtile = sizeof(float4) * N * kPad;  // Gram tile buffer (padded rows)
     double2* partial = static_cast<double2*>(ws);
-    double2* Gd = partial + (size_t)nblk * N * N;
+    double2* Gd = partial + (size_t)kGrid * N * N;
     float2* Md = reinterpret_cast<float2*>(Gd + N * N);
+    static bool configured = false;  // the Gram of 16 columns takes 100 KB of tile buffers
+    if (!configured) {
+        const int gb = (int)(2 * kGramStages * sizeof(float4) * kMaxBlockRhs * kPad);
+        if (cudaFuncSetAttribute(block_gram_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, gb) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(block_gram_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, gb / 2) !=
+                cudaSuccess)
+            return LQ_ERR_CUDA;
+        configured = true;
+    }
+    const int g_same = block_grid(M, block_gram_kernel<true>, kGramThreads, kGramStages * gtile);
+    const int g_pair = block_grid(M, block_gram_kernel<false>, kGramThreads, 2 * kGramStages * gtile);
+    const int g_upd = block_grid(M, block_update_kernel, nthr, 2 * tile + mat);
+    const int g_pup = block_grid(M, block_pupdate_kernel, nthr, tile + mat);
+    auto f4 = [](const char* q) { return reinterpret_cast<const float4*>(q); };
+    auto w4 = [](char* q) { return reinterpret_cast<float4*>(q); };
     auto gram = [&](const char* A, const char* Bm, std::vector<cd>& G) -> int {
-        dim3 grid(nblk, N);
-        gram_partial_kernel<LQ_F32><<<grid, kGT, 0, s>>>(A, Bm, stride, nsites, Vh, N, partial);
-        gram_final_kernel<<<(N * N + 127) / 128, 128, 0, s>>>(partial, nblk, N, Gd);
+        // tile buffers; the final reduction reuses them ([8 warps][N][16] double2 fit in kGramStages buffers)
+        const int nb = A == Bm ? g_same : g_pair;
+        if (A == Bm)
+            block_gram_kernel<true><<<nb, kGramThreads, kGramStages * gtile, s>>>(f4(A), f4(Bm), stride4, M, N,
+                                                                                 partial);
+        else
+            block_gram_kernel<false><<<nb, kGramThreads, 2 * kGramStages * gtile, s>>>(f4(A), f4(Bm), stride4, M, N,
+                                                                                      partial);
+        gram_final_kernel<<<(N * N + 7) / 8, 256, 0, s>>>(partial, nb, N, Gd);
         if (cudaMemcpyAsync(hostbuf, Gd, sizeof(double2) * N * N, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return LQ_ERR_CUDA;
         G.resize(N * N);
         for (int e = 0; e < N * N; ++e) G[e] = cd(hostbuf[e].x, hostbuf[e].y);
+        if (A == Bm)  // A^H A: make it exactly Hermitian
+            for (int i = 0; i < N; ++i)
+                for (int j = 0; j < i; ++j) G[i * N + j] = std::conj(G[j * N + i]);
         return LQ_OK;
     };
-    auto upload = [&](const std::vector<cd>& M) -> int {
+    auto upload = [&](const std::vector<cd>& Mx) -> int {
         float2* hf = reinterpret_cast<float2*>(hostbuf);
-        for (int e = 0; e < N * N; ++e) hf[e] = make_float2((float)M[e].real(), (float)M[e].imag());
-        return cudaMemcpyAsync(Md, hf, sizeof(float2) * N * N, cudaMemcpyHostToDevice, s) == cudaSuccess
-                   ? LQ_OK : LQ_ERR_CUDA;
-    };
-    auto axpy = [&](char* Y, const char* Xv, float cy, char* Y2, const char* X2, float sign2) -> int {
-        dim3 grid(nblk, N);
-        block_axpy_kernel<LQ_F32><<<grid, kGT, 0, s>>>(Y, Xv, cy, Y2, X2, sign2, Md, stride, nsites, Vh, N);
-        return cudaGetLastError() == cudaSuccess ? LQ_OK : LQ_ERR_CUDA;
+        for (int e = 0; e < N * N; ++e) hf[e] = make_float2((float)Mx[e].real(), (float)Mx[e].imag());
+        return cudaMemcpyAsync(Md, hf, mat, cudaMemcpyHostToDevice, s) == cudaSuccess ? LQ_OK : LQ_ERR_CUDA;
     };
 
     // X = 0, R = B, P = R
     if (cudaMemsetAsync(X, 0, stride * N, s) != cudaSuccess ||
         cudaMemcpyAsync(R, Bv, stride * N, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(Pa, Bv, stride * N, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        cudaMemcpyAsync(P, Bv, stride * N, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return LQ_ERR_CUDA;
     std::vector<cd> rho, rho0, delta, alpha, beta, rhonew;
     int rc = gram(R, R, rho);
     if (rc) return rc;
     rho0 = rho;
-    char* P = Pa;
-    char* Pn = Pb;
     int it = 0;
     for (; it < maxiter; ++it) {
         bool done = true;
@@ -241,17 +454,15 @@ int block_cg(const BlockCgOps& ops, char* X, const char* Bv, char* R, char* Pa, 
         if (!chol_solve(delta, rho, alpha, N)) break;  // block lost rank: hand back to the outer loop
         if ((rc = upload(alpha))) return rc;
         // X += P alpha ; R -= Q alpha
-        if ((rc = axpy(X, P, 1.f, R, Q, -1.f))) return rc;
+        block_update_kernel<<<g_upd, nthr, 2 * tile + mat, s>>>(w4(X), f4(P), w4(R), f4(Q), stride4, M, N, Md);
         if ((rc = gram(R, R, rhonew))) return rc;
         if (!chol_solve(rho, rhonew, beta, N)) {
             ++it;
             break;
         }
         if ((rc = upload(beta))) return rc;
-        // Pn = R + P beta  (R enters with coefficient 1 through the identity trick below)
-        if (cudaMemcpyAsync(Pn, R, stride * N, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return LQ_ERR_CUDA;
-        if ((rc = axpy(Pn, P, 1.f, nullptr, nullptr, 0.f))) return rc;
-        std::swap(P, Pn);
+        // P = R + P beta
+        block_pupdate_kernel<<<g_pup, nthr, tile + mat, s>>>(w4(P), f4(R), stride4, M, N, Md);
         rho = rhonew;
     }
     *iters = it;

@@ -21,12 +21,11 @@ inline size_t block_cg_scratch_bytes(int N) {
 }
 
 // Block CG on A X = B from X = 0 for N columns of FP32 native fields, each
-// `stride` bytes, nsites sites (parity blocks of Vh).  R, Pa, Pb, Q are
+// `stride` bytes (a multiple of 16) holding nsites sites.  R, P, Q are
 // scratch fields of the same shape; ws: block_cg_scratch_bytes(N) device
 // bytes; hostbuf: N*N pinned double2.  Stops when every column's residual is
 // below tol times its start, when the block loses rank, or after maxiter.
-int block_cg(const BlockCgOps& ops, char* X, const char* B, char* R, char* Pa, char* Pb, char* Q, size_t stride,
-             long nsites, int Vh, int N, double tol, int maxiter, void* ws, double2* hostbuf, cudaStream_t s,
-             int* iters);
+int block_cg(const BlockCgOps& ops, char* X, const char* B, char* R, char* P, char* Q, size_t stride, long nsites,
+             int N, double tol, int maxiter, void* ws, double2* hostbuf, cudaStream_t s, int* iters);
 
 }  // namespace lq

@@ -445,14 +445,13 @@ extern "C" int cg_solve(lq_handle* h, void* x, const void* b, const lq_cg_params
         // per right-hand side, or one block CG over all of them)
         const bool block = mode == LQ_CG_BLOCK;
         const int ip = block ? LQ_F32 : cp->inner;
-        const double itol = cp->inner_tol > 0 ? cp->inner_tol : (block ? 1e-5 : default_inner_tol(ip));
+        const double itol = cp->inner_tol > 0 ? cp->inner_tol : (block ? 3e-6 : default_inner_tol(ip));
         BlockCtx bctx{h, &og, nullptr, nullptr, s};
-        void *bws = nullptr, *bR = nullptr, *bPa = nullptr, *bPb = nullptr, *bQ = nullptr;
+        void *bws = nullptr, *bR = nullptr, *bP = nullptr, *bQ = nullptr;
         if (block) {
             void *bt, *btmp;
             if ((rc = ensure_ws(h, WS_CG0 + 0, og.bytes(h, LQ_F32), &bR)) ||
-                (rc = ensure_ws(h, WS_CG0 + 1, og.bytes(h, LQ_F32), &bPa)) ||
-                (rc = ensure_ws(h, WS_CG0 + 2, og.bytes(h, LQ_F32), &bPb)) ||
+                (rc = ensure_ws(h, WS_CG0 + 1, og.bytes(h, LQ_F32), &bP)) ||
                 (rc = ensure_ws(h, WS_CG0 + 3, og.bytes(h, LQ_F32), &bQ)) ||
                 (rc = ensure_ws(h, WS_CG0 + 4, og.bytes(h, LQ_F32), &bt)) ||
                 (rc = ensure_ws(h, 17, block_cg_scratch_bytes(og.nrhs), &bws)) ||
@@ -517,32 +516,48 @@ extern "C" int cg_solve(lq_handle* h, void* x, const void* b, const lq_cg_params
                     if (!conv[k]) status[k] = LQ_ERR_NOT_CONVERGED;
                 break;
             }
-            // inner solve A e = r (FP32 copy of r; finished right-hand sides get r = 0)
-            if (launch_axpby(RIN, R64, 1.0, 0.0, h->g.Vh, og.nblk, og.nrhs, s) != cudaSuccess) return LQ_ERR_CUDA;
+            // inner tolerance: the precision's floor itol, or less work once the outer
+            // target is within reach (relative to the current residual, with margin)
+            double reach = 0.5;  // the smallest reduction every unfinished right-hand side still needs
             for (int k = 0; k < og.nrhs; ++k)
-                if (conv[k] && cudaMemsetAsync(RIN.ptr + k * RIN.rhs_stride, 0, RIN.rhs_stride, s) != cudaSuccess)
-                    return LQ_ERR_CUDA;
+                if (!conv[k] && rel[k] > 0) reach = std::min(reach, 0.5 * cp->tol / rel[k]);
             int most = 0;
             if (block) {
+                // one block CG over the unfinished right-hand sides, moved to the leading
+                // columns of the FP32 block (a finished or zero column would make the block
+                // rank-deficient); its correction is added back column by column
+                std::vector<int> cols;
+                for (int k = 0; k < og.nrhs; ++k)
+                    if (!conv[k]) cols.push_back(k);
+                const int nb = (int)cols.size();
+                auto col = [](const VecRef& v, int k) { return VecRef{v.ptr + k * v.rhs_stride, v.prec, v.rhs_stride}; };
+                for (int m = 0; m < nb; ++m)
+                    if (launch_axpby(col(RIN, m), col(R64, cols[m]), 1.0, 0.0, h->g.Vh, og.nblk, 1, s) != cudaSuccess)
+                        return LQ_ERR_CUDA;
                 if ((rc = ensure_pinned(h, sizeof(double2) * og.nrhs * og.nrhs + 64))) return rc;
+                OpGeom ogb = og;
+                ogb.nrhs = nb;
+                bctx.og = &ogb;
                 BlockCgOps ops{&bctx, block_apply};
                 int bit = 0;
-                rc = block_cg(ops, E.ptr, RIN.ptr, static_cast<char*>(bR), static_cast<char*>(bPa),
-                              static_cast<char*>(bPb), static_cast<char*>(bQ), E.rhs_stride,
-                              (long)og.nblk * h->g.Vh, h->g.Vh, og.nrhs, itol, cp->maxiter - total_inner, bws,
-                              static_cast<double2*>(h->pinned), s, &bit);
+                const double need = std::max(itol, reach);
+                rc = block_cg(ops, E.ptr, RIN.ptr, static_cast<char*>(bR), static_cast<char*>(bP),
+                              static_cast<char*>(bQ), E.rhs_stride, (long)og.nblk * h->g.Vh, nb, need,
+                              cp->maxiter - total_inner, bws, static_cast<double2*>(h->pinned), s, &bit);
                 if (rc) return rc;
-                for (int k = 0; k < og.nrhs; ++k) {
-                    iters[k] += conv[k] ? 0 : bit;
-                    if (!conv[k]) outer[k] += 1;
+                for (int m = 0; m < nb; ++m) {
+                    if (launch_axpby(col(X, cols[m]), col(E, m), 1.0, 1.0, h->g.Vh, og.nblk, 1, s) != cudaSuccess)
+                        return LQ_ERR_CUDA;
+                    iters[cols[m]] += bit;
+                    outer[cols[m]] += 1;
                 }
                 most = bit;
             } else {
-                // inner tolerance: the precision's floor itol, or less work once the outer
-                // target is within reach (relative to the current residual, with margin)
-                double reach = 0.5;  // the smallest reduction every unfinished right-hand side still needs
+                // inner solve A e = r (FP32 copy of r; finished right-hand sides get r = 0)
+                if (launch_axpby(RIN, R64, 1.0, 0.0, h->g.Vh, og.nblk, og.nrhs, s) != cudaSuccess) return LQ_ERR_CUDA;
                 for (int k = 0; k < og.nrhs; ++k)
-                    if (!conv[k] && rel[k] > 0) reach = std::min(reach, 0.5 * cp->tol / rel[k]);
+                    if (conv[k] && cudaMemsetAsync(RIN.ptr + k * RIN.rhs_stride, 0, RIN.rhs_stride, s) != cudaSuccess)
+                        return LQ_ERR_CUDA;
                 if (ip == LQ_F32) {
                     const double need = std::max(itol, reach);
                     if ((rc = run_cg(h, og, c, ip, E, RIN, need, cp->maxiter - total_inner, WS_CG0, s))) return rc;
@@ -561,9 +576,9 @@ extern "C" int cg_solve(lq_handle* h, void* x, const void* b, const lq_cg_params
                 }
                 for (int k = 0; k < og.nrhs; ++k)
                     if (!conv[k]) outer[k] += 1;
+                if (launch_axpby(X, E, 1.0, 1.0, h->g.Vh, og.nblk, og.nrhs, s) != cudaSuccess) return LQ_ERR_CUDA;
             }
             total_inner += std::max(most, 1);
-            if (launch_axpby(X, E, 1.0, 1.0, h->g.Vh, og.nblk, og.nrhs, s) != cudaSuccess) return LQ_ERR_CUDA;
         }
     }
     // native working precision -> user layout

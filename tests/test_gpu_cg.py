@@ -245,3 +245,49 @@ def test_block_cg_even_odd_gaussian():
         assert st[k].true_rel_residual < 1e-10
         x_or, _, _, _ = oracle.cg(oracle.OP_WILSON_EO, be[k], U, prm, 1e-12)
         assert rel_err(xg[k], x_or) < 1e-7
+
+
+@pytest.mark.parametrize("nrhs", [1, 3, 16])
+def test_block_cg_ragged_tiles_and_sizes(nrhs):
+    """Block sizes 1, 3 (odd: one warp owns a single column) and 16 (the
+    largest) on a lattice whose field length is not a whole number of tiles."""
+    dims = (6, 2, 2, 6)
+    V = int(np.prod(dims))
+    m = 0.1
+    U = inputs.gauge_field(dims, "random", seed=1007)
+    b = inputs.gaussian_spinor(V, seed=2007, nrhs=nrhs)
+    prm = oracle.params(dims, mass=m)
+    with Handle(dims, U, mass=m) as H:
+        bd = dev(b)
+        xd = torch.zeros_like(bd)
+        cp = lqcd.make_cg_params(lqcd.LQ_OP_WILSON_NORMAL, lqcd.LQ_CG_BLOCK, lqcd.LQ_F64, nrhs=nrhs, tol=1e-10)
+        rc, st = lqcd.cg_solve(H.h, xd, bd, cp)
+        xg = host(xd)
+    assert rc == 0
+    for k in range(nrhs):
+        assert st[k].true_rel_residual < 1e-10
+        x_or, _, _, _ = oracle.cg(oracle.OP_WILSON, b[k], U, prm, 1e-12)
+        assert rel_err(xg[k], x_or) < 1e-7
+
+
+def test_block_cg_zero_column_is_left_out():
+    """A zero right-hand side inside the block: its solution is zero and the
+    other columns still converge (the block holds only unfinished columns)."""
+    dims = (4, 4, 2, 4)
+    V = int(np.prod(dims))
+    m = 0.1
+    U = inputs.gauge_field(dims, "random", seed=1008)
+    b = inputs.gaussian_spinor(V, seed=2008, nrhs=4)
+    b[2] = 0
+    with Handle(dims, U, mass=m) as H:
+        bd = dev(b)
+        xd = torch.full_like(bd, 7.0)
+        cp = lqcd.make_cg_params(lqcd.LQ_OP_WILSON_NORMAL, lqcd.LQ_CG_BLOCK, lqcd.LQ_F64, nrhs=4, tol=1e-10)
+        rc, st = lqcd.cg_solve(H.h, xd, bd, cp)
+        xg = host(xd)
+    assert rc == 0
+    assert np.all(xg[2] == 0) and st[2].iters == 0
+    prm = oracle.params(dims, mass=m)
+    for k in (0, 1, 3):
+        assert st[k].true_rel_residual < 1e-10
+        assert rel_err(oracle.apply_normal(oracle.OP_WILSON, xg[k], U, prm), b[k]) < 1e-9
