@@ -40,6 +40,8 @@ struct AsyncStage {
     static constexpr int LKT_OFF = LK_OFF + L::LK16 * 16 * NT;
     static constexpr int BYTES = ((LKT_OFF + L::LKT * NT) + 15) / 16 * 16;
     static constexpr int SPIN_BYTES = ((L::SP_CH * 16 + (L::NORM ? 4 : 0)) * NT + 15) / 16 * 16;
+    // half spinor (spins 0,1 or 2,3): FP32 3 x 16 B; FP16/BF16 16 + 8 B + norm
+    static constexpr int HALF_BYTES = (((L::NORM ? 28 : 48)) * NT + 15) / 16 * 16;
 };
 
 // issue the copies of one spinor (all chunks + norm) into a spinor slot
@@ -66,6 +68,54 @@ __device__ __forceinline__ void async_link(unsigned char* stage, const char* __r
     if constexpr (L::LKT > 0)
         __pipeline_memcpy_async(stage + St::LKT_OFF + t * L::LKT,
                                 blk + (size_t)L::LK16 * 16 * Vh + (size_t)site * L::LKT, L::LKT);
+}
+
+// issue the copies of the upper (spins 0,1) or lower (spins 2,3) half of a
+// spinor into a half slot.  FP32: planes 0-2 or 3-5.  FP16/BF16 (3 planes of
+// 4 complex): upper = plane 0 + the first 8 bytes of plane 1, lower = the last
+// 8 bytes of plane 1 + plane 2.
+template <int P, bool R12, int NT, bool UPPER>
+__device__ __forceinline__ void async_half_spinor(unsigned char* slot, const char* __restrict__ blk, int Vh, int site,
+                                                  int t) {
+    using L = AsyncLayout<P, R12>;
+    if constexpr (!L::NORM) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            __pipeline_memcpy_async(slot + (k * NT + t) * 16, blk + ((size_t)(UPPER ? k : 3 + k) * Vh + site) * 16, 16);
+    } else {
+        __pipeline_memcpy_async(slot + t * 16, blk + ((size_t)(UPPER ? 0 : 2) * Vh + site) * 16, 16);
+        __pipeline_memcpy_async(slot + 16 * NT + t * 8, blk + ((size_t)Vh + site) * 16 + (UPPER ? 0 : 8), 8);
+        __pipeline_memcpy_async(slot + 24 * NT + t * 4, blk + (size_t)48 * Vh + (size_t)site * 4, 4);
+    }
+}
+
+// read a staged half spinor back: 6 complex in spin-colour order of its half
+template <int P, bool R12, int NT, bool UPPER>
+__device__ __forceinline__ void smem_half_spinor(const unsigned char* slot, int t, cplx<float> (&s)[6], float& nrm) {
+    using L = AsyncLayout<P, R12>;
+    if constexpr (!L::NORM) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float4 v = *reinterpret_cast<const float4*>(slot + (k * NT + t) * 16);
+            s[2 * k] = {v.x, v.y};
+            s[2 * k + 1] = {v.z, v.w};
+        }
+        nrm = 1.f;
+    } else {
+        std::integral_constant<int, P> tag;
+        const uint4 v = *reinterpret_cast<const uint4*>(slot + t * 16);
+        const uint2 w = *reinterpret_cast<const uint2*>(slot + 16 * NT + t * 8);
+        const float2 q0 = h2f(v.x, tag), q1 = h2f(v.y, tag), q2 = h2f(v.z, tag), q3 = h2f(v.w, tag);
+        const float2 r0 = h2f(w.x, tag), r1 = h2f(w.y, tag);
+        const int a = UPPER ? 0 : 2, b = UPPER ? 4 : 0;  // where the 16-byte and the 8-byte parts go
+        s[a + 0] = {q0.x, q0.y};
+        s[a + 1] = {q1.x, q1.y};
+        s[a + 2] = {q2.x, q2.y};
+        s[a + 3] = {q3.x, q3.y};
+        s[b + 0] = {r0.x, r0.y};
+        s[b + 1] = {r1.x, r1.y};
+        nrm = *reinterpret_cast<const float*>(slot + 24 * NT + t * 4);
+    }
 }
 
 // read one staged spinor back (unscaled values + norm)
@@ -153,15 +203,26 @@ __device__ __forceinline__ void smem_words_link(const unsigned char* stage, int 
 template <int P, bool R12, int NT, int EPI>
 constexpr int async_smem_bytes(int S) {
     using St = AsyncStage<P, R12, NT>;
-    return S * St::BYTES + (EPI >= EPI_DIAG ? St::SPIN_BYTES : 0) + (EPI == EPI_DWF ? 2 * St::SPIN_BYTES : 0);
+    return S * St::BYTES + (EPI >= EPI_DIAG ? St::SPIN_BYTES : 0) + (EPI == EPI_DWF ? 2 * St::HALF_BYTES : 0);
 }
 
-// launch configuration per storage precision: threads per block, stages
+// launch configuration per storage precision: threads per block, stages.
+// Fewer stages leave room for more resident blocks; on 32^4 (one rhs) and
+// 24^3x48 (12 rhs) FP32 is fastest with 2 stages and FP16/BF16 with 3
+// (FP32 3 -> 2: 12 rhs 652 -> 626 us; FP16 4 -> 3: 437 -> 414 us, 37.5 -> 37.0 us).
 template <int P>
 struct AsyncCfg {
     static constexpr int NT = kHopThreads;
-    static constexpr int S = (P == LQ_F32) ? 3 : 4;
+    static constexpr int S = (P == LQ_F32) ? 2 : 3;
 };
+
+// stages of the domain-wall variant: its three extra spinor slots cost shared
+// memory, and two stages keep more blocks resident per SM (measured on
+// 16^4 x 16: FP32 112 -> 98 us, FP16 72 -> 60 us against 3 and 4 stages)
+template <int P, int EPI>
+constexpr int async_stages() {
+    return EPI == EPI_DWF ? 2 : AsyncCfg<P>::S;
+}
 
 // One output site (checkerboard index i < Vh, right-hand side rhs, parity p):
 // the staged 8-direction gather and the epilogue, result in o (not stored).
@@ -229,8 +290,10 @@ __device__ __forceinline__ void hop_async_site(const HopArgs& a, int i, int rhs,
         const bool wrap_dn = DAG ? (sl == 0) : (sl + 1 == Ls);
         c_up = wrap_up ? (T)a.mf : (T)-1;
         c_dn = wrap_dn ? (T)a.mf : (T)-1;
-        async_spinor<P, R12, NT>(extra + St::SPIN_BYTES, a.x[p] + (size_t)s_up * a.x_rhs, g.Vh, i, t);
-        async_spinor<P, R12, NT>(extra + 2 * St::SPIN_BYTES, a.x[p] + (size_t)s_dn * a.x_rhs, g.Vh, i, t);
+        // only P+ psi(s_up) (spins 0,1) and P- psi(s_dn) (spins 2,3) are needed
+        async_half_spinor<P, R12, NT, true>(extra + St::SPIN_BYTES, a.x[p] + (size_t)s_up * a.x_rhs, g.Vh, i, t);
+        async_half_spinor<P, R12, NT, false>(extra + St::SPIN_BYTES + St::HALF_BYTES,
+                                             a.x[p] + (size_t)s_dn * a.x_rhs, g.Vh, i, t);
     }
     __pipeline_commit();
 #pragma unroll
@@ -309,17 +372,17 @@ __device__ __forceinline__ void hop_async_site(const HopArgs& a, int i, int rhs,
         }
     }
     if constexpr (EPI == EPI_DWF) {
-        cplx<T> su[12], sd[12];
+        cplx<T> su[6], sd[6];
         T nu, nd;
-        smem_spinor<P, R12, NT>(extra + St::SPIN_BYTES, t, su, nu);
-        smem_spinor<P, R12, NT>(extra + 2 * St::SPIN_BYTES, t, sd, nd);
+        smem_half_spinor<P, R12, NT, true>(extra + St::SPIN_BYTES, t, su, nu);
+        smem_half_spinor<P, R12, NT, false>(extra + St::SPIN_BYTES + St::HALF_BYTES, t, sd, nd);
         const T cu = c_up * nu, cdn = c_dn * nd;
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             o[k].re = fma(cu, su[k].re, o[k].re);
             o[k].im = fma(cu, su[k].im, o[k].im);
-            o[6 + k].re = fma(cdn, sd[6 + k].re, o[6 + k].re);
-            o[6 + k].im = fma(cdn, sd[6 + k].im, o[6 + k].im);
+            o[6 + k].re = fma(cdn, sd[k].re, o[6 + k].re);
+            o[6 + k].im = fma(cdn, sd[k].im, o[6 + k].im);
         }
     }
 }
@@ -367,7 +430,7 @@ __global__ void __launch_bounds__(NT) wilson_hop_async_kernel(const HopArgs a) {
 
 template <int P, bool R12, bool DAG, int EPI, bool RED>
 cudaError_t launch_async_one(const HopArgs& a, cudaStream_t st) {
-    constexpr int NT = AsyncCfg<P>::NT, S = AsyncCfg<P>::S;
+    constexpr int NT = AsyncCfg<P>::NT, S = async_stages<P, EPI>();
     constexpr int smem = async_smem_bytes<P, R12, NT, EPI>(S);
     auto kern = wilson_hop_async_kernel<P, R12, DAG, EPI, NT, S, RED>;
     static bool configured = false;  // attribute set once per process (per instantiation)
