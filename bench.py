@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--config", default="c3_32x4", choices=sorted(CONFIGS))
     ap.add_argument("--prec", default="f16", choices=sorted(PREC_NAMES))
     ap.add_argument("--compress12", type=int, default=0)
+    ap.add_argument("--hops-only", action="store_true",
+                    help="time only the 12-RHS and domain-wall hops (the workload of their ncu captures)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the CPU baseline, e2e and per-precision table (for profiler runs)")
     return ap.parse_args()
@@ -308,6 +310,9 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
+    if args.hops_only:
+        hops_only(args)
+        return
 
     import torch
     import torch.distributed as dist
@@ -523,6 +528,81 @@ def _time(fn, st, reps, torch):
     return e0.elapsed_time(e1) / reps
 
 
+def mrhs_hops(lqcd, torch, st, hbm, U, reps, variants=((False, 1), (True, 1), (False, 2))):
+    """24^3x48, m = 0.02: the full-lattice hop on 12 point sources in one launch."""
+    from paper_2001_07557_gb300 import inputs
+
+    dims = (24, 24, 24, 48)
+    V = int(np.prod(dims))
+    res = {}
+    for r12, hp in variants:
+        h = lqcd.lq_create(lqcd.make_params(dims, mass=0.02, compress12=r12), torch.from_numpy(U).cuda())
+        nat = lqcd.LQ_NATIVE | hp
+        pts = torch.from_numpy(inputs.point_sources(V).astype(np.complex64)).cuda()
+        nb = lqcd.lq_field_bytes(h, nat, lqcd.LQ_FULL, 12)
+        a_, b_ = (torch.empty(nb, dtype=torch.uint8, device="cuda") for _ in range(2))
+        lqcd.lq_convert(h, a_, nat, pts, lqcd.LQ_F32, lqcd.LQ_FULL, 12, stream=st)
+        pname = {1: "f32", 2: "f16"}[hp]
+        del pts
+        ms = _time(lambda: lqcd.dslash_apply(h, b_, a_, nat, lqcd.LQ_FULL, nrhs=12, stream=st), st, reps, torch)
+        link = 4 * {(1, True): 48, (1, False): 72, (2, False): 36}[(hp, r12)]
+        byts = V * (link + 12 * 2 * {1: 96, 2: 52}[hp])
+        res[f"hop_{pname}_12rhs_r{12 if r12 else 18}"] = {
+            "gflops": FLOP_PER_SITE * V * 12 / (ms * 1e-3) / 1e9, "ms": ms,
+            "model_gbs": byts / (ms * 1e-3) / 1e9, "frac_hbm": byts / (ms * 1e-3) / 1e9 / hbm,
+            "bytes_model": "links once per site (4 x link) + 12 x (in + out)"}
+        lqcd.lq_destroy(h)
+        del a_, b_
+    return res
+
+
+def dwf_hops(lqcd, torch, st, hbm, U, reps, precs=(("f32", 1), ("f16", 2), ("bf16", 3))):
+    """16^4 x Ls = 16, M5 = 1.8, mf = 0.01: the domain-wall operator on a Gaussian 5-d field."""
+    from paper_2001_07557_gb300 import inputs
+
+    dims = (16, 16, 16, 16)
+    Ls = 16
+    V = int(np.prod(dims))
+    res = {}
+    for pname, p in precs:
+        # 18-real links: the Ls = 16 slices share every link load
+        h = lqcd.lq_create(lqcd.make_params(dims, Ls=Ls, M5=1.8, mf=0.01, compress12=False),
+                           torch.from_numpy(U).cuda())
+        nat = lqcd.LQ_NATIVE | p
+        nb = lqcd.lq_field_bytes(h, nat, five_d=True)
+        a_, b_ = (torch.empty(nb, dtype=torch.uint8, device="cuda") for _ in range(2))
+        lqcd.lq_convert(h, a_, nat, torch.from_numpy(inputs.gaussian_spinor(V, seed=2004, nrhs=Ls)).cuda(),
+                        lqcd.LQ_F64, five_d=True, stream=st)
+        ms = _time(lambda: lqcd.dwf_dslash_apply(h, b_, a_, nat, False, stream=st), st, reps, torch)
+        sp = {1: 96, 2: 52, 3: 52}[p]
+        byts = V * (4 * {1: 72, 2: 36, 3: 36}[p] + Ls * 2 * sp)  # minimum: links once per 4-d site, 5-d in once, out once
+        res[f"dwf_{pname}_r18"] = {"gflops_4d": FLOP_PER_SITE * V * Ls / (ms * 1e-3) / 1e9, "ms": ms,
+                                   "model_gbs": byts / (ms * 1e-3) / 1e9,
+                                   "frac_hbm": byts / (ms * 1e-3) / 1e9 / hbm,
+                                   "extra_5d_flop_per_site": 96}
+        lqcd.lq_destroy(h)
+    return res
+
+
+def hops_only(args):
+    """The 12-RHS and domain-wall hops alone (FP32 and FP16, 18-real links), each
+    run args.steps times after 3 warm-up launches: the workload of their ncu captures."""
+    import torch
+
+    from paper_2001_07557_gb300 import build as lqbuild
+    from paper_2001_07557_gb300 import inputs, lqcd
+
+    lqbuild.build()
+    hbm, _ = peaks()
+    st = torch.cuda.Stream()
+    U4 = inputs.gauge_field((24, 24, 24, 48), "smooth", seed=1003)
+    out = mrhs_hops(lqcd, torch, st, hbm, U4, args.steps, variants=((False, 1), (False, 2)))
+    del U4
+    U5 = inputs.gauge_field((16, 16, 16, 16), "smooth", seed=1004)
+    out.update(dwf_hops(lqcd, torch, st, hbm, U5, args.steps, precs=(("f32", 1), ("f16", 2))))
+    print(json.dumps({"hops_only": out}))
+
+
 def other_configs(lqcd, torch):
     """The other workloads of the method, one short measurement each."""
     from paper_2001_07557_gb300 import inputs
@@ -579,25 +659,7 @@ def other_configs(lqcd, torch):
     dims = (24, 24, 24, 48)
     V = int(np.prod(dims))
     U = inputs.gauge_field(dims, "smooth", seed=1003)
-    res = {}
-    for r12, hp in ((False, 1), (True, 1), (False, 2)):
-        h = lqcd.lq_create(lqcd.make_params(dims, mass=0.02, compress12=r12), torch.from_numpy(U).cuda())
-        nat = lqcd.LQ_NATIVE | hp
-        pts = torch.from_numpy(inputs.point_sources(V).astype(np.complex64)).cuda()
-        nb = lqcd.lq_field_bytes(h, nat, lqcd.LQ_FULL, 12)
-        a_, b_ = (torch.empty(nb, dtype=torch.uint8, device="cuda") for _ in range(2))
-        lqcd.lq_convert(h, a_, nat, pts, lqcd.LQ_F32, lqcd.LQ_FULL, 12, stream=st)
-        pname = {1: "f32", 2: "f16"}[hp]
-        del pts
-        ms = _time(lambda: lqcd.dslash_apply(h, b_, a_, nat, lqcd.LQ_FULL, nrhs=12, stream=st), st, 10, torch)
-        link = 4 * {(1, True): 48, (1, False): 72, (2, False): 36}[(hp, r12)]
-        byts = V * (link + 12 * 2 * {1: 96, 2: 52}[hp])
-        res[f"hop_{pname}_12rhs_r{12 if r12 else 18}"] = {
-            "gflops": FLOP_PER_SITE * V * 12 / (ms * 1e-3) / 1e9, "ms": ms,
-            "model_gbs": byts / (ms * 1e-3) / 1e9, "frac_hbm": byts / (ms * 1e-3) / 1e9 / hbm,
-            "bytes_model": "links once per site (4 x link) + 12 x (in + out)"}
-        lqcd.lq_destroy(h)
-        del a_, b_
+    res = mrhs_hops(lqcd, torch, st, hbm, U, 10)
     # solves to 1e-10 on D^dag D x = D^dag (point source): one FP64 CG, 12 FP64 CGs in one batch,
     # 12 mixed CGs in one batch (FP16 inner), and block CG over the 12 (FP32 inner)
     # 18-real links: with 12 right-hand sides sharing every link load, rebuilding row 3 costs more than it saves
@@ -684,24 +746,7 @@ def other_configs(lqcd, torch):
     Ls = 16
     V = int(np.prod(dims))
     U = inputs.gauge_field(dims, "smooth", seed=1004)
-    res = {}
-    for pname, p in (("f32", 1), ("f16", 2), ("bf16", 3)):
-        # 18-real links: the Ls = 16 slices share every link load
-        h = lqcd.lq_create(lqcd.make_params(dims, Ls=Ls, M5=1.8, mf=0.01, compress12=False),
-                           torch.from_numpy(U).cuda())
-        nat = lqcd.LQ_NATIVE | p
-        nb = lqcd.lq_field_bytes(h, nat, five_d=True)
-        a_, b_ = (torch.empty(nb, dtype=torch.uint8, device="cuda") for _ in range(2))
-        lqcd.lq_convert(h, a_, nat, torch.from_numpy(inputs.gaussian_spinor(V, seed=2004, nrhs=Ls)).cuda(),
-                        lqcd.LQ_F64, five_d=True, stream=st)
-        ms = _time(lambda: lqcd.dwf_dslash_apply(h, b_, a_, nat, False, stream=st), st, 20, torch)
-        sp = {1: 96, 2: 52, 3: 52}[p]
-        byts = V * (4 * {1: 72, 2: 36, 3: 36}[p] + Ls * 2 * sp)  # minimum: links once per 4-d site, 5-d in once, out once
-        res[f"dwf_{pname}_r18"] = {"gflops_4d": FLOP_PER_SITE * V * Ls / (ms * 1e-3) / 1e9, "ms": ms,
-                                   "model_gbs": byts / (ms * 1e-3) / 1e9,
-                                   "frac_hbm": byts / (ms * 1e-3) / 1e9 / hbm,
-                                   "extra_5d_flop_per_site": 96}
-        lqcd.lq_destroy(h)
+    res = dwf_hops(lqcd, torch, st, hbm, U, 20)
     # CG on D_dw^dag D_dw: FP32 alone to 1e-8, and FP64 refinement around FP32 inner solves to 1e-10
     h = lqcd.lq_create(lqcd.make_params(dims, Ls=Ls, M5=1.8, mf=0.01, compress12=False), torch.from_numpy(U).cuda())
     eta = torch.from_numpy(inputs.gaussian_spinor(V, seed=2004, nrhs=Ls)).cuda()
