@@ -9,7 +9,7 @@ of that file; the pins that tie it to the mathematics live in
 
 Arrays are numpy complex128, C-contiguous, in the site-major layouts:
 spinor [V][4][3], half spinor [V/2][4][3] (cb = lexi/2), gauge [V][4][3][3],
-5-d spinor [Ls][V][4][3].
+5-d spinor [Ls][V][4][3], a field of colour matrices [n][3][3].
 """
 from __future__ import annotations
 
@@ -76,6 +76,7 @@ def _configure(L):
     L.orc_apply_normal.restype = i
     L.orc_cg.argtypes = [i, p, p, p, ctypes.POINTER(Params), d, i, i4, ctypes.POINTER(d)]
     L.orc_cg.restype = i
+    L.orc_su3_mul.argtypes = [p, p, p, ctypes.c_long]
     return L
 
 
@@ -221,3 +222,14 @@ def cg(op, b, U, prm: Params, tol, maxiter=100000):
     rc = lib().orc_cg(op, _ptr(x), _ptr(b), _ptr(U), ctypes.byref(prm), float(tol), int(maxiter),
                       ctypes.byref(it), ctypes.byref(res))
     return x, it.value, res.value, rc
+
+
+def su3_mul(A, B):
+    """C[x] = A[x] B[x] for fields of 3x3 complex matrices, shape (n, 3, 3):
+    the lattice-wide product of the paper's SU(3) benchmark (Sec. 3.3, Fig. 4a-c)."""
+    A, B = _c(A), _c(B)
+    if A.shape != B.shape or A.shape[-2:] != (3, 3):
+        raise ValueError("su3_mul takes two (n, 3, 3) arrays of the same shape")
+    C = np.empty_like(A)
+    lib().orc_su3_mul(_ptr(C), _ptr(A), _ptr(B), int(A.size // 9))
+    return C

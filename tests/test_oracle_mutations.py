@@ -39,6 +39,10 @@ MUTANTS = [
     ("domain-wall wall sign", "if (sp == Ls) { sp = 0; cp = mf; }", "if (sp == Ls) { sp = 0; cp = -mf; }",
      ["dwf"]),
     ("CG beta inverted", "double beta = rr_new / rr;", "double beta = rr / rr_new;", ["cg"]),
+    ("SU(3) product with B transposed", "t += a[3 * i + k] * b[3 * k + j];", "t += a[3 * i + k] * b[3 * j + k];",
+     ["su3"]),
+    ("SU(3) product in the wrong order", "t += a[3 * i + k] * b[3 * k + j];", "t += b[3 * i + k] * a[3 * k + j];",
+     ["su3"]),
 ]
 
 
@@ -56,6 +60,8 @@ def run_pin(kind, orc):
         pins.test_dwf_free_field_closed_form(orc)
     elif kind == "cg":
         pins.test_cg_matches_dense_lu_on_4444(orc)
+    elif kind == "su3":
+        pins.test_su3_mul_matches_numpy_and_group_closure(orc)
 
 
 @pytest.mark.parametrize("name,old,new,kinds", MUTANTS, ids=[m[0] for m in MUTANTS])

@@ -356,6 +356,33 @@ def test_dwf_cg_small(orc):
     assert rel(orc.apply_op(orc.OP_DWF, x, U, prm), eta) < 1e-8
 
 
+# ------------------------------------------------------------ SU(3) x SU(3)
+
+
+def test_su3_mul_matches_numpy_and_group_closure(orc):
+    """The lattice-wide product C(x) = A(x) B(x) against numpy's matmul (an
+    independent library routine) on general complex matrices, the identity on
+    either side, (AB)^dag = B^dag A^dag, and closure of SU(3): a product of
+    special unitary matrices is special unitary.  Catches transposed or
+    conjugated operands, a swapped product order and dropped terms."""
+    rng = np.random.default_rng(11)
+    n = 37
+    A = rng.normal(size=(n, 3, 3)) + 1j * rng.normal(size=(n, 3, 3))
+    B = rng.normal(size=(n, 3, 3)) + 1j * rng.normal(size=(n, 3, 3))
+    C = orc.su3_mul(A, B)
+    assert np.max(np.abs(C - A @ B)) < 1e-13 * np.max(np.abs(C))
+    eye = np.broadcast_to(np.eye(3), (n, 3, 3))
+    assert np.array_equal(orc.su3_mul(A, eye), A) and np.array_equal(orc.su3_mul(eye, B), B)
+    dag = lambda M: np.conj(np.swapaxes(M, 1, 2))  # noqa: E731
+    assert np.max(np.abs(dag(C) - orc.su3_mul(dag(B), dag(A)))) < 1e-13 * np.max(np.abs(C))
+    U = inputs.gauge_field((2, 2, 2, 2), "random", seed=7).reshape(-1, 3, 3)
+    W = inputs.gauge_field((2, 2, 2, 2), "smooth", seed=8).reshape(-1, 3, 3)
+    P = orc.su3_mul(U, W)
+    assert np.max(np.abs(dag(P) @ P - np.eye(3))) < 1e-13
+    assert np.max(np.abs(np.linalg.det(P) - 1)) < 1e-13
+    assert orc.su3_mul(np.zeros((0, 3, 3)), np.zeros((0, 3, 3))).shape == (0, 3, 3)
+
+
 # ------------------------------------------------------------- generators
 
 
