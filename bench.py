@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--config", default="c3_32x4", choices=sorted(CONFIGS))
     ap.add_argument("--prec", default="f16", choices=sorted(PREC_NAMES))
     ap.add_argument("--compress12", type=int, default=0)
+    ap.add_argument("--su3-only", action="store_true",
+                    help="time only the lattice-wide SU(3) product sweep (the workload of its ncu capture)")
     ap.add_argument("--hops-only", action="store_true",
                     help="time only the 12-RHS and domain-wall hops (the workload of their ncu captures)")
     ap.add_argument("--no-extras", action="store_true",
@@ -312,6 +314,9 @@ def main():
         return
     if args.hops_only:
         hops_only(args)
+        return
+    if args.su3_only:
+        su3_only(args)
         return
 
     import torch
@@ -584,6 +589,50 @@ def dwf_hops(lqcd, torch, st, hbm, U, reps, precs=(("f32", 1), ("f16", 2), ("bf1
     return res
 
 
+def su3_sweep(lqcd, torch, st, hbm, reps, sides=(8, 16, 24, 32, 48)):
+    """The paper's SU(3) matrix-matrix benchmark (Sec. 3.3, Fig. 4a-c): C(x) =
+    A(x) B(x) on one colour matrix per site of an L^4 lattice, FP32 and FP64,
+    random SU(3) factors.  198 flop per product (27 complex multiplies, 18
+    complex adds); 3 x 72 B (FP32) or 3 x 144 B (FP64) of algorithmic traffic."""
+    from paper_2001_07557_gb300 import inputs
+
+    base = inputs.gauge_field((4, 4, 4, 4), "random", seed=1000).reshape(-1, 3, 3)  # 1024 SU(3) matrices
+    out = {}
+    for pname, fmt, dt, mb in (("f32", lqcd.LQ_F32, torch.complex64, 72), ("f64", lqcd.LQ_F64, torch.complex128, 144)):
+        for L in sides:
+            n = L ** 4
+            reps_src = (n + len(base) - 1) // len(base)
+            a = torch.from_numpy(np.tile(base, (reps_src, 1, 1))[:n].copy()).to(dt).cuda()
+            b = torch.roll(a, 1, 0).contiguous()
+            c = torch.empty_like(a)
+            ms = _time(lambda: lqcd.lq_su3_mul(c, a, b, n, fmt, stream=st), st, reps, torch)
+            gbs = 3 * mb * n / (ms * 1e-3) / 1e9
+            e = {"n": n, "us": ms * 1e3, "gflops": 198 * n / (ms * 1e-3) / 1e9, "model_gbs": gbs}
+            if 3 * mb * n < 129e6:
+                e["note"] = "working set fits in L2"
+            if fmt == lqcd.LQ_F32:
+                e["frac_hbm"] = gbs / hbm
+            else:
+                e["frac_fp64_alu"] = e["gflops"] / (FP64_PEAK_TFLOPS * 1e3)
+            out[f"{pname}_L{L}"] = e
+            del a, b, c
+    out["timeouts"] = lqcd.lq_wait_timeouts()
+    return out
+
+
+def su3_only(args):
+    """The SU(3) product sweep alone (the workload of its ncu capture)."""
+    import torch
+
+    from paper_2001_07557_gb300 import build as lqbuild
+    from paper_2001_07557_gb300 import lqcd
+
+    lqbuild.build()
+    hbm, _ = peaks()
+    st = torch.cuda.Stream()
+    print(json.dumps({"su3_mul": su3_sweep(lqcd, torch, st, hbm, args.steps)}))
+
+
 def hops_only(args):
     """The 12-RHS and domain-wall hops alone (FP32 and FP16, 18-real links), each
     run args.steps times after 3 warm-up launches: the workload of their ncu captures."""
@@ -772,6 +821,7 @@ def other_configs(lqcd, torch):
                                             "true_rel_residual": stt[0].true_rel_residual}
     lqcd.lq_destroy(h)
     out["c5_16x4xLs16_dwf"] = res
+    out["su3_mul"] = su3_sweep(lqcd, torch, st, hbm, 20)
     return out
 
 

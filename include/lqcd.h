@@ -232,6 +232,36 @@ int cg_solve(lq_handle *h, void *x, const void *b, const lq_cg_params *cp, lq_cg
 int lq_batch_cg_solve(lq_handle **hs, int nlat, void **xs, const void **bs, const lq_cg_params *cp,
                       lq_cg_stats *stats, void *stream);
 
+/* ---------------------------------------------------- SU(3) x SU(3) */
+
+/*
+ * lq_su3_mul: the lattice-wide colour-matrix product of the paper's SU(3)
+ * matrix-matrix benchmark (Sec. 3.3, Fig. 4a-c):  C[x] = A[x] B[x],
+ * C_ij = sum_k A_ik B_kj, for x = 0 .. n-1.
+ *   - A, B, C: device pointers to n 3x3 complex matrices stored
+ *     [x][row][col] as interleaved {re, im} pairs (the paper's array of
+ *     two-element structures), FP64 (fmt = LQ_F64, 144 bytes per matrix) or
+ *     FP32 (fmt = LQ_F32, 72 bytes).  Each must be 16-byte aligned
+ *     (LQ_ERR_LAYOUT otherwise).  The caller owns all three.
+ *   - C may be the same pointer as A or as B (the product is formed in place
+ *     tile by tile); any other overlap is LQ_ERR_ARG.
+ *   - n = 0 is a no-op; n < 0 or a null pointer with n > 0 is LQ_ERR_ARG.
+ *   - Asynchronous on `stream`.  No handle is needed and nothing is allocated.
+ * Tiles of A and B move to shared memory by bulk asynchronous copies that
+ * complete on shared-memory barriers, and tiles of C leave by bulk stores.
+ * Every wait on a barrier is bounded; a wait that runs out leaves its tile of
+ * C unwritten and is counted (see lq_wait_timeouts).
+ */
+int lq_su3_mul(void *C, const void *A, const void *B, long n, int fmt, void *stream);
+
+/*
+ * lq_wait_timeouts: the number of device-side barrier waits that ran out
+ * since the last call (on the current device), then reset to zero.
+ * Synchronises the device.  A nonzero count means some results of the
+ * kernels that wait on barriers (lq_su3_mul) were not written.
+ */
+int lq_wait_timeouts(unsigned *count);
+
 /* Human-readable text for a status code (static storage). */
 const char *lq_status_string(int status);
 

@@ -26,7 +26,8 @@ STATUS = {0: "LQ_OK", -1: "LQ_ERR_ARG", -2: "LQ_ERR_LAYOUT", -3: "LQ_ERR_CUDA", 
 
 # every function the header declares
 EXPORTS = ["lq_create", "lq_destroy", "lq_field_bytes", "lq_convert", "dslash_apply", "dslash_dag_apply",
-           "dwf_dslash_apply", "lq_dot", "lq_dot_noalloc", "cg_solve", "lq_batch_cg_solve", "lq_status_string"]
+           "dwf_dslash_apply", "lq_dot", "lq_dot_noalloc", "cg_solve", "lq_batch_cg_solve", "lq_su3_mul",
+           "lq_wait_timeouts", "lq_status_string"]
 LQ_DOT_NOALLOC_MAX_RHS = 32
 
 
@@ -76,6 +77,8 @@ def lib():
         L.cg_solve.argtypes = [vp, vp, vp, ctypes.POINTER(lq_cg_params), ctypes.POINTER(lq_cg_stats), vp]
         L.lq_batch_cg_solve.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                         ctypes.POINTER(lq_cg_params), ctypes.POINTER(lq_cg_stats), vp]
+        L.lq_su3_mul.argtypes = [vp, vp, vp, ctypes.c_long, i, vp]
+        L.lq_wait_timeouts.argtypes = [ctypes.POINTER(ctypes.c_uint)]
         L.lq_status_string.argtypes = [i]
         L.lq_status_string.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -195,3 +198,16 @@ def lq_batch_cg_solve(hs, xs, bs, cp: lq_cg_params, stream=None, check=True):
 
 def lq_status_string(status: int) -> str:
     return lib().lq_status_string(status).decode()
+
+
+def lq_su3_mul(C, A, B, n, fmt, stream=None):
+    """C[x] = A[x] B[x] for n 3x3 complex matrices [x][row][col]{re, im},
+    fmt LQ_F64 or LQ_F32 (device pointers or tensors, 16-byte aligned)."""
+    _check(lib().lq_su3_mul(_ptr(C), _ptr(A), _ptr(B), int(n), fmt, _stream(stream)), "lq_su3_mul")
+
+
+def lq_wait_timeouts():
+    """Device-side barrier waits that ran out since the last call (resets the count)."""
+    c = ctypes.c_uint(0)
+    _check(lib().lq_wait_timeouts(ctypes.byref(c)), "lq_wait_timeouts")
+    return c.value

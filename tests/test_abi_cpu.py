@@ -66,3 +66,19 @@ def test_null_arguments_are_rejected_before_any_launch(L):
     assert L.lq_create(None, ctypes.byref(p), None, 0, None) == -1
     assert L.dslash_apply(None, None, None, 0, -1, 1, None) == -1
     assert L.lq_destroy(None) == -1
+
+
+def test_su3_mul_argument_checks_before_any_launch(L):
+    """lq_su3_mul rejects bad arguments before touching the device: the
+    pointers below are never dereferenced."""
+    A, B = 0x10000, 0x20000
+    assert L.lq_su3_mul(0x30000, A, B, -1, 0, None) == -1  # n < 0
+    assert L.lq_su3_mul(0x30000, A, B, 4, 2, None) == -1  # FP16 is not a product format
+    assert L.lq_su3_mul(None, A, B, 4, 0, None) == -1
+    assert L.lq_su3_mul(0x30000, None, B, 4, 1, None) == -1
+    assert L.lq_su3_mul(0x30008, A, B, 4, 0, None) == -2  # C not 16-byte aligned
+    assert L.lq_su3_mul(0x30000, A + 8, B, 4, 1, None) == -2
+    assert L.lq_su3_mul(A + 16, A, B, 4, 0, None) == -1  # C overlaps A without being A
+    assert L.lq_su3_mul(B - 16, A, B, 4, 1, None) == -1  # C's 288 bytes run into B
+    assert L.lq_su3_mul(None, None, None, 0, 0, None) == 0  # n = 0 is a no-op
+    assert L.lq_wait_timeouts(None) == -1
