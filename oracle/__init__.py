@@ -27,6 +27,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 OP_WILSON = 0
 OP_WILSON_EO = 1
 OP_DWF = 2
+OP_DWF_EO = 3
 
 OK = 0
 NOT_CONVERGED = -3
@@ -77,6 +78,15 @@ def _configure(L):
     L.orc_cg.argtypes = [i, p, p, p, ctypes.POINTER(Params), d, i, i4, ctypes.POINTER(d)]
     L.orc_cg.restype = i
     L.orc_su3_mul.argtypes = [p, p, p, ctypes.c_long]
+    L.orc_dwf_m5.argtypes = [p, p, ctypes.c_long, i, d, d, i]
+    L.orc_dwf_m5_inv.argtypes = [p, p, ctypes.c_long, i, d, d, i]
+    L.orc_dwf_m5_inv.restype = i
+    L.orc_dwf_schur.argtypes = [p, p, p, i4, i4, i, d, d, i]
+    L.orc_dwf_schur.restype = i
+    L.orc_dwf_eo_prepare.argtypes = [p, p, p, i4, i4, i, d, d]
+    L.orc_dwf_eo_prepare.restype = i
+    L.orc_dwf_eo_reconstruct.argtypes = [p, p, p, p, i4, i4, i, d, d]
+    L.orc_dwf_eo_reconstruct.restype = i
     return L
 
 
@@ -183,6 +193,52 @@ def dwf_dslash(psi5, U, dims, Ls, M5, mf, bc=(1, 1, 1, -1), dagger=False):
     out = np.empty_like(psi5)
     rc = lib().orc_dwf_dslash(_ptr(out), _ptr(psi5), _ptr(U), _i4(dims), _i4(bc), int(Ls), M5, mf,
                               int(dagger))
+    assert rc == OK, rc
+    return out
+
+
+def dwf_m5(psi5, Ls, M5, mf, dagger=False):
+    """The 4-d-site-local part of D_dw: (5 - M5) psi(s) - P- psi(s+1) - P+ psi(s-1)
+    (walls -> +mf), on a 5-d field [Ls][n][4][3] of any site subset."""
+    psi5 = _c(psi5)
+    out = np.empty_like(psi5)
+    lib().orc_dwf_m5(_ptr(out), _ptr(psi5), int(psi5.size // (12 * Ls)), int(Ls), M5, mf, int(dagger))
+    return out
+
+
+def dwf_m5_inv(psi5, Ls, M5, mf, dagger=False):
+    """(M5)^{-1} psi (dagger: (M5^dag)^{-1}) by dense Gaussian elimination."""
+    psi5 = _c(psi5)
+    out = np.empty_like(psi5)
+    rc = lib().orc_dwf_m5_inv(_ptr(out), _ptr(psi5), int(psi5.size // (12 * Ls)), int(Ls), M5, mf, int(dagger))
+    assert rc == OK, rc
+    return out
+
+
+def dwf_schur(psi5e, U, dims, Ls, M5, mf, bc=(1, 1, 1, -1), dagger=False):
+    """Mhat = M5 - M_eo M5^{-1} M_oe (dagger: its adjoint) on an even 5-d half field [Ls][V/2][4][3]."""
+    psi5e, U = _c(psi5e), _c(U)
+    out = np.empty_like(psi5e)
+    rc = lib().orc_dwf_schur(_ptr(out), _ptr(psi5e), _ptr(U), _i4(dims), _i4(bc), int(Ls), M5, mf, int(dagger))
+    assert rc == OK, rc
+    return out
+
+
+def dwf_eo_prepare(eta5, U, dims, Ls, M5, mf, bc=(1, 1, 1, -1)):
+    """eta_hat_e = eta_e - M_eo M5^{-1} eta_o for a full 5-d source [Ls][V][4][3]."""
+    eta5, U = _c(eta5), _c(U)
+    out = np.empty((Ls, _vol(dims) // 2, 4, 3), dtype=np.complex128)
+    rc = lib().orc_dwf_eo_prepare(_ptr(out), _ptr(eta5), _ptr(U), _i4(dims), _i4(bc), int(Ls), M5, mf)
+    assert rc == OK, rc
+    return out
+
+
+def dwf_eo_reconstruct(x5e, eta5, U, dims, Ls, M5, mf, bc=(1, 1, 1, -1)):
+    """The full 5-d solution: psi_e = x_e, psi_o = M5^{-1} (eta_o - M_oe x_e)."""
+    x5e, eta5, U = _c(x5e), _c(eta5), _c(U)
+    out = np.empty_like(eta5)
+    rc = lib().orc_dwf_eo_reconstruct(_ptr(out), _ptr(x5e), _ptr(eta5), _ptr(U), _i4(dims), _i4(bc), int(Ls),
+                                      M5, mf)
     assert rc == OK, rc
     return out
 

@@ -31,8 +31,18 @@
  *      (D_dw psi)(s) = D_W(-M5) psi(s) + psi(s) - P- psi(s+1) - P+ psi(s-1),
  *    where P- psi(Ls) is read as -mf P- psi(0) and P+ psi(-1) as
  *    -mf P+ psi(Ls-1); D_dw^dag swaps P+ and P- and uses D_W^dag.
- *  - CG (Hestenes-Stiefel) on A x = b with A = K^dag K for K = D, Mhat or D_dw,
+ *  - CG (Hestenes-Stiefel) on A x = b with A = K^dag K for K = D, Mhat, D_dw or
+ *    the domain-wall Mhat,
  *    x0 = 0, stopping when |r|/|b| < tol.
+ *  - Even-odd (4-d parity) Schur complement of the domain-wall operator.  With
+ *    M5 the part of D_dw that stays on a 4-d site,
+ *      (M5 psi)(s) = (5 - M5) psi(s) - P- psi(s+1) - P+ psi(s-1)   (walls as above),
+ *    and M_eo = -1/2 H_eo, M_oe = -1/2 H_oe on every slice:
+ *      Mhat = M5 - M_eo M5^{-1} M_oe   on even 5-d half fields,
+ *      Mhat^dag = M5^dag - M_oe^dag (M5^dag)^{-1} M_eo^dag,
+ *    the source eta_hat_e = eta_e - M_eo M5^{-1} eta_o and the odd half of the
+ *    solution psi_o = M5^{-1} (eta_o - M_oe psi_e).  M5^{-1} is applied by
+ *    Gaussian elimination of M5's dense (4 Ls) x (4 Ls) spin-slice matrix.
  *  - The lattice-wide SU(3) product of the paper's matrix-matrix benchmark
  *    (Sec. 3.3, Fig. 4a-c): C(x) = A(x) B(x) for 3x3 complex matrices stored
  *    [x][row][col] as {re, im} pairs, each entry summed over k = 0, 1, 2 in
@@ -49,7 +59,7 @@
 typedef double complex cplx;
 
 enum { ORC_OK = 0, ORC_ERR_ARG = -1, ORC_ERR_NOMEM = -2, ORC_NOT_CONVERGED = -3 };
-enum { ORC_OP_WILSON = 0, ORC_OP_WILSON_EO = 1, ORC_OP_DWF = 2 };
+enum { ORC_OP_WILSON = 0, ORC_OP_WILSON_EO = 1, ORC_OP_DWF = 2, ORC_OP_DWF_EO = 3 };
 
 typedef struct {
     int dims[4];
@@ -307,6 +317,189 @@ int orc_dwf_dslash(cplx *out, const cplx *in, const cplx *U, const int d[4], con
     return ORC_OK;
 }
 
+/* ------------------------------------------- domain wall, even-odd (4-d) */
+
+/* P+ and P- (dagger: swapped) as dense 4x4 matrices: Pup acts with psi(s+1), Pdn with psi(s-1). */
+static void dwf_projectors(int dagger, cplx Pup[4][4], cplx Pdn[4][4])
+{
+    cplx g5[4][4];
+    orc_gamma(4, g5);
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+            cplx id = (a == b) ? 1.0 : 0.0;
+            cplx pp = 0.5 * (id + g5[a][b]), pm = 0.5 * (id - g5[a][b]);
+            Pup[a][b] = dagger ? pp : pm;
+            Pdn[a][b] = dagger ? pm : pp;
+        }
+}
+
+/* out = M5 in (dagger: M5^dag) on 5-d fields [Ls][nsites][4][3] of any site subset. */
+void orc_dwf_m5(cplx *out, const cplx *in, long nsites, int Ls, double M5, double mf, int dagger)
+{
+    cplx Pup[4][4], Pdn[4][4];
+    dwf_projectors(dagger, Pup, Pdn);
+    long n4 = nsites * SITE_DOF;
+    for (int s = 0; s < Ls; ++s) {
+        cplx *o = out + s * n4;
+        const cplx *v = in + s * n4;
+        for (long i = 0; i < n4; ++i) o[i] = (5.0 - M5) * v[i];
+        int sp = s + 1, sm = s - 1;
+        double cp = -1.0, cm = -1.0;
+        if (sp == Ls) { sp = 0; cp = mf; }
+        if (sm < 0) { sm = Ls - 1; cm = mf; }
+        add_spin(o, cp, Pup, in + sp * n4, nsites);
+        add_spin(o, cm, Pdn, in + sm * n4, nsites);
+    }
+}
+
+/* out = M5^{-1} in (dagger: (M5^dag)^{-1}).  M5 is the same (4 Ls) x (4 Ls)
+   matrix on the (slice, spin) index of every site and colour: it is built from
+   orc_dwf_m5 applied to unit vectors, factorised once by Gaussian elimination
+   with partial pivoting, and solved for every (site, colour). */
+int orc_dwf_m5_inv(cplx *out, const cplx *in, long nsites, int Ls, double M5, double mf, int dagger)
+{
+    if (Ls < 1 || Ls > 64) return ORC_ERR_ARG;
+    const int n = 4 * Ls;
+    cplx *A = calloc((size_t)n * n, sizeof(cplx));
+    cplx *e = calloc((size_t)Ls * SITE_DOF, sizeof(cplx));
+    cplx *col = malloc((size_t)Ls * SITE_DOF * sizeof(cplx));
+    int *piv = malloc((size_t)n * sizeof(int));
+    if (!A || !e || !col || !piv) { free(A); free(e); free(col); free(piv); return ORC_ERR_NOMEM; }
+    /* column j = (s', b) of A: M5 applied to the unit vector at slice s', spin b, colour 0 (one site) */
+    for (int j = 0; j < n; ++j) {
+        memset(e, 0, (size_t)Ls * SITE_DOF * sizeof(cplx));
+        e[(j / 4) * SITE_DOF + (j % 4) * 3] = 1.0;
+        orc_dwf_m5(col, e, 1, Ls, M5, mf, dagger);
+        for (int i = 0; i < n; ++i) A[i * n + j] = col[(i / 4) * SITE_DOF + (i % 4) * 3];
+    }
+    /* LU with partial pivoting, in place */
+    for (int k = 0; k < n; ++k) {
+        int p = k;
+        for (int i = k + 1; i < n; ++i)
+            if (cabs(A[i * n + k]) > cabs(A[p * n + k])) p = i;
+        piv[k] = p;
+        if (p != k)
+            for (int j = 0; j < n; ++j) { cplx t = A[k * n + j]; A[k * n + j] = A[p * n + j]; A[p * n + j] = t; }
+        if (A[k * n + k] == 0) { free(A); free(e); free(col); free(piv); return ORC_ERR_ARG; }
+        for (int i = k + 1; i < n; ++i) {
+            cplx f = A[i * n + k] / A[k * n + k];
+            A[i * n + k] = f;
+            for (int j = k + 1; j < n; ++j) A[i * n + j] -= f * A[k * n + j];
+        }
+    }
+    long n4 = nsites * SITE_DOF;
+#pragma omp parallel for schedule(static)
+    for (long site = 0; site < nsites; ++site) {
+        for (int c = 0; c < 3; ++c) {
+            cplx y[4 * 64];
+            for (int i = 0; i < n; ++i) y[i] = in[(i / 4) * n4 + site * SITE_DOF + (i % 4) * 3 + c];
+            for (int k = 0; k < n; ++k)
+                if (piv[k] != k) { cplx t = y[k]; y[k] = y[piv[k]]; y[piv[k]] = t; }
+            for (int i = 1; i < n; ++i)
+                for (int j = 0; j < i; ++j) y[i] -= A[i * n + j] * y[j];
+            for (int i = n - 1; i >= 0; --i) {
+                for (int j = i + 1; j < n; ++j) y[i] -= A[i * n + j] * y[j];
+                y[i] /= A[i * n + i];
+            }
+            for (int i = 0; i < n; ++i) out[(i / 4) * n4 + site * SITE_DOF + (i % 4) * 3 + c] = y[i];
+        }
+    }
+    free(A);
+    free(e);
+    free(col);
+    free(piv);
+    return ORC_OK;
+}
+
+/* -1/2 H between parities on every slice of a 5-d half field [Ls][V/2][4][3]. */
+static int dwf_hop_eo(cplx *out, const cplx *in, const cplx *U, const int d[4], const int bc[4], int Ls,
+                      int dagger, int out_parity)
+{
+    long nh = orc_volume(d) / 2 * SITE_DOF;
+    for (int s = 0; s < Ls; ++s) {
+        int rc = orc_wilson_hop_eo(out + s * nh, in + s * nh, U, d, bc, 1.0, dagger, out_parity);
+        if (rc != ORC_OK) return rc;
+        for (long i = 0; i < nh; ++i) out[s * nh + i] *= -0.5;
+    }
+    return ORC_OK;
+}
+
+/* Mhat in_e (dagger: Mhat^dag) on even 5-d half fields. */
+int orc_dwf_schur(cplx *out, const cplx *in, const cplx *U, const int d[4], const int bc[4], int Ls, double M5,
+                  double mf, int dagger)
+{
+    long Vh = orc_volume(d) / 2, n5 = (long)Ls * Vh * SITE_DOF;
+    if (Ls < 1 || Ls > 64) return ORC_ERR_ARG;
+    cplx *t = malloc((size_t)n5 * sizeof(cplx)), *u = malloc((size_t)n5 * sizeof(cplx));
+    if (!t || !u) { free(t); free(u); return ORC_ERR_NOMEM; }
+    int rc = dwf_hop_eo(t, in, U, d, bc, Ls, dagger, 1);                        /* t_o = M_oe in_e   */
+    if (rc == ORC_OK) rc = orc_dwf_m5_inv(u, t, Vh, Ls, M5, mf, dagger);         /* u_o = M5^-1 t_o   */
+    if (rc == ORC_OK) rc = dwf_hop_eo(t, u, U, d, bc, Ls, dagger, 0);            /* t_e = M_eo u_o    */
+    if (rc == ORC_OK) {
+        orc_dwf_m5(out, in, Vh, Ls, M5, mf, dagger);                             /* out = M5 in_e     */
+        for (long i = 0; i < n5; ++i) out[i] -= t[i];
+    }
+    free(t);
+    free(u);
+    return rc;
+}
+
+/* a full 5-d field [Ls][V][4][3] <-> the half field [Ls][V/2][4][3] of one parity */
+static void split_parity(cplx *half, const cplx *full, const int d[4], int Ls, int parity, int to_full)
+{
+    long V = orc_volume(d);
+    for (int s = 0; s < Ls; ++s)
+        for (long site = 0; site < V; ++site) {
+            int x[4];
+            site_coords(site, d, x);
+            if (site_parity(x) != parity) continue;
+            cplx *h = half + ((long)s * (V / 2) + site / 2) * SITE_DOF;
+            cplx *f = (cplx *)full + ((long)s * V + site) * SITE_DOF;
+            if (to_full) memcpy(f, h, SITE_DOF * sizeof(cplx));
+            else memcpy(h, f, SITE_DOF * sizeof(cplx));
+        }
+}
+
+/* bhat_e = eta_e - M_eo M5^{-1} eta_o (eta a full 5-d field, bhat_e an even half field). */
+int orc_dwf_eo_prepare(cplx *bhat, const cplx *eta, const cplx *U, const int d[4], const int bc[4], int Ls,
+                       double M5, double mf)
+{
+    long n5 = (long)Ls * orc_volume(d) / 2 * SITE_DOF;
+    cplx *eo = malloc((size_t)n5 * sizeof(cplx)), *u = malloc((size_t)n5 * sizeof(cplx));
+    if (!eo || !u) { free(eo); free(u); return ORC_ERR_NOMEM; }
+    split_parity(eo, eta, d, Ls, 1, 0);
+    split_parity(bhat, eta, d, Ls, 0, 0);
+    int rc = orc_dwf_m5_inv(u, eo, orc_volume(d) / 2, Ls, M5, mf, 0);
+    if (rc == ORC_OK) rc = dwf_hop_eo(eo, u, U, d, bc, Ls, 0, 0);
+    if (rc == ORC_OK)
+        for (long i = 0; i < n5; ++i) bhat[i] -= eo[i];
+    free(eo);
+    free(u);
+    return rc;
+}
+
+/* psi (full 5-d field) from its even half x_e: psi_o = M5^{-1} (eta_o - M_oe x_e). */
+int orc_dwf_eo_reconstruct(cplx *psi, const cplx *xe, const cplx *eta, const cplx *U, const int d[4],
+                           const int bc[4], int Ls, double M5, double mf)
+{
+    long n5 = (long)Ls * orc_volume(d) / 2 * SITE_DOF;
+    cplx *t = malloc((size_t)n5 * sizeof(cplx)), *eo = malloc((size_t)n5 * sizeof(cplx));
+    if (!t || !eo) { free(t); free(eo); return ORC_ERR_NOMEM; }
+    split_parity(eo, eta, d, Ls, 1, 0);
+    int rc = dwf_hop_eo(t, xe, U, d, bc, Ls, 0, 1);
+    if (rc == ORC_OK) {
+        for (long i = 0; i < n5; ++i) eo[i] -= t[i];
+        rc = orc_dwf_m5_inv(t, eo, orc_volume(d) / 2, Ls, M5, mf, 0);
+    }
+    if (rc == ORC_OK) {
+        split_parity((cplx *)xe, psi, d, Ls, 0, 1);
+        split_parity(t, psi, d, Ls, 1, 1);
+    }
+    free(t);
+    free(eo);
+    return rc;
+}
+
 /* ---------------------------------------------------------- normal ops, CG */
 
 static long op_length(int op, const orc_params *p)
@@ -315,10 +508,11 @@ static long op_length(int op, const orc_params *p)
     if (op == ORC_OP_WILSON) return V * SITE_DOF;
     if (op == ORC_OP_WILSON_EO) return V / 2 * SITE_DOF;
     if (op == ORC_OP_DWF) return (long)p->Ls * V * SITE_DOF;
+    if (op == ORC_OP_DWF_EO) return (long)p->Ls * (V / 2) * SITE_DOF;
     return -1;
 }
 
-/* out = K in (dagger: K^dag) for K = D, Mhat or D_dw. */
+/* out = K in (dagger: K^dag) for K = D, Mhat, D_dw or the domain-wall Mhat. */
 int orc_apply_op(int op, cplx *out, const cplx *in, const cplx *U, const orc_params *p, int dagger)
 {
     switch (op) {
@@ -329,6 +523,8 @@ int orc_apply_op(int op, cplx *out, const cplx *in, const cplx *U, const orc_par
         return orc_wilson_schur(out, in, U, p->dims, p->bc, p->mass, p->r, dagger);
     case ORC_OP_DWF:
         return orc_dwf_dslash(out, in, U, p->dims, p->bc, p->Ls, p->M5, p->mf, dagger);
+    case ORC_OP_DWF_EO:
+        return orc_dwf_schur(out, in, U, p->dims, p->bc, p->Ls, p->M5, p->mf, dagger);
     }
     return ORC_ERR_ARG;
 }

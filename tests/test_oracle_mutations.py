@@ -39,6 +39,12 @@ MUTANTS = [
     ("domain-wall wall sign", "if (sp == Ls) { sp = 0; cp = mf; }", "if (sp == Ls) { sp = 0; cp = -mf; }",
      ["dwf"]),
     ("CG beta inverted", "double beta = rr_new / rr;", "double beta = rr / rr_new;", ["cg"]),
+    ("domain-wall Schur complement sign", "for (long i = 0; i < n5; ++i) out[i] -= t[i];",
+     "for (long i = 0; i < n5; ++i) out[i] += t[i];", ["dwf_eo"]),
+    ("domain-wall M5 inverse ignores the dagger", "orc_dwf_m5(col, e, 1, Ls, M5, mf, dagger);",
+     "orc_dwf_m5(col, e, 1, Ls, M5, mf, 0);", ["dwf_eo"]),
+    ("domain-wall source preparation with the wrong sign", "for (long i = 0; i < n5; ++i) bhat[i] -= eo[i];",
+     "for (long i = 0; i < n5; ++i) bhat[i] += eo[i];", ["dwf_eo"]),
     ("SU(3) product with B transposed", "t += a[3 * i + k] * b[3 * k + j];", "t += a[3 * i + k] * b[3 * j + k];",
      ["su3"]),
     ("SU(3) product in the wrong order", "t += a[3 * i + k] * b[3 * k + j];", "t += b[3 * i + k] * a[3 * k + j];",
@@ -60,6 +66,8 @@ def run_pin(kind, orc):
         pins.test_dwf_free_field_closed_form(orc)
     elif kind == "cg":
         pins.test_cg_matches_dense_lu_on_4444(orc)
+    elif kind == "dwf_eo":
+        pins.test_dwf_eo_schur_solve_matches_full_solve(orc)
     elif kind == "su3":
         pins.test_su3_mul_matches_numpy_and_group_closure(orc)
 
