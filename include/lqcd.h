@@ -143,6 +143,31 @@ int dslash_dag_apply(lq_handle *h, void *out, const void *in, int fmt, int parit
 int dwf_dslash_apply(lq_handle *h, void *out, const void *in, int fmt, int dagger, void *stream);
 
 /*
+ * Even-odd (4-d parity) preconditioned domain wall.  The paper does not treat
+ * the domain-wall operator; this is the standard Schur decomposition of D_dw
+ * by 4-d parity.  With M5 the part of D_dw that stays on a 4-d site,
+ *   (M5 psi)(s) = (5 - M5) psi(s) - P- psi(s+1) - P+ psi(s-1)  (walls -> +mf),
+ * and M_eo = -1/2 H_eo, M_oe = -1/2 H_oe (the Wilson hop between parities, on
+ * every slice), D_dw psi = eta is solved on the even sites through
+ *   Mhat = M5 - M_eo M5^{-1} M_oe,   Mhat psi_e = eta_e - M_eo M5^{-1} eta_o,
+ * and psi_o = M5^{-1} (eta_o - M_oe psi_e).
+ * Field layouts: a 5-d half field is Ls half fields of the even parity, slice
+ * after slice ([s][cb][4][3] site-major, or Ls native blocks); lq_field_bytes
+ * and lq_convert handle it as subset LQ_EVEN with nrhs = Ls.  A full 5-d field
+ * is the five_d layout above.  fmt: LQ_F64 or LQ_F32, site-major or native
+ * (FP16/BF16: LQ_ERR_ARG).  All three are asynchronous on `stream` and
+ * reject overlapping buffers (LQ_ERR_ARG); they need lq_params.Ls >= 1.
+ *
+ * dwf_schur_apply: out_e = Mhat in_e (dagger != 0: Mhat^dag in_e), 5-d half fields.
+ * dwf_eo_prepare: bhat_e = eta_e - M_eo M5^{-1} eta_o from a full 5-d source eta.
+ * dwf_eo_reconstruct: the full 5-d solution psi (psi_e = x_e, psi_o as above)
+ *   from the even half x_e and the source eta.
+ */
+int dwf_schur_apply(lq_handle *h, void *out_e, const void *in_e, int fmt, int dagger, void *stream);
+int dwf_eo_prepare(lq_handle *h, void *bhat_e, const void *eta, int fmt, void *stream);
+int dwf_eo_reconstruct(lq_handle *h, void *psi, const void *x_e, const void *eta, int fmt, void *stream);
+
+/*
  * lq_dot: FP64 complex inner products <a, b> = sum_x conj(a(x)) . b(x) of
  * nrhs pairs of fields (layout and precision fmt, sites as in lq_field_bytes;
  * five_d != 0: one 5-d field of Ls slices).  result: DEVICE pointer to
@@ -186,7 +211,9 @@ int lq_dot_noalloc(lq_handle *h, double *result, const void *a, const void *b, i
 enum {
     LQ_OP_WILSON_NORMAL = 0,    /* A = D^dag D on full fields           */
     LQ_OP_WILSON_EO_NORMAL = 1, /* A = Mhat^dag Mhat on even half fields */
-    LQ_OP_DWF_NORMAL = 2        /* A = D_dw^dag D_dw on 5-d fields       */
+    LQ_OP_DWF_NORMAL = 2,       /* A = D_dw^dag D_dw on 5-d fields       */
+    LQ_OP_DWF_EO_NORMAL = 3     /* A = Mhat^dag Mhat on 5-d even half fields (domain-wall Schur
+                                   complement; FP64/FP32, inner precision LQ_F32 only) */
 };
 enum {
     LQ_CG_PLAIN = 0,   /* CG in the precision of fmt (FP64 or FP32) */

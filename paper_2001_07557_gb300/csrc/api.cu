@@ -197,6 +197,98 @@ int native_dwf(lq_handle* h, int prec, char* out, const char* in, bool dag, cuda
     return status_of(launch_hop(prec, a, link_r12(h, prec), dag, EPI_DWF, h->hop_block[prec], st));
 }
 
+// Even-odd domain wall: Mhat = M5 - M_eo M5^{-1} M_oe with M_eo = -1/2 H_eo on
+// every slice (the 5th-dimension index runs as the right-hand-side index of
+// the Wilson hop) and M5 the site-local part of D_dw.
+//   tmp_o = -1/2 H_oe in_e;  tmp_o = M5^{-1} tmp_o;  out_e = M5 in_e + 1/2 H_eo tmp_o,
+// the last as one domain-wall hop launch (its epilogue is exactly M5 in_e).
+// The dagger uses the daggered hop, (M5^dag)^{-1} and M5^dag.
+int native_dwf_schur(lq_handle* h, int prec, char* out_e, const char* in_e, char* tmp, bool dag, cudaStream_t st) {
+    if (prec != LQ_F64 && prec != LQ_F32) return LQ_ERR_ARG;
+    const int Ls = h->p.Ls;
+    const size_t blk = native_block_bytes(h, prec);
+    HopArgs a1;
+    int rc = prep_wilson_block(h, prec, tmp, in_e, 1, Ls, -0.5, &a1, st);
+    if (rc) return rc;
+    a1.skip_stride = 0;  // the slices of one system share the system's skip flag
+    if ((rc = status_of(launch_hop(prec, a1, link_r12(h, prec), dag, EPI_HOP, h->hop_block[prec], st)))) return rc;
+    if (launch_m5inv(prec, tmp, tmp, h->g.Vh, blk, blk, Ls, h->p.M5, h->p.mf, dag, st) != cudaSuccess)
+        return LQ_ERR_CUDA;
+    const char* L;
+    size_t lb;
+    if ((rc = get_links(h, prec, &L, &lb, st))) return rc;
+    HopArgs a = base_args(h, L, lb);
+    a.in[0] = tmp;
+    a.x[0] = in_e;
+    a.out[0] = out_e;
+    a.in_rhs = a.out_rhs = a.x_rhs = blk;
+    a.parity0 = 0;
+    a.nparity = 1;
+    a.nrhs = Ls;
+    a.Ls = Ls;
+    a.mf = h->p.mf;
+    a.c_hop = 0.5;
+    a.c_diag = 5.0 - h->p.M5;
+    set_red(a, h);
+    return status_of(launch_hop(prec, a, link_r12(h, prec), dag, EPI_DWF, h->hop_block[prec], st));
+}
+
+// bhat_e = eta_e - M_eo M5^{-1} eta_o = eta_e + 1/2 H_eo M5^{-1} eta_o  (eta a full 5-d field)
+int native_dwf_prepare(lq_handle* h, int prec, char* bhat_e, const char* eta, char* tmp, cudaStream_t st) {
+    if (prec != LQ_F64 && prec != LQ_F32) return LQ_ERR_ARG;
+    const int Ls = h->p.Ls;
+    const size_t blk = native_block_bytes(h, prec);
+    if (launch_m5inv(prec, tmp, eta + blk, h->g.Vh, blk, 2 * blk, Ls, h->p.M5, h->p.mf, false, st) != cudaSuccess)
+        return LQ_ERR_CUDA;
+    const char* L;
+    size_t lb;
+    int rc = get_links(h, prec, &L, &lb, st);
+    if (rc) return rc;
+    HopArgs a = base_args(h, L, lb);
+    a.in[0] = tmp;
+    a.x[0] = eta;
+    a.out[0] = bhat_e;
+    a.in_rhs = a.out_rhs = blk;
+    a.x_rhs = 2 * blk;
+    a.parity0 = 0;
+    a.nparity = 1;
+    a.nrhs = Ls;
+    a.c_hop = 0.5;
+    a.c_diag = 1.0;
+    a.skip = nullptr;  // a source preparation is never skipped
+    return status_of(launch_hop(prec, a, link_r12(h, prec), false, EPI_DIAG, h->hop_block[prec], st));
+}
+
+// psi_e = x_e;  psi_o = M5^{-1} (eta_o - M_oe x_e) = M5^{-1} (eta_o + 1/2 H_oe x_e)
+int native_dwf_reconstruct(lq_handle* h, int prec, char* psi, const char* x_e, const char* eta, cudaStream_t st) {
+    if (prec != LQ_F64 && prec != LQ_F32) return LQ_ERR_ARG;
+    const int Ls = h->p.Ls;
+    const size_t blk = native_block_bytes(h, prec);
+    const char* L;
+    size_t lb;
+    int rc = get_links(h, prec, &L, &lb, st);
+    if (rc) return rc;
+    HopArgs a = base_args(h, L, lb);
+    a.in[1] = x_e;
+    a.x[1] = eta + blk;
+    a.out[1] = psi + blk;
+    a.in_rhs = blk;
+    a.out_rhs = a.x_rhs = 2 * blk;
+    a.parity0 = 1;
+    a.nparity = 1;
+    a.nrhs = Ls;
+    a.c_hop = 0.5;
+    a.c_diag = 1.0;
+    a.skip = nullptr;
+    if ((rc = status_of(launch_hop(prec, a, link_r12(h, prec), false, EPI_DIAG, h->hop_block[prec], st))))
+        return rc;
+    if (launch_m5inv(prec, psi + blk, psi + blk, h->g.Vh, 2 * blk, 2 * blk, Ls, h->p.M5, h->p.mf, false, st) !=
+            cudaSuccess ||
+        cudaMemcpy2DAsync(psi, 2 * blk, x_e, blk, blk, Ls, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return LQ_ERR_CUDA;
+    return LQ_OK;
+}
+
 }  // namespace lq
 
 using namespace lq;
@@ -403,6 +495,106 @@ int dwf_dslash_apply(lq_handle* h, void* out, const void* in, int fmt, int dagge
         if (launch_spinor_from_native(prec, out, prec, nout, h->g, true, 0, Ls, st) != cudaSuccess)
             return LQ_ERR_CUDA;
     }
+    return LQ_OK;
+}
+
+// Even-odd domain wall: argument checks shared by the three calls (FP64/FP32 only).
+static int dwf_eo_args(lq_handle* h, int fmt) {
+    if (!h || !valid_fmt(fmt)) return LQ_ERR_ARG;
+    const int prec = fmt & 0xF;
+    if (h->p.Ls < 1 || (prec != LQ_F64 && prec != LQ_F32)) return LQ_ERR_ARG;
+    return LQ_OK;
+}
+
+int dwf_schur_apply(lq_handle* h, void* out, const void* in, int fmt, int dagger, void* stream) {
+    int rc = dwf_eo_args(h, fmt);
+    if (rc) return rc;
+    if (!out || !in) return LQ_ERR_ARG;
+    if (!aligned16(out) || !aligned16(in)) return LQ_ERR_LAYOUT;
+    const int Ls = h->p.Ls, prec = fmt & 0xF;
+    const size_t nb = field_bytes(h, fmt, LQ_EVEN, Ls);
+    if (overlap(out, nb, in, nb)) return LQ_ERR_ARG;
+    DeviceGuard dg(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool native = (fmt & LQ_NATIVE) != 0;
+    const size_t nat = field_bytes(h, prec | LQ_NATIVE, LQ_EVEN, Ls);
+    void* tmp;
+    if ((rc = ensure_ws(h, WS_TMP, nat, &tmp))) return rc;
+    const char* nin = static_cast<const char*>(in);
+    char* nout = static_cast<char*>(out);
+    if (!native) {
+        void *a, *b;
+        if ((rc = ensure_ws(h, WS_IN, nat, &a)) || (rc = ensure_ws(h, WS_OUT, nat, &b))) return rc;
+        if (launch_spinor_to_native(prec, a, prec, in, h->g, false, LQ_EVEN, Ls, st) != cudaSuccess)
+            return LQ_ERR_CUDA;
+        nin = static_cast<const char*>(a);
+        nout = static_cast<char*>(b);
+    }
+    if ((rc = native_dwf_schur(h, prec, nout, nin, static_cast<char*>(tmp), dagger != 0, st))) return rc;
+    if (!native && launch_spinor_from_native(prec, out, prec, nout, h->g, false, LQ_EVEN, Ls, st) != cudaSuccess)
+        return LQ_ERR_CUDA;
+    return LQ_OK;
+}
+
+int dwf_eo_prepare(lq_handle* h, void* bhat_e, const void* eta, int fmt, void* stream) {
+    int rc = dwf_eo_args(h, fmt);
+    if (rc) return rc;
+    if (!bhat_e || !eta) return LQ_ERR_ARG;
+    if (!aligned16(bhat_e) || !aligned16(eta)) return LQ_ERR_LAYOUT;
+    const int Ls = h->p.Ls, prec = fmt & 0xF;
+    if (overlap(bhat_e, field_bytes(h, fmt, LQ_EVEN, Ls), eta, field_bytes(h, fmt, LQ_FULL, Ls))) return LQ_ERR_ARG;
+    DeviceGuard dg(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool native = (fmt & LQ_NATIVE) != 0;
+    void* tmp;
+    if ((rc = ensure_ws(h, WS_TMP, field_bytes(h, prec | LQ_NATIVE, LQ_EVEN, Ls), &tmp))) return rc;
+    const char* neta = static_cast<const char*>(eta);
+    char* nb = static_cast<char*>(bhat_e);
+    if (!native) {
+        void *a, *b;
+        if ((rc = ensure_ws(h, WS_IN, field_bytes(h, prec | LQ_NATIVE, LQ_FULL, Ls), &a)) ||
+            (rc = ensure_ws(h, WS_OUT, field_bytes(h, prec | LQ_NATIVE, LQ_EVEN, Ls), &b)))
+            return rc;
+        if (launch_spinor_to_native(prec, a, prec, eta, h->g, true, 0, Ls, st) != cudaSuccess) return LQ_ERR_CUDA;
+        neta = static_cast<const char*>(a);
+        nb = static_cast<char*>(b);
+    }
+    if ((rc = native_dwf_prepare(h, prec, nb, neta, static_cast<char*>(tmp), st))) return rc;
+    if (!native && launch_spinor_from_native(prec, bhat_e, prec, nb, h->g, false, LQ_EVEN, Ls, st) != cudaSuccess)
+        return LQ_ERR_CUDA;
+    return LQ_OK;
+}
+
+int dwf_eo_reconstruct(lq_handle* h, void* psi, const void* x_e, const void* eta, int fmt, void* stream) {
+    int rc = dwf_eo_args(h, fmt);
+    if (rc) return rc;
+    if (!psi || !x_e || !eta) return LQ_ERR_ARG;
+    if (!aligned16(psi) || !aligned16(x_e) || !aligned16(eta)) return LQ_ERR_LAYOUT;
+    const int Ls = h->p.Ls, prec = fmt & 0xF;
+    const size_t full = field_bytes(h, fmt, LQ_FULL, Ls), half = field_bytes(h, fmt, LQ_EVEN, Ls);
+    if (overlap(psi, full, x_e, half) || overlap(psi, full, eta, full)) return LQ_ERR_ARG;
+    DeviceGuard dg(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool native = (fmt & LQ_NATIVE) != 0;
+    const char* nx = static_cast<const char*>(x_e);
+    const char* neta = static_cast<const char*>(eta);
+    char* npsi = static_cast<char*>(psi);
+    if (!native) {
+        void *a, *b, *c;
+        if ((rc = ensure_ws(h, WS_IN, field_bytes(h, prec | LQ_NATIVE, LQ_EVEN, Ls), &a)) ||
+            (rc = ensure_ws(h, WS_TMP, field_bytes(h, prec | LQ_NATIVE, LQ_FULL, Ls), &b)) ||
+            (rc = ensure_ws(h, WS_OUT, field_bytes(h, prec | LQ_NATIVE, LQ_FULL, Ls), &c)))
+            return rc;
+        if (launch_spinor_to_native(prec, a, prec, x_e, h->g, false, LQ_EVEN, Ls, st) != cudaSuccess ||
+            launch_spinor_to_native(prec, b, prec, eta, h->g, true, 0, Ls, st) != cudaSuccess)
+            return LQ_ERR_CUDA;
+        nx = static_cast<const char*>(a);
+        neta = static_cast<const char*>(b);
+        npsi = static_cast<char*>(c);
+    }
+    if ((rc = native_dwf_reconstruct(h, prec, npsi, nx, neta, st))) return rc;
+    if (!native && launch_spinor_from_native(prec, psi, prec, npsi, h->g, true, 0, Ls, st) != cudaSuccess)
+        return LQ_ERR_CUDA;
     return LQ_OK;
 }
 

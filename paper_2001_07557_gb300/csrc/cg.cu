@@ -37,6 +37,10 @@ struct OpGeom {
         return (size_t)nblk * spinor_site_bytes(prec) * (size_t)h->g.Vh;
     }
     size_t bytes(const lq_handle* h, int prec) const { return stride(h, prec) * nrhs; }
+    // the odd-parity scratch of one operator application: nrhs blocks, or Ls for the domain-wall Schur complement
+    size_t tmp_bytes(const lq_handle* h, int prec) const {
+        return (size_t)spinor_site_bytes(prec) * h->g.Vh * (op == LQ_OP_DWF_EO_NORMAL ? h->p.Ls : nrhs);
+    }
     VecRef ref(const lq_handle* h, void* p, int prec) const { return VecRef{static_cast<char*>(p), prec, stride(h, prec)}; }
 };
 
@@ -109,6 +113,7 @@ int apply_normal(lq_handle* h, const OpGeom& og, int prec, char* out, const char
     case LQ_OP_WILSON_NORMAL: rc = native_wilson_full(h, prec, t, in, og.nrhs, false, st); break;
     case LQ_OP_WILSON_EO_NORMAL: rc = native_wilson_schur(h, prec, t, in, tmp, og.nrhs, false, st); break;
     case LQ_OP_DWF_NORMAL: rc = native_dwf(h, prec, t, in, false, st); break;
+    case LQ_OP_DWF_EO_NORMAL: rc = native_dwf_schur(h, prec, t, in, tmp, false, st); break;
     default: rc = LQ_ERR_ARG;
     }
     h->red_partial = nullptr;
@@ -118,6 +123,7 @@ int apply_normal(lq_handle* h, const OpGeom& og, int prec, char* out, const char
     switch (og.op) {
     case LQ_OP_WILSON_NORMAL: return native_wilson_full(h, prec, out, t, og.nrhs, true, st);
     case LQ_OP_WILSON_EO_NORMAL: return native_wilson_schur(h, prec, out, t, tmp, og.nrhs, true, st);
+    case LQ_OP_DWF_EO_NORMAL: return native_dwf_schur(h, prec, out, t, tmp, true, st);
     default: return native_dwf(h, prec, out, t, true, st);
     }
 }
@@ -127,6 +133,7 @@ int hop_warps(const lq_handle* h, const OpGeom& og) {
     switch (og.op) {
     case LQ_OP_WILSON_NORMAL: return (int)hop_red_warps(h->g.Vh, 2, 1);
     case LQ_OP_WILSON_EO_NORMAL: return (int)hop_red_warps(h->g.Vh, 1, 1);
+    case LQ_OP_DWF_EO_NORMAL: return (int)hop_red_warps(h->g.Vh, 1, h->p.Ls);
     default: return (int)hop_red_warps(h->g.Vh, 2, h->p.Ls);
     }
 }
@@ -153,8 +160,7 @@ struct CgVecs {
 
 int cg_vectors(lq_handle* h, const OpGeom& og, int px, int pp, int slot0, CgVecs* v) {
     void* ptr[5];
-    const size_t sz[5] = {og.bytes(h, px), og.bytes(h, pp), og.bytes(h, pp), og.bytes(h, pp),
-                          (size_t)spinor_site_bytes(pp) * h->g.Vh * og.nrhs};
+    const size_t sz[5] = {og.bytes(h, px), og.bytes(h, pp), og.bytes(h, pp), og.bytes(h, pp), og.tmp_bytes(h, pp)};
     for (int k = 0; k < 5; ++k) {
         int rc = ensure_ws(h, slot0 + k, sz[k], &ptr[k]);
         if (rc) return rc;
@@ -273,7 +279,7 @@ int solve_fp32_middle(lq_handle* h, const OpGeom& og, const Ctl& c, int ip, cons
     int rc;
     if ((rc = ensure_ws(h, 20, og.bytes(h, LQ_F32), &rp)) || (rc = ensure_ws(h, 21, og.bytes(h, LQ_F32), &dp)) ||
         (rc = ensure_ws(h, 22, og.bytes(h, LQ_F32), &qp)) || (rc = ensure_ws(h, 23, og.bytes(h, LQ_F32), &tp)) ||
-        (rc = ensure_ws(h, 16, (size_t)spinor_site_bytes(LQ_F32) * Vh * nr, &tmpp)))
+        (rc = ensure_ws(h, 16, og.tmp_bytes(h, LQ_F32), &tmpp)))
         return rc;
     const VecRef R = og.ref(h, rp, LQ_F32), Dv = og.ref(h, dp, LQ_F32), Q = og.ref(h, qp, LQ_F32);
     std::vector<double> bb(nr), rr(nr);
@@ -349,13 +355,21 @@ extern "C" int cg_solve(lq_handle* h, void* x, const void* b, const lq_cg_params
         og.nblk = 2 * h->p.Ls;
         subset = LQ_FULL;
         break;
+    case LQ_OP_DWF_EO_NORMAL:
+        // Ls even half fields; the site-local inverse M5^{-1} exists for FP64/FP32 fields only
+        if (h->p.Ls < 1 || cp->nrhs != 1 || (fprec != LQ_F64 && fprec != LQ_F32)) return LQ_ERR_ARG;
+        if (cp->mode != LQ_CG_PLAIN && cp->inner != LQ_F32) return LQ_ERR_ARG;
+        og.nblk = h->p.Ls;
+        subset = LQ_EVEN;
+        break;
     default: return LQ_ERR_ARG;
     }
     const int mode = cp->mode == LQ_CG_BATCHED ? LQ_CG_MIXED : cp->mode;
     if (mode != LQ_CG_PLAIN && mode != LQ_CG_MIXED && mode != LQ_CG_BLOCK) return LQ_ERR_ARG;
     if (mode == LQ_CG_MIXED && (cp->inner < LQ_F32 || cp->inner > LQ_BF16)) return LQ_ERR_ARG;
-    if (mode == LQ_CG_BLOCK && (cp->nrhs > kMaxBlockRhs || cp->op == LQ_OP_DWF_NORMAL)) return LQ_ERR_ARG;
-    const int nf = cp->op == LQ_OP_DWF_NORMAL ? h->p.Ls : cp->nrhs;  // fields in the user's buffers
+    const bool dwf = cp->op == LQ_OP_DWF_NORMAL || cp->op == LQ_OP_DWF_EO_NORMAL;
+    if (mode == LQ_CG_BLOCK && (cp->nrhs > kMaxBlockRhs || dwf)) return LQ_ERR_ARG;
+    const int nf = dwf ? h->p.Ls : cp->nrhs;  // fields in the user's buffers
     const size_t ub = field_bytes(h, cp->fmt, subset, nf);
     if (overlap(x, ub, b, ub)) return LQ_ERR_ARG;
     DeviceGuard dg(h->device);

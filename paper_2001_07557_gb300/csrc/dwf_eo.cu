@@ -1,0 +1,96 @@
+// dwf_eo.cu -- the site-local inverse M5^{-1} of the even-odd preconditioned
+// domain-wall operator.
+//
+// M5 is the part of D_dw that stays on a 4-d site (Shamir form, walls -mf):
+//   (M5 psi)(s) = a psi(s) - P- psi(s+1) - P+ psi(s-1),   a = 5 - M5.
+// With gamma_5 = diag(1, 1, -1, -1), P+ keeps spins 0,1 and P- spins 2,3, so M5
+// is one real Ls x Ls matrix per chirality, the same for every site, colour
+// and spin of that chirality:
+//   spins 0,1:  a y(s) - y(s-1),  row 0: a y(0) + mf y(Ls-1)    (lower bidiagonal + corner)
+//   spins 2,3:  a y(s) - y(s+1),  row Ls-1: a y(Ls-1) + mf y(0)  (upper bidiagonal + corner)
+// and M5^dag swaps the two forms.  Each is B + mf u v^T with B bidiagonal, so
+// the inverse is one sweep for B^{-1} plus a Sherman-Morrison correction:
+//   z = B^{-1} x (z = (x + z_prev) / a along the sweep),
+//   y = z - c w z_end,  w at sweep step j = a^{-(j+1)},  c = mf / (1 + mf a^{-Ls}),
+// where z_end is z at the end of the sweep (s = Ls-1 forward, s = 0 backward).
+// A thread owns one (site, 16-byte plane) and sweeps twice over the Ls slices:
+// once for z_end, once to write y.  Each slice is read before it is written, so
+// the call may run in place.  O(Ls) work per component, bandwidth-bound.
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "lqcd_kernels.h"
+
+namespace lq {
+
+namespace {
+
+template <typename V, typename T>
+__device__ __forceinline__ V axpby4(T a, V x, T b, V y);  // a x + b y
+
+template <>
+__device__ __forceinline__ float4 axpby4<float4, float>(float a, float4 x, float b, float4 y) {
+    return make_float4(fmaf(a, x.x, b * y.x), fmaf(a, x.y, b * y.y), fmaf(a, x.z, b * y.z), fmaf(a, x.w, b * y.w));
+}
+
+template <>
+__device__ __forceinline__ double2 axpby4<double2, double>(double a, double2 x, double b, double2 y) {
+    return make_double2(fma(a, x.x, b * y.x), fma(a, x.y, b * y.y));
+}
+
+// P = LQ_F32: 6 planes of float4 (2 complex) per site; LQ_F64: 12 planes of double2.
+template <int P>
+__global__ void __launch_bounds__(256) m5inv_kernel(char* out, const char* in, int Vh, size_t out_stride,
+                                                    size_t in_stride, int Ls, double inv_a_d, double c_d, int dag) {
+    using V = typename std::conditional<P == LQ_F64, double2, float4>::type;
+    using T = typename std::conditional<P == LQ_F64, double, float>::type;
+    constexpr int NPL = P == LQ_F64 ? 12 : 6;
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)Vh * NPL) return;
+    const int k = (int)(idx / Vh), i = (int)(idx - (long)k * Vh);  // plane-major: a warp reads 32 sites of a plane
+    const bool fwd = (k < NPL / 2) != (dag != 0);  // spins 0,1 sweep upwards in s unless daggered
+    const T inv_a = (T)inv_a_d, c = (T)c_d;
+    const char* src = in + ((size_t)k * Vh + i) * sizeof(V);
+    char* dst = out + ((size_t)k * Vh + i) * sizeof(V);
+    auto slice = [&](int j) { return fwd ? j : Ls - 1 - j; };
+    V z = {};
+    for (int j = 0; j < Ls; ++j) {
+        const V x = *reinterpret_cast<const V*>(src + (size_t)slice(j) * in_stride);
+        z = axpby4<V, T>(inv_a, x, inv_a, z);
+    }
+    const V zend = z;
+    z = V{};
+    T w = inv_a;
+    for (int j = 0; j < Ls; ++j) {
+        const int s = slice(j);
+        const V x = *reinterpret_cast<const V*>(src + (size_t)s * in_stride);
+        z = axpby4<V, T>(inv_a, x, inv_a, z);
+        *reinterpret_cast<V*>(dst + (size_t)s * out_stride) = axpby4<V, T>((T)1, z, -c * w, zend);
+        w *= inv_a;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_m5inv(int prec, void* out, const void* in, int Vh, size_t out_stride, size_t in_stride, int Ls,
+                         double M5, double mf, bool dag, cudaStream_t st) {
+    const double a = 5.0 - M5;
+    double aL = 1.0;  // a^{-Ls}
+    for (int s = 0; s < Ls; ++s) aL /= a;
+    const double c = mf / (1.0 + mf * aL);
+    const int npl = prec == LQ_F64 ? 12 : 6;
+    const long n = (long)Vh * npl;
+    const int grid = (int)((n + 255) / 256);
+    if (prec == LQ_F64)
+        m5inv_kernel<LQ_F64><<<grid, 256, 0, st>>>(static_cast<char*>(out), static_cast<const char*>(in), Vh,
+                                                   out_stride, in_stride, Ls, 1.0 / a, c, dag);
+    else if (prec == LQ_F32)
+        m5inv_kernel<LQ_F32><<<grid, 256, 0, st>>>(static_cast<char*>(out), static_cast<const char*>(in), Vh,
+                                                   out_stride, in_stride, Ls, 1.0 / a, c, dag);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+}  // namespace lq

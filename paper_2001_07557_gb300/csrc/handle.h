@@ -65,6 +65,11 @@ int native_wilson_block(lq_handle* h, int prec, char* out, const char* in, int o
 int native_wilson_schur(lq_handle* h, int prec, char* out, const char* in, char* tmp, int nrhs, bool dag,
                         cudaStream_t st);
 int native_dwf(lq_handle* h, int prec, char* out, const char* in, bool dag, cudaStream_t st);
+// Even-odd domain wall (FP64/FP32).  Half fields: Ls even (or odd) blocks
+// back to back; full fields: Ls slices of two blocks.  tmp holds Ls blocks.
+int native_dwf_schur(lq_handle* h, int prec, char* out_e, const char* in_e, char* tmp, bool dag, cudaStream_t st);
+int native_dwf_prepare(lq_handle* h, int prec, char* bhat_e, const char* eta, char* tmp, cudaStream_t st);
+int native_dwf_reconstruct(lq_handle* h, int prec, char* psi, const char* x_e, const char* eta, cudaStream_t st);
 
 // Launch descriptors of the Wilson operator pieces (links packed on demand).
 int prep_wilson_full(lq_handle* h, int prec, char* out, const char* in, int nrhs, HopArgs* a, cudaStream_t st);

@@ -54,6 +54,12 @@ inline size_t hop_red_warps(int Vh, int nparity, int slices) {
 cudaError_t launch_hop_norm_finalize(const double* partial, int nwarps, int ngroups, CgScalars* st, cudaStream_t s);
 
 cudaError_t launch_hop(int prec, const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st);
+
+// out = M5^{-1} in (dag: (M5^dag)^{-1}) on the Ls slices of one parity block of
+// a native FP64/FP32 5-d field; slice s of out/in at s * out_stride/in_stride
+// bytes.  In place allowed.  (dwf_eo.cu)
+cudaError_t launch_m5inv(int prec, void* out, const void* in, int Vh, size_t out_stride, size_t in_stride, int Ls,
+                         double M5, double mf, bool dag, cudaStream_t st);
 cudaError_t launch_hop_f64(const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st);
 cudaError_t launch_hop_f32(const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st);
 cudaError_t launch_hop_f16(const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st);

@@ -19,14 +19,14 @@ LQ_OK = 0
 LQ_F64, LQ_F32, LQ_F16, LQ_BF16 = 0, 1, 2, 3
 LQ_NATIVE = 0x10
 LQ_FULL, LQ_EVEN, LQ_ODD, LQ_SCHUR_EVEN = -1, 0, 1, 2
-LQ_OP_WILSON_NORMAL, LQ_OP_WILSON_EO_NORMAL, LQ_OP_DWF_NORMAL = 0, 1, 2
+LQ_OP_WILSON_NORMAL, LQ_OP_WILSON_EO_NORMAL, LQ_OP_DWF_NORMAL, LQ_OP_DWF_EO_NORMAL = 0, 1, 2, 3
 LQ_CG_PLAIN, LQ_CG_MIXED, LQ_CG_BLOCK, LQ_CG_BATCHED = 0, 1, 2, 3
 STATUS = {0: "LQ_OK", -1: "LQ_ERR_ARG", -2: "LQ_ERR_LAYOUT", -3: "LQ_ERR_CUDA", -4: "LQ_ERR_NOMEM",
           -5: "LQ_ERR_NOT_CONVERGED", -6: "LQ_ERR_BREAKDOWN", -7: "LQ_ERR_TIMEOUT", -8: "LQ_ERR_NAN"}
 
 # every function the header declares
 EXPORTS = ["lq_create", "lq_destroy", "lq_field_bytes", "lq_convert", "dslash_apply", "dslash_dag_apply",
-           "dwf_dslash_apply", "lq_dot", "lq_dot_noalloc", "cg_solve", "lq_batch_cg_solve", "lq_su3_mul",
+           "dwf_dslash_apply", "dwf_schur_apply", "dwf_eo_prepare", "dwf_eo_reconstruct", "lq_dot", "lq_dot_noalloc", "cg_solve", "lq_batch_cg_solve", "lq_su3_mul",
            "lq_wait_timeouts", "lq_status_string"]
 LQ_DOT_NOALLOC_MAX_RHS = 32
 
@@ -72,6 +72,9 @@ def lib():
         L.dslash_apply.argtypes = [vp, vp, vp, i, i, i, vp]
         L.dslash_dag_apply.argtypes = [vp, vp, vp, i, i, i, vp]
         L.dwf_dslash_apply.argtypes = [vp, vp, vp, i, i, vp]
+        L.dwf_schur_apply.argtypes = [vp, vp, vp, i, i, vp]
+        L.dwf_eo_prepare.argtypes = [vp, vp, vp, i, vp]
+        L.dwf_eo_reconstruct.argtypes = [vp, vp, vp, vp, i, vp]
         L.lq_dot.argtypes = [vp, vp, vp, vp, i, i, i, i, vp]
         L.lq_dot_noalloc.argtypes = [vp, vp, vp, vp, i, i, i, i, vp]
         L.cg_solve.argtypes = [vp, vp, vp, ctypes.POINTER(lq_cg_params), ctypes.POINTER(lq_cg_stats), vp]
@@ -152,6 +155,22 @@ def dslash_dag_apply(h, out, inp, fmt, parity=LQ_FULL, nrhs=1, stream=None):
 
 def dwf_dslash_apply(h, out, inp, fmt, dagger=False, stream=None):
     _check(lib().dwf_dslash_apply(h, _ptr(out), _ptr(inp), fmt, int(dagger), _stream(stream)), "dwf_dslash_apply")
+
+
+def dwf_schur_apply(h, out, inp, fmt, dagger=False, stream=None):
+    """Even-odd domain-wall Schur complement Mhat (or Mhat^dag) on 5-d even half fields."""
+    _check(lib().dwf_schur_apply(h, _ptr(out), _ptr(inp), fmt, int(dagger), _stream(stream)), "dwf_schur_apply")
+
+
+def dwf_eo_prepare(h, bhat_e, eta, fmt, stream=None):
+    """bhat_e = eta_e - M_eo M5^{-1} eta_o from a full 5-d source."""
+    _check(lib().dwf_eo_prepare(h, _ptr(bhat_e), _ptr(eta), fmt, _stream(stream)), "dwf_eo_prepare")
+
+
+def dwf_eo_reconstruct(h, psi, x_e, eta, fmt, stream=None):
+    """The full 5-d solution from its even half and the source."""
+    _check(lib().dwf_eo_reconstruct(h, _ptr(psi), _ptr(x_e), _ptr(eta), fmt, _stream(stream)),
+           "dwf_eo_reconstruct")
 
 
 def lq_dot(h, result, a, b, fmt, subset=LQ_FULL, nrhs=1, five_d=False, stream=None):
