@@ -262,6 +262,13 @@ def oracle_normal_op(dims, mass, U, psi_e):
     return time.perf_counter() - t0, out
 
 
+def oracle_timed(fn, *a, **k):
+    """CPU-baseline leg: one call of an oracle function, wall seconds and result."""
+    t0 = time.perf_counter()
+    r = fn(*a, **k)
+    return time.perf_counter() - t0, r
+
+
 def host_cores():
     try:
         import oracle
@@ -674,6 +681,12 @@ def other_configs(lqcd, torch):
     rc, stt = lqcd.cg_solve(h, x, b, cp, check=False)
     out["c1_4x4_fp64_cg"] = {"status": rc, "seconds": time.perf_counter() - t0, "iters": stt[0].iters,
                              "true_rel_residual": stt[0].true_rel_residual}
+    import oracle  # CPU-baseline leg: the oracle timed on the host cores beside each GPU figure
+
+    cores = host_cores()
+    prm = oracle.params(dims, mass=0.1)
+    dt, (xo, it, _, _) = oracle_timed(oracle.cg, oracle.OP_WILSON, b.cpu().numpy(), U, prm, 1e-12)
+    out["c1_4x4_fp64_cg"]["cpu_baseline"] = {"seconds": dt, "iters": it, "cores": cores, "kind": "oracle"}
     lqcd.lq_destroy(h)
 
     # 16^3x32 even-odd, smooth links, m = 0.05: FP64 and FP32 hops; FP64 and mixed CG to 1e-10
@@ -701,6 +714,14 @@ def other_configs(lqcd, torch):
         rc, stt = lqcd.cg_solve(h, x, bd, cp, check=False)
         res[name] = {"status": rc, "seconds": time.perf_counter() - t0, "iters": stt[0].iters,
                      "true_rel_residual": stt[0].true_rel_residual}
+    dt, _ = oracle_timed(oracle.wilson_hop_eo, src, U, dims, 0)
+    prm = oracle.params(dims, mass=0.05)
+    dt_cg, (_, it, _, _) = oracle_timed(oracle.cg, oracle.OP_WILSON_EO, src, U, prm, 1e-10, maxiter=10)
+    res["cpu_baseline"] = {"eo_hop_gflops": FLOP_PER_SITE * (V // 2) / dt / 1e9,
+                           "cg_seconds_per_iteration": dt_cg / max(it, 1),
+                           "cg_seconds_projected": dt_cg / max(it, 1) * res["fp64_cg"]["iters"],
+                           "cores": cores, "kind": "oracle",
+                           "sample": "one FP64 eo hop; 10 CG iterations, projected to the GPU FP64 CG's count"}
     out["c2_16x3x32_eo"] = res
     lqcd.lq_destroy(h)
 
@@ -709,6 +730,9 @@ def other_configs(lqcd, torch):
     V = int(np.prod(dims))
     U = inputs.gauge_field(dims, "smooth", seed=1003)
     res = mrhs_hops(lqcd, torch, st, hbm, U, 10)
+    dt, _ = oracle_timed(oracle.wilson_dslash, inputs.point_sources(V), U, dims, 0.02)
+    res["cpu_baseline"] = {"hop_12rhs_gflops": FLOP_PER_SITE * V * 12 / dt / 1e9, "seconds": dt, "cores": cores,
+                           "kind": "oracle", "sample": "one 12-source full-lattice D application in FP64"}
     # solves to 1e-10 on D^dag D x = D^dag (point source): one FP64 CG, 12 FP64 CGs in one batch,
     # 12 mixed CGs in one batch (FP16 inner), and block CG over the 12 (FP32 inner)
     # 18-real links: with 12 right-hand sides sharing every link load, rebuilding row 3 costs more than it saves
@@ -796,6 +820,13 @@ def other_configs(lqcd, torch):
     V = int(np.prod(dims))
     U = inputs.gauge_field(dims, "smooth", seed=1004)
     res = dwf_hops(lqcd, torch, st, hbm, U, 20)
+    psi5 = inputs.gaussian_spinor(V, seed=2004, nrhs=Ls)
+    dt, _ = oracle_timed(oracle.dwf_dslash, psi5, U, dims, Ls, 1.8, 0.01)
+    dt_s, _ = oracle_timed(oracle.dwf_schur, psi5[:, : V // 2], U, dims, Ls, 1.8, 0.01)
+    res["cpu_baseline"] = {"dwf_gflops_4d": FLOP_PER_SITE * V * Ls / dt / 1e9, "dwf_seconds": dt,
+                           "eo_schur_seconds": dt_s, "cores": cores, "kind": "oracle",
+                           "sample": "one D_dw and one Mhat application in FP64"}
+    del psi5
     # CG on D_dw^dag D_dw: FP32 alone to 1e-8, and FP64 refinement around FP32 inner solves to 1e-10
     h = lqcd.lq_create(lqcd.make_params(dims, Ls=Ls, M5=1.8, mf=0.01, compress12=False), torch.from_numpy(U).cuda())
     eta = torch.from_numpy(inputs.gaussian_spinor(V, seed=2004, nrhs=Ls)).cuda()
@@ -856,6 +887,10 @@ def other_configs(lqcd, torch):
     lqcd.lq_destroy(h)
     out["c5_16x4xLs16_dwf"] = res
     out["su3_mul"] = su3_sweep(lqcd, torch, st, hbm, 20)
+    A = inputs.gauge_field((16, 16, 16, 16), "random", seed=1000).reshape(-1, 3, 3)  # 262,144 matrices
+    dt, _ = oracle_timed(oracle.su3_mul, A, np.roll(A, 1, axis=0))
+    out["su3_mul"]["cpu_baseline"] = {"gflops": 198 * len(A) / dt / 1e9, "n": len(A), "cores": cores,
+                                      "kind": "oracle", "sample": "one FP64 product over 16^4 x 4 link matrices"}
     return out
 
 

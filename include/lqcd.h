@@ -289,6 +289,17 @@ int lq_su3_mul(void *C, const void *A, const void *B, long n, int fmt, void *str
  */
 int lq_wait_timeouts(unsigned *count);
 
+/*
+ * lq_test_stalled_wait: exercises the timeout path of the barrier waits.  It
+ * runs the SU(3) product kernel on one tile of zero matrices (in its own
+ * scratch) with the stage barrier armed for 16 more bytes than the copies
+ * bring, so that the phase never completes: the bounded wait gives up after
+ * about a second, the kernel returns, and the count read by lq_wait_timeouts
+ * grows by one.  No fault and no hang; the device stays usable.  Synchronises
+ * the device.  For tests of the failure path only.
+ */
+int lq_test_stalled_wait(void);
+
 /* Human-readable text for a status code (static storage). */
 const char *lq_status_string(int status);
 

@@ -50,9 +50,17 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-// Poll the barrier's phase; false after about a second without completion.
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Poll the barrier's phase; false once about a second has passed without
+// completion (the iteration cap is a second bound should the timer stall).
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-    for (int i = 0; i < (1 << 24); ++i) {
+    const uint64_t t0 = globaltimer_ns();
+    for (int i = 0; i < (1 << 26); ++i) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -62,6 +70,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
             : "r"(bar), "r"(parity)
             : "memory");
         if (done) return true;
+        if ((i & 255) == 255 && globaltimer_ns() - t0 > 1000000000ull) return false;
         __nanosleep(32);
     }
     return false;
@@ -109,8 +118,10 @@ struct Su3Cfg {
     static constexpr int SMEM = 6 * TB + 16;
 };
 
+// stall != 0 (testing only) arms each stage barrier for 16 more bytes than its
+// copies bring, so that the bounded wait runs out.
 template <typename T, int TS>
-__global__ void __launch_bounds__(TS) su3_mul_kernel(const char* A, const char* B, char* C, long n) {
+__global__ void __launch_bounds__(TS) su3_mul_kernel(const char* A, const char* B, char* C, long n, int stall) {
     using Cfg = Su3Cfg<T, TS>;
     using T2 = typename Cfg::T2;
     constexpr int MB = Cfg::MB, TB = Cfg::TB;
@@ -126,7 +137,7 @@ __global__ void __launch_bounds__(TS) su3_mul_kernel(const char* A, const char* 
     auto issue = [&](long tile, int s) {
         const uint32_t bytes = (uint32_t)bulk(count(tile)) * MB;
         const uint32_t bar = smem_u32(&bars[s]);
-        mbar_arrive_expect_tx(bar, 2 * bytes);
+        mbar_arrive_expect_tx(bar, 2 * bytes + (stall ? 16u : 0u));
         if (bytes) {
             bulk_load(smem_u32(sm + 2 * s * TB), A + tile * TB, bytes, bar);
             bulk_load(smem_u32(sm + (2 * s + 1) * TB), B + tile * TB, bytes, bar);
@@ -184,7 +195,7 @@ __global__ void __launch_bounds__(TS) su3_mul_kernel(const char* A, const char* 
 }
 
 template <typename T, int TS>
-int launch_su3(void* C, const void* A, const void* B, long n, cudaStream_t st) {
+int launch_su3(void* C, const void* A, const void* B, long n, cudaStream_t st, int stall = 0) {
     using Cfg = Su3Cfg<T, TS>;
     auto kern = su3_mul_kernel<T, TS>;
     static int grid_max = 0;  // resident blocks on this device, found once
@@ -200,7 +211,7 @@ int launch_su3(void* C, const void* A, const void* B, long n, cudaStream_t st) {
     const long ntiles = (n + TS - 1) / TS;
     const int grid = (int)std::min<long>(ntiles, grid_max);
     kern<<<grid, TS, Cfg::SMEM, st>>>(static_cast<const char*>(A), static_cast<const char*>(B),
-                                      static_cast<char*>(C), n);
+                                      static_cast<char*>(C), n, stall);
     return cudaGetLastError() == cudaSuccess ? LQ_OK : LQ_ERR_CUDA;
 }
 
@@ -223,6 +234,22 @@ int lq_su3_mul(void* C, const void* A, const void* B, long n, int fmt, void* str
     if ((C != A && lq::overlaps(C, A, bytes)) || (C != B && lq::overlaps(C, B, bytes))) return LQ_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     return fmt == LQ_F64 ? lq::launch_su3<double, 128>(C, A, B, n, st) : lq::launch_su3<float, 256>(C, A, B, n, st);
+}
+
+int lq_test_stalled_wait(void) {
+    // one tile of zero matrices, product kernel with its barrier armed for bytes that never come
+    const long n = 256;
+    void* buf = nullptr;
+    if (cudaMalloc(&buf, 3 * 72 * n) != cudaSuccess) {
+        cudaGetLastError();
+        return LQ_ERR_NOMEM;
+    }
+    char* p = static_cast<char*>(buf);
+    int rc = cudaMemset(buf, 0, 3 * 72 * n) == cudaSuccess ? LQ_OK : LQ_ERR_CUDA;
+    if (rc == LQ_OK) rc = lq::launch_su3<float, 256>(p + 2 * 72 * n, p, p + 72 * n, n, nullptr, 1);
+    if (rc == LQ_OK && cudaDeviceSynchronize() != cudaSuccess) rc = LQ_ERR_CUDA;
+    cudaFree(buf);
+    return rc;
 }
 
 int lq_wait_timeouts(unsigned* count) {

@@ -27,7 +27,7 @@ STATUS = {0: "LQ_OK", -1: "LQ_ERR_ARG", -2: "LQ_ERR_LAYOUT", -3: "LQ_ERR_CUDA", 
 # every function the header declares
 EXPORTS = ["lq_create", "lq_destroy", "lq_field_bytes", "lq_convert", "dslash_apply", "dslash_dag_apply",
            "dwf_dslash_apply", "dwf_schur_apply", "dwf_eo_prepare", "dwf_eo_reconstruct", "lq_dot", "lq_dot_noalloc", "cg_solve", "lq_batch_cg_solve", "lq_su3_mul",
-           "lq_wait_timeouts", "lq_status_string"]
+           "lq_wait_timeouts", "lq_test_stalled_wait", "lq_status_string"]
 LQ_DOT_NOALLOC_MAX_RHS = 32
 
 
@@ -82,6 +82,7 @@ def lib():
                                         ctypes.POINTER(lq_cg_params), ctypes.POINTER(lq_cg_stats), vp]
         L.lq_su3_mul.argtypes = [vp, vp, vp, ctypes.c_long, i, vp]
         L.lq_wait_timeouts.argtypes = [ctypes.POINTER(ctypes.c_uint)]
+        L.lq_test_stalled_wait.argtypes = []
         L.lq_status_string.argtypes = [i]
         L.lq_status_string.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -230,3 +231,8 @@ def lq_wait_timeouts():
     c = ctypes.c_uint(0)
     _check(lib().lq_wait_timeouts(ctypes.byref(c)), "lq_wait_timeouts")
     return c.value
+
+
+def lq_test_stalled_wait():
+    """Run one product tile whose barrier wait must run out (tests the timeout path)."""
+    _check(lib().lq_test_stalled_wait(), "lq_test_stalled_wait")

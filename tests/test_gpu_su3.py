@@ -84,3 +84,20 @@ def test_su3_mul_full_size(fmt):
     A, B = matrices(n, 31), matrices(n, 32)
     want = oracle.su3_mul(A.astype(DT[fmt][0]), B.astype(DT[fmt][0]))
     check(run(A, B, fmt), want, fmt)
+
+
+def test_a_wait_that_runs_out_is_reported_and_the_device_stays_usable():
+    """The failure path of the barrier waits, without a fault: a product tile
+    whose barrier is armed for bytes that never come gives up after about a
+    second, the count of waits that ran out reads 1, and the next product on
+    the same context is correct."""
+    import time
+
+    assert lqcd.lq_wait_timeouts() == 0
+    t0 = time.perf_counter()
+    lqcd.lq_test_stalled_wait()
+    dt = time.perf_counter() - t0
+    assert lqcd.lq_wait_timeouts() == 1
+    assert 0.5 < dt < 20.0, dt
+    A, B = matrices(1000, 41), matrices(1000, 42)
+    check(run(A, B, lqcd.LQ_F32), oracle.su3_mul(A.astype(np.complex64), B.astype(np.complex64)), lqcd.LQ_F32)
