@@ -659,6 +659,74 @@ def hops_only(args):
     print(json.dumps({"hops_only": out}))
 
 
+def halo_emulation(lqcd, torch, hbm, reps=20):
+    """Time-slab decomposition of the full-lattice FP16 Wilson hop on 32^4 into
+    two ranks on one GPU: each rank a 32^3 x 18 lattice (16 own slices + two
+    ghosts); per hop, 4 face copies (the antiperiodic sign folded into the
+    copy at the global boundary) on one stream while the interior slices run on
+    another, then the edge slices.  Compared with the single-domain hop."""
+    from paper_2001_07557_gb300 import inputs
+
+    dims, R, mass = (32, 32, 32, 32), 2, 0.01
+    L3, V3 = dims[3], dims[0] * dims[1] * dims[2]
+    Lt = L3 // R
+    U = inputs.gauge_field((32, 32, 32, 4), "smooth", seed=1002)  # 4 time slices of links, tiled in t
+    Ug = np.tile(U.reshape(4, V3, 4, 3, 3), (L3 // 4, 1, 1, 1, 1))
+    nat = lqcd.LQ_NATIVE | lqcd.LQ_F16
+    src = torch.randn(L3 * V3 * 12, dtype=torch.complex64, device="cuda").reshape(-1, 4, 3)
+    # single domain
+    h = lqcd.lq_create(lqcd.make_params(dims, mass=mass), torch.from_numpy(Ug.reshape(-1, 4, 3, 3)).cuda())
+    nb = lqcd.lq_field_bytes(h, nat, lqcd.LQ_FULL, 1)
+    a_, b_ = (torch.empty(nb, dtype=torch.uint8, device="cuda") for _ in range(2))
+    lqcd.lq_convert(h, a_, nat, src, lqcd.LQ_F32)
+    st = torch.cuda.Stream()
+    single = _time(lambda: lqcd.dslash_apply(h, b_, a_, nat, lqcd.LQ_FULL, stream=st), st, reps, torch)
+    lqcd.lq_destroy(h)
+    del a_, b_
+    # two slabs with ghosts
+    hs, ins, outs = [], [], []
+    srcg = src.reshape(L3, V3, 4, 3)
+    for r in range(R):
+        ts = [(r * Lt + tp - 1) % L3 for tp in range(Lt + 2)]
+        hr = lqcd.lq_create(lqcd.make_params((32, 32, 32, Lt + 2), mass=mass, bc=(1, 1, 1, 1)),
+                            torch.from_numpy(np.ascontiguousarray(Ug[ts]).reshape(-1, 4, 3, 3)).cuda())
+        n = lqcd.lq_field_bytes(hr, nat, lqcd.LQ_FULL, 1)
+        i_, o_ = torch.empty(n, dtype=torch.uint8, device="cuda"), torch.zeros(n, dtype=torch.uint8, device="cuda")
+        loc = torch.zeros((Lt + 2, V3, 4, 3), dtype=torch.complex64, device="cuda")
+        loc[1:Lt + 1] = srcg[r * Lt:(r + 1) * Lt]
+        lqcd.lq_convert(hr, i_, nat, loc.reshape(-1, 4, 3), lqcd.LQ_F32)
+        hs.append(hr)
+        ins.append(i_)
+        outs.append(o_)
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    ev = torch.cuda.Event()
+
+    def step():
+        ev.record(sa)
+        sb.wait_event(ev)
+        for r in range(R):
+            lqcd.dslash_apply_slices(hs[r], outs[r], ins[r], nat, 2, Lt, stream=sa)
+        for r in range(R):
+            lo, hi = (r - 1) % R, (r + 1) % R
+            lqcd.lq_face_copy(hs[r], ins[r], 0, hs[lo], ins[lo], Lt, nat, -1.0 if r == 0 else 1.0, sb)
+            lqcd.lq_face_copy(hs[r], ins[r], Lt + 1, hs[hi], ins[hi], 1, nat, -1.0 if r == R - 1 else 1.0, sb)
+        for r in range(R):
+            lqcd.dslash_apply_slices(hs[r], outs[r], ins[r], nat, 1, 2, stream=sb)
+            lqcd.dslash_apply_slices(hs[r], outs[r], ins[r], nat, Lt, Lt + 1, stream=sb)
+        ev.record(sb)
+        sa.wait_event(ev)
+
+    split = _time(step, sa, reps, torch)
+    for hr in hs:
+        lqcd.lq_destroy(hr)
+    face = 2 * R * V3 * 52  # bytes of the four faces (FP16 + norms, full spinors)
+    return {"single_domain_us": single * 1e3, "two_slabs_us": split * 1e3,
+            "gflops_single": FLOP_PER_SITE * L3 * V3 / (single * 1e-3) / 1e9,
+            "gflops_two_slabs": FLOP_PER_SITE * L3 * V3 / (split * 1e-3) / 1e9,
+            "face_bytes_per_hop": face, "ghost_compute": "none (only own slices are computed)",
+            "note": "both ranks on one GPU; interior slices overlap the face copies on a second stream"}
+
+
 def other_configs(lqcd, torch):
     """The other workloads of the method, one short measurement each."""
     from paper_2001_07557_gb300 import inputs
@@ -886,6 +954,7 @@ def other_configs(lqcd, torch):
                            "note": "flops of the two half-lattice 4-d hops only"}
     lqcd.lq_destroy(h)
     out["c5_16x4xLs16_dwf"] = res
+    out["halo_2rank_32x4"] = halo_emulation(lqcd, torch, hbm)
     out["su3_mul"] = su3_sweep(lqcd, torch, st, hbm, 20)
     A = inputs.gauge_field((16, 16, 16, 16), "random", seed=1000).reshape(-1, 3, 3)  # 262,144 matrices
     dt, _ = oracle_timed(oracle.su3_mul, A, np.roll(A, 1, axis=0))

@@ -259,6 +259,36 @@ int cg_solve(lq_handle *h, void *x, const void *b, const lq_cg_params *cp, lq_cg
 int lq_batch_cg_solve(lq_handle **hs, int nlat, void **xs, const void **bs, const lq_cg_params *cp,
                       lq_cg_stats *stats, void *stream);
 
+/* ------------------------------------------- time-slab decomposition */
+
+/*
+ * Building blocks of a domain decomposition in time: every rank holds a slab
+ * of time slices plus one ghost slice on each side (a lattice of its own
+ * handle, L3 = slab + 2), fills the ghosts from its neighbours' edge slices
+ * before each hop, and keeps the output of its own slices.  The paper's MPI
+ * shift (Sec. 3.2) is unfinished; these calls carry the same exchange between
+ * handles on one device.
+ *
+ * dslash_apply_slices: the full-lattice Wilson operator D (dagger != 0: D^dag)
+ *   with output on the time slices t0 <= t < t1 only; other sites of out are
+ *   not written.  in and out are full native fields (fmt = LQ_NATIVE | prec;
+ *   site-major formats give LQ_ERR_LAYOUT).  0 <= t0 < t1 <= L3.  Computing
+ *   the slab's interior slices while the ghosts are copied, then its two edge
+ *   slices, overlaps the exchange with the hop.
+ *
+ * lq_face_copy: time slice t_src of src (a full native field of hs's lattice)
+ *   times scale, into time slice t_dst of dst (a full native field of hd's
+ *   lattice).  hd and hs must have the same L0, L1, L2 (LQ_ERR_ARG).  scale is
+ *   +1, or -1 where the copy crosses the global antiperiodic time boundary
+ *   (FP16/BF16 fields carry it in their site norms).  If t_dst - t_src is odd
+ *   the local parities of the slice's sites differ between the two lattices and
+ *   the parity blocks are swapped.  dst and src may be one field if the slices
+ *   differ.  Asynchronous on `stream`.
+ */
+int dslash_apply_slices(lq_handle *h, void *out, const void *in, int fmt, int t0, int t1, int dagger, void *stream);
+int lq_face_copy(lq_handle *hd, void *dst, int t_dst, lq_handle *hs, const void *src, int t_src, int fmt, double scale,
+                 void *stream);
+
 /* ---------------------------------------------------- SU(3) x SU(3) */
 
 /*

@@ -24,12 +24,13 @@ __global__ void __launch_bounds__(128) wilson_hop_kernel(const HopArgs a) {
     // grid.y = output parity
     const int rhs = blockIdx.x % a.nrhs;
     const Geom& g = a.g;
-    const int i0 = (blockIdx.x / a.nrhs) * blockDim.x + threadIdx.x;
-    const bool active = i0 < g.Vh;
+    const int end = a.nsite ? a.site0 + a.nsite : g.Vh;
+    const int i0 = a.site0 + (blockIdx.x / a.nrhs) * blockDim.x + threadIdx.x;
+    const bool active = i0 < end;
     if constexpr (!RED) {
         if (!active) return;
     }
-    const int i = active ? i0 : g.Vh - 1;  // (fused norm: a thread past the end stores nothing)
+    const int i = active ? i0 : end - 1;  // (fused norm: a thread past the end stores nothing)
     const int p = a.parity0 + blockIdx.y;
     if (a.skip && a.skip[(EPI == EPI_DWF ? 0 : rhs) * a.skip_stride]) return;
 
@@ -181,7 +182,8 @@ __global__ void __launch_bounds__(128) wilson_hop_kernel(const HopArgs a) {
 
 template <int P>
 cudaError_t launch_hop_prec(const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st) {
-    dim3 grid(((a.g.Vh + block - 1) / block) * a.nrhs, a.nparity);
+    const int nsite = a.nsite ? a.nsite : a.g.Vh;
+    dim3 grid(((nsite + block - 1) / block) * a.nrhs, a.nparity);
     dim3 blk(block);
     const bool red = a.red_partial != nullptr;
     if (red && epi == EPI_HOP) return cudaErrorInvalidValue;

@@ -397,14 +397,15 @@ __global__ void __launch_bounds__(NT) wilson_hop_async_kernel(const HopArgs a) {
     const int t = threadIdx.x;
     const int rhs = blockIdx.x % a.nrhs;
     const Geom& g = a.g;
-    const int i0 = (blockIdx.x / a.nrhs) * NT + t;
-    const bool active = i0 < g.Vh;
+    const int end = a.nsite ? a.site0 + a.nsite : g.Vh;
+    const int i0 = a.site0 + (blockIdx.x / a.nrhs) * NT + t;
+    const bool active = i0 < end;
     // without the fused norm there is no block barrier: a thread past the end leaves;
     // with it, such a thread recomputes the last site and stores nothing
     if constexpr (!RED) {
         if (!active) return;
     }
-    const int i = active ? i0 : g.Vh - 1;
+    const int i = active ? i0 : end - 1;
     const int p = a.parity0 + blockIdx.y;
     if (a.skip && a.skip[(EPI == EPI_DWF ? 0 : rhs) * a.skip_stride]) return;  // uniform per block
     cplx<T> o[12];
@@ -439,7 +440,8 @@ cudaError_t launch_async_one(const HopArgs& a, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    dim3 grid(((a.g.Vh + NT - 1) / NT) * a.nrhs, a.nparity);
+    const int nsite = a.nsite ? a.nsite : a.g.Vh;
+    dim3 grid(((nsite + NT - 1) / NT) * a.nrhs, a.nparity);
     kern<<<grid, NT, smem, st>>>(a);
     return cudaGetLastError();
 }

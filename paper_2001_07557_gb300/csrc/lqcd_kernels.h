@@ -25,6 +25,7 @@ struct HopArgs {
     size_t in_rhs, out_rhs, x_rhs;
     int parity0;  // first output parity
     int nparity;  // 1 (one parity) or 2 (both: full-lattice operator)
+    int site0, nsite;  // output checkerboard sites [site0, site0 + nsite) of each parity (nsite 0: all Vh)
     int nrhs;     // right-hand sides, or Ls for the domain-wall epilogue
     double c_hop, c_diag;
     int Ls;

@@ -26,8 +26,8 @@ STATUS = {0: "LQ_OK", -1: "LQ_ERR_ARG", -2: "LQ_ERR_LAYOUT", -3: "LQ_ERR_CUDA", 
 
 # every function the header declares
 EXPORTS = ["lq_create", "lq_destroy", "lq_field_bytes", "lq_convert", "dslash_apply", "dslash_dag_apply",
-           "dwf_dslash_apply", "dwf_schur_apply", "dwf_eo_prepare", "dwf_eo_reconstruct", "lq_dot", "lq_dot_noalloc", "cg_solve", "lq_batch_cg_solve", "lq_su3_mul",
-           "lq_wait_timeouts", "lq_test_stalled_wait", "lq_status_string"]
+           "dwf_dslash_apply", "dwf_schur_apply", "dwf_eo_prepare", "dwf_eo_reconstruct", "lq_dot", "lq_dot_noalloc", "cg_solve", "lq_batch_cg_solve", "dslash_apply_slices",
+           "lq_face_copy", "lq_su3_mul", "lq_wait_timeouts", "lq_test_stalled_wait", "lq_status_string"]
 LQ_DOT_NOALLOC_MAX_RHS = 32
 
 
@@ -80,6 +80,8 @@ def lib():
         L.cg_solve.argtypes = [vp, vp, vp, ctypes.POINTER(lq_cg_params), ctypes.POINTER(lq_cg_stats), vp]
         L.lq_batch_cg_solve.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                         ctypes.POINTER(lq_cg_params), ctypes.POINTER(lq_cg_stats), vp]
+        L.dslash_apply_slices.argtypes = [vp, vp, vp, i, i, i, i, vp]
+        L.lq_face_copy.argtypes = [vp, vp, i, vp, vp, i, i, ctypes.c_double, vp]
         L.lq_su3_mul.argtypes = [vp, vp, vp, ctypes.c_long, i, vp]
         L.lq_wait_timeouts.argtypes = [ctypes.POINTER(ctypes.c_uint)]
         L.lq_test_stalled_wait.argtypes = []
@@ -236,3 +238,15 @@ def lq_wait_timeouts():
 def lq_test_stalled_wait():
     """Run one product tile whose barrier wait must run out (tests the timeout path)."""
     _check(lib().lq_test_stalled_wait(), "lq_test_stalled_wait")
+
+
+def dslash_apply_slices(h, out, inp, fmt, t0, t1, dagger=False, stream=None):
+    """Full-lattice D (or D^dag) on native fields with output on time slices [t0, t1) only."""
+    _check(lib().dslash_apply_slices(h, _ptr(out), _ptr(inp), fmt, int(t0), int(t1), int(dagger), _stream(stream)),
+           "dslash_apply_slices")
+
+
+def lq_face_copy(hd, dst, t_dst, hs, src, t_src, fmt, scale=1.0, stream=None):
+    """Time slice t_src of src (hs's lattice) times scale into slice t_dst of dst (hd's lattice)."""
+    _check(lib().lq_face_copy(hd, _ptr(dst), int(t_dst), hs, _ptr(src), int(t_src), fmt, float(scale),
+                              _stream(stream)), "lq_face_copy")
