@@ -78,6 +78,8 @@ def _configure(L):
     L.orc_cg.argtypes = [i, p, p, p, ctypes.POINTER(Params), d, i, i4, ctypes.POINTER(d)]
     L.orc_cg.restype = i
     L.orc_su3_mul.argtypes = [p, p, p, ctypes.c_long]
+    L.orc_dwf_mobius_dslash.argtypes = [p, p, p, i4, i4, i, d, d, d, d, i]
+    L.orc_dwf_mobius_dslash.restype = i
     L.orc_dwf_m5.argtypes = [p, p, ctypes.c_long, i, d, d, i]
     L.orc_dwf_m5_inv.argtypes = [p, p, ctypes.c_long, i, d, d, i]
     L.orc_dwf_m5_inv.restype = i
@@ -193,6 +195,16 @@ def dwf_dslash(psi5, U, dims, Ls, M5, mf, bc=(1, 1, 1, -1), dagger=False):
     out = np.empty_like(psi5)
     rc = lib().orc_dwf_dslash(_ptr(out), _ptr(psi5), _ptr(U), _i4(dims), _i4(bc), int(Ls), M5, mf,
                               int(dagger))
+    assert rc == OK, rc
+    return out
+
+
+def dwf_mobius_dslash(psi5, U, dims, Ls, M5, mf, b5, c5, bc=(1, 1, 1, -1), dagger=False):
+    """Moebius D_M psi = (b5 D_W + 1) psi + (c5 D_W - 1) S psi (dagger: its adjoint) on [Ls][V][4][3]."""
+    psi5, U = _c(psi5), _c(U)
+    out = np.empty_like(psi5)
+    rc = lib().orc_dwf_mobius_dslash(_ptr(out), _ptr(psi5), _ptr(U), _i4(dims), _i4(bc), int(Ls), M5, mf, b5, c5,
+                                     int(dagger))
     assert rc == OK, rc
     return out
 

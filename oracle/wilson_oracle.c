@@ -34,6 +34,10 @@
  *  - CG (Hestenes-Stiefel) on A x = b with A = K^dag K for K = D, Mhat, D_dw or
  *    the domain-wall Mhat,
  *    x0 = 0, stopping when |r|/|b| < tol.
+ *  - Moebius domain wall (b5, c5; b5 = 1, c5 = 0 is the Shamir form above), with
+ *    S psi(s) = P- psi(s+1) + P+ psi(s-1) under the same walls (-mf):
+ *      D_M psi = (b5 D_W(-M5) + 1) psi + (c5 D_W(-M5) - 1) S psi,
+ *      D_M^dag psi = (b5 D_W^dag + 1) psi + S^dag (c5 D_W^dag - 1) psi.
  *  - Even-odd (4-d parity) Schur complement of the domain-wall operator.  With
  *    M5 the part of D_dw that stays on a 4-d site,
  *      (M5 psi)(s) = (5 - M5) psi(s) - P- psi(s+1) - P+ psi(s-1)   (walls as above),
@@ -314,6 +318,59 @@ int orc_dwf_dslash(cplx *out, const cplx *in, const cplx *U, const int d[4], con
         add_spin(o, cp, Pup, in + sp * n4, V);
         add_spin(o, cm, Pdn, in + sm * n4, V);
     }
+    return ORC_OK;
+}
+
+/* ----------------------------------------------------- Moebius domain wall */
+
+/* out = S in (dagger: S^dag) on 5-d fields [Ls][nsites][4][3]:
+   S psi(s) = P- psi(s+1) + P+ psi(s-1), walls: P- psi(Ls) -> -mf P- psi(0), P+ psi(-1) -> -mf P+ psi(Ls-1). */
+static void dwf_shift(cplx *out, const cplx *in, long nsites, int Ls, double mf, int dagger)
+{
+    cplx g5[4][4], Pp[4][4], Pm[4][4];
+    orc_gamma(4, g5);
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+            cplx id = (a == b) ? 1.0 : 0.0;
+            Pp[a][b] = 0.5 * (id + g5[a][b]);
+            Pm[a][b] = 0.5 * (id - g5[a][b]);
+        }
+    const cplx(*Pup)[4] = dagger ? (const cplx(*)[4])Pp : (const cplx(*)[4])Pm;
+    const cplx(*Pdn)[4] = dagger ? (const cplx(*)[4])Pm : (const cplx(*)[4])Pp;
+    long n4 = nsites * SITE_DOF;
+    memset(out, 0, (size_t)Ls * n4 * sizeof(cplx));
+    for (int s = 0; s < Ls; ++s) {
+        int sp = s + 1, sm = s - 1;
+        double cp = 1.0, cm = 1.0;
+        if (sp == Ls) { sp = 0; cp = -mf; }
+        if (sm < 0) { sm = Ls - 1; cm = -mf; }
+        add_spin(out + s * n4, cp, Pup, in + sp * n4, nsites);
+        add_spin(out + s * n4, cm, Pdn, in + sm * n4, nsites);
+    }
+}
+
+/* out = D_M in (dagger: D_M^dag), 5-d fields [Ls][V][4][3]. */
+int orc_dwf_mobius_dslash(cplx *out, const cplx *in, const cplx *U, const int d[4], const int bc[4], int Ls,
+                          double M5, double mf, double b5, double c5, int dagger)
+{
+    long V = orc_volume(d), n4 = V * SITE_DOF, n5 = (long)Ls * n4;
+    cplx *t = malloc((size_t)n5 * sizeof(cplx)), *u = malloc((size_t)n5 * sizeof(cplx));
+    if (!t || !u) { free(t); free(u); return ORC_ERR_NOMEM; }
+    if (!dagger) {
+        dwf_shift(t, in, V, Ls, mf, 0);                                  /* t = S in              */
+        for (long i = 0; i < n5; ++i) u[i] = b5 * in[i] + c5 * t[i];      /* u = b5 in + c5 S in   */
+        for (int s = 0; s < Ls; ++s)                                      /* out = D_W u           */
+            orc_wilson_dslash(out + s * n4, u + s * n4, U, d, bc, -M5, 1.0, 0);
+        for (long i = 0; i < n5; ++i) out[i] += in[i] - t[i];            /* + in - S in           */
+    } else {
+        for (int s = 0; s < Ls; ++s)                                      /* t = D_W^dag in        */
+            orc_wilson_dslash(t + s * n4, in + s * n4, U, d, bc, -M5, 1.0, 1);
+        for (long i = 0; i < n5; ++i) u[i] = c5 * t[i] - in[i];           /* u = (c5 D_W^dag - 1) in */
+        dwf_shift(out, u, V, Ls, mf, 1);                                  /* out = S^dag u         */
+        for (long i = 0; i < n5; ++i) out[i] += b5 * t[i] + in[i];       /* + (b5 D_W^dag + 1) in */
+    }
+    free(t);
+    free(u);
     return ORC_OK;
 }
 

@@ -39,6 +39,10 @@ MUTANTS = [
     ("domain-wall wall sign", "if (sp == Ls) { sp = 0; cp = mf; }", "if (sp == Ls) { sp = 0; cp = -mf; }",
      ["dwf"]),
     ("CG beta inverted", "double beta = rr_new / rr;", "double beta = rr / rr_new;", ["cg"]),
+    ("Moebius c5 term applied without the shift", "for (long i = 0; i < n5; ++i) u[i] = b5 * in[i] + c5 * t[i];",
+     "for (long i = 0; i < n5; ++i) u[i] = b5 * in[i] + c5 * in[i];", ["mobius"]),
+    ("Moebius dagger with the shift after the hop's b5 part", "for (long i = 0; i < n5; ++i) u[i] = c5 * t[i] - in[i];",
+     "for (long i = 0; i < n5; ++i) u[i] = (c5 + b5) * t[i] - in[i];", ["mobius"]),
     ("domain-wall Schur complement sign", "for (long i = 0; i < n5; ++i) out[i] -= t[i];",
      "for (long i = 0; i < n5; ++i) out[i] += t[i];", ["dwf_eo"]),
     ("domain-wall M5 inverse ignores the dagger", "orc_dwf_m5(col, e, 1, Ls, M5, mf, dagger);",
@@ -66,6 +70,8 @@ def run_pin(kind, orc):
         pins.test_dwf_free_field_closed_form(orc)
     elif kind == "cg":
         pins.test_cg_matches_dense_lu_on_4444(orc)
+    elif kind == "mobius":
+        pins.test_mobius_reduces_to_shamir_and_its_c5_term_is_dw_times_s(orc)
     elif kind == "dwf_eo":
         pins.test_dwf_eo_schur_solve_matches_full_solve(orc)
     elif kind == "su3":

@@ -370,6 +370,32 @@ def dense_map(fn, n):
     return M
 
 
+def test_mobius_reduces_to_shamir_and_its_c5_term_is_dw_times_s(orc):
+    """Moebius D_M(b5, c5): b5 = 1, c5 = 0 gives the Shamir operator (a separate
+    code path); D_M is affine in (b5, c5), its b5 part is D_W on every slice and
+    its c5 part is D_W applied to S psi, where S psi = -M5op(psi) at M5 = 5 comes
+    from the pinned site-local operator; the dagger is the adjoint."""
+    dims, Ls, M5, mf = (2, 2, 2, 4), 4, 1.8, 0.07
+    V = 32
+    U = inputs.gauge_field(dims, "random", seed=31)
+    psi = inputs.gaussian_spinor(V, seed=32, nrhs=Ls)
+    y = inputs.gaussian_spinor(V, seed=33, nrhs=Ls)
+    for dag in (False, True):
+        shamir = orc.dwf_dslash(psi, U, dims, Ls, M5, mf, dagger=dag)
+        assert rel(orc.dwf_mobius_dslash(psi, U, dims, Ls, M5, mf, 1.0, 0.0, dagger=dag), shamir) < 1e-14
+    D = lambda b5, c5: orc.dwf_mobius_dslash(psi, U, dims, Ls, M5, mf, b5, c5)  # noqa: E731
+    base = D(0.0, 0.0)
+    DW = np.stack([orc.wilson_dslash(psi[s], U, dims, -M5) for s in range(Ls)])
+    assert rel(D(1.0, 0.0) - base, DW) < 1e-13
+    S = -orc.dwf_m5(psi, Ls, 5.0, mf)
+    DWS = np.stack([orc.wilson_dslash(S[s], U, dims, -M5) for s in range(Ls)])
+    assert rel(D(0.0, 1.0) - base, DWS) < 1e-13
+    assert rel(D(1.5, 0.5) - base, 1.5 * DW + 0.5 * DWS) < 1e-13
+    lhs = np.vdot(y.ravel(), orc.dwf_mobius_dslash(psi, U, dims, Ls, M5, mf, 1.5, 0.5).ravel())
+    rhs = np.vdot(orc.dwf_mobius_dslash(y, U, dims, Ls, M5, mf, 1.5, 0.5, dagger=True).ravel(), psi.ravel())
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
 def test_dwf_m5_is_the_zero_link_operator(orc):
     """M5 (the site-local part of D_dw) equals D_dw with all links zero, where
     the 4-d hop vanishes; also for the dagger.  Catches a wrong diagonal
