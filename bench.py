@@ -953,6 +953,28 @@ def other_configs(lqcd, torch):
     res["eo_schur_f32"] = {"ms": ms, "gflops_hops": 2 * FLOP_PER_SITE * (V // 2) * Ls / (ms * 1e-3) / 1e9,
                            "note": "flops of the two half-lattice 4-d hops only"}
     lqcd.lq_destroy(h)
+    # Moebius (b5 = 1.5, c5 = 0.5, b5 - c5 = 1): one FP32 operator application and the FP64-refined solve
+    hm = lqcd.lq_create(lqcd.make_params(dims, Ls=Ls, M5=1.8, mf=0.01, mobius=True, b5=1.5, c5=0.5),
+                        torch.from_numpy(U).cuda())
+    nat = lqcd.LQ_NATIVE | lqcd.LQ_F32
+    nb = lqcd.lq_field_bytes(hm, nat, five_d=True)
+    a_, b_ = (torch.empty(nb, dtype=torch.uint8, device="cuda") for _ in range(2))
+    lqcd.lq_convert(hm, a_, nat, eta, lqcd.LQ_F64, five_d=True, stream=st)
+    ms = _time(lambda: lqcd.dwf_dslash_apply(hm, b_, a_, nat, False, stream=st), st, 20, torch)
+    bm = torch.empty_like(eta)
+    lqcd.dwf_dslash_apply(hm, bm, eta, lqcd.LQ_F64, True)
+    x = torch.zeros_like(bm)
+    cp = lqcd.make_cg_params(lqcd.LQ_OP_DWF_NORMAL, lqcd.LQ_CG_MIXED, lqcd.LQ_F64, tol=1e-10, maxiter=40000,
+                             inner=lqcd.LQ_F32, inner_tol=1e-6)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, stt = lqcd.cg_solve(hm, x, bm, cp, check=False)
+    res["mobius_b1.5_c0.5"] = {"dslash_f32_ms": ms, "gflops_4d": FLOP_PER_SITE * V * Ls / (ms * 1e-3) / 1e9,
+                               "cg_status": rc, "cg_seconds": time.perf_counter() - t0, "cg_iters": stt[0].iters,
+                               "cg_true_rel_residual": stt[0].true_rel_residual,
+                               "note": "two 5th-dimension passes + one Wilson hop launch per application"}
+    lqcd.lq_destroy(hm)
+    del a_, b_
     out["c5_16x4xLs16_dwf"] = res
     out["halo_2rank_32x4"] = halo_emulation(lqcd, torch, hbm)
     out["su3_mul"] = su3_sweep(lqcd, torch, st, hbm, 20)

@@ -93,6 +93,10 @@ typedef struct {
     double M5;       /* domain-wall height */
     double mf;       /* domain-wall quark mass */
     int compress12;  /* 1: links stored as their first two rows, row 3 = conj(row1 x row2) */
+    int mobius;      /* 0: Shamir domain wall; 1: Moebius with b5, c5 (FP64/FP32 fields, no even-odd form):
+                        D_M = (b5 D_W(-M5) + 1) + (c5 D_W(-M5) - 1) S,  S psi(s) = P- psi(s+1) + P+ psi(s-1)
+                        (walls -mf); b5 = 1, c5 = 0 is the Shamir operator */
+    double b5, c5;   /* Moebius coefficients (read only when mobius = 1) */
 } lq_params;
 
 typedef struct lq_handle lq_handle;
@@ -137,8 +141,9 @@ int dslash_apply(lq_handle *h, void *out, const void *in, int fmt, int parity, i
 int dslash_dag_apply(lq_handle *h, void *out, const void *in, int fmt, int parity, int nrhs, void *stream);
 
 /*
- * dwf_dslash_apply: Shamir domain-wall operator D_dw (dagger != 0: D_dw^dag)
- * on one 5-d field of Ls slices (lq_params.Ls), layout by fmt as above.
+ * dwf_dslash_apply: domain-wall operator D_dw (dagger != 0: D_dw^dag) on one
+ * 5-d field of Ls slices (lq_params.Ls), layout by fmt as above: Shamir, or
+ * Moebius when lq_params.mobius = 1 (then FP64/FP32 only, LQ_ERR_ARG else).
  */
 int dwf_dslash_apply(lq_handle *h, void *out, const void *in, int fmt, int dagger, void *stream);
 
@@ -156,7 +161,8 @@ int dwf_dslash_apply(lq_handle *h, void *out, const void *in, int fmt, int dagge
  * and lq_convert handle it as subset LQ_EVEN with nrhs = Ls.  A full 5-d field
  * is the five_d layout above.  fmt: LQ_F64 or LQ_F32, site-major or native
  * (FP16/BF16: LQ_ERR_ARG).  All three are asynchronous on `stream` and
- * reject overlapping buffers (LQ_ERR_ARG); they need lq_params.Ls >= 1.
+ * reject overlapping buffers (LQ_ERR_ARG); they need lq_params.Ls >= 1 and the
+ * Shamir form (lq_params.mobius = 0).
  *
  * dwf_schur_apply: out_e = Mhat in_e (dagger != 0: Mhat^dag in_e), 5-d half fields.
  * dwf_eo_prepare: bhat_e = eta_e - M_eo M5^{-1} eta_o from a full 5-d source eta.

@@ -173,7 +173,60 @@ int native_wilson_schur(lq_handle* h, int prec, char* out, const char* in, char*
     return status_of(launch_hop(prec, a, link_r12(h, prec), dag, EPI_DIAG, h->hop_block[prec], st));
 }
 
+// Moebius domain wall, D_M = D_W(-M5) chi + psi - S psi with chi = b5 psi + c5 S psi:
+//   chi = b5 psi + c5 S psi;  w = [(4-M5) b5 + 1] psi + [(4-M5) c5 - 1] S psi  (5th-dimension kernels)
+//   out = -1/2 H chi + w                         (one Wilson hop launch, the Ls slices as right-hand sides)
+// and D_M^dag psi = (b5 + c5 S^dag) D_W^dag psi + (1 - S^dag) psi:
+//   z = (4-M5) psi - 1/2 H^dag psi;  out = b5 z + c5 S^dag z + psi - S^dag psi.
+// The fused norm of the solver rides on the hop, whose per-slice partials
+// fill the same slots as the Shamir operator's one group.
+static int native_dwf_mobius(lq_handle* h, int prec, char* out, const char* in, bool dag, cudaStream_t st) {
+    if (prec != LQ_F64 && prec != LQ_F32) return LQ_ERR_ARG;
+    const int Ls = h->p.Ls;
+    const size_t blk = native_block_bytes(h, prec);
+    const double b5 = h->p.b5, c5 = h->p.c5, d4 = 4.0 - h->p.M5, mf = h->p.mf;
+    const size_t f5 = 2 * blk * (size_t)Ls;
+    void *chi, *w;
+    int rc;
+    if ((rc = ensure_ws(h, WS_MOB, f5, &chi)) || (rc = ensure_ws(h, WS_MOB + 1, f5, &w))) return rc;
+    HopArgs a;
+    if (!dag) {
+        if (launch_m5_lincomb(prec, chi, in, nullptr, h->g.Vh, 2, 2 * blk, Ls, b5, c5, 0, 0, mf, false, st) !=
+                cudaSuccess ||
+            launch_m5_lincomb(prec, w, in, nullptr, h->g.Vh, 2, 2 * blk, Ls, d4 * b5 + 1, d4 * c5 - 1, 0, 0, mf, false,
+                              st) != cudaSuccess)
+            return LQ_ERR_CUDA;
+        if ((rc = prep_wilson_full(h, prec, out, static_cast<const char*>(chi), Ls, &a, st))) return rc;
+        for (int p = 0; p < 2; ++p) {
+            a.in[p] = static_cast<const char*>(chi) + (size_t)(1 - p) * blk;
+            a.x[p] = static_cast<const char*>(w) + (size_t)p * blk;
+            a.out[p] = out + (size_t)p * blk;
+        }
+        a.in_rhs = a.out_rhs = a.x_rhs = 2 * blk;
+        a.c_diag = 1.0;
+        a.skip_stride = 0;  // the slices of one system share the system's skip flag
+        return status_of(launch_hop(prec, a, link_r12(h, prec), false, EPI_DIAG, h->hop_block[prec], st));
+    }
+    if ((rc = prep_wilson_full(h, prec, static_cast<char*>(chi), in, Ls, &a, st))) return rc;
+    for (int p = 0; p < 2; ++p) {
+        a.in[p] = in + (size_t)(1 - p) * blk;
+        a.x[p] = in + (size_t)p * blk;
+        a.out[p] = static_cast<char*>(chi) + (size_t)p * blk;
+    }
+    a.in_rhs = a.out_rhs = a.x_rhs = 2 * blk;
+    a.c_diag = d4;
+    a.skip_stride = 0;
+    a.red_partial = nullptr;
+    a.red_st = nullptr;
+    if ((rc = status_of(launch_hop(prec, a, link_r12(h, prec), true, EPI_DIAG, h->hop_block[prec], st)))) return rc;
+    return launch_m5_lincomb(prec, out, chi, in, h->g.Vh, 2, 2 * blk, Ls, b5, c5, 1.0, -1.0, mf, true, st) ==
+                   cudaSuccess
+               ? LQ_OK
+               : LQ_ERR_CUDA;
+}
+
 int native_dwf(lq_handle* h, int prec, char* out, const char* in, bool dag, cudaStream_t st) {
+    if (h->p.mobius) return native_dwf_mobius(h, prec, out, in, dag, st);
     const char* L;
     size_t lb;
     int rc = get_links(h, prec, &L, &lb, st);
@@ -357,6 +410,7 @@ int lq_create(lq_handle** hp, const lq_params* p, const void* U, int U_prec, voi
     if (V / 2 >= (1LL << 27)) return LQ_ERR_LAYOUT;  // cb indices < 2^27: exact fast division
     if (p->r != 1.0) return LQ_ERR_ARG;
     if (p->Ls < 0 || p->Ls > 4096) return LQ_ERR_ARG;
+    if (p->mobius && (p->mobius != 1 || p->Ls < 1)) return LQ_ERR_ARG;
     lq_handle* h = new (std::nothrow) lq_handle;
     if (!h) return LQ_ERR_NOMEM;
     std::memset(h, 0, sizeof(*h));
@@ -502,7 +556,7 @@ int dwf_dslash_apply(lq_handle* h, void* out, const void* in, int fmt, int dagge
 static int dwf_eo_args(lq_handle* h, int fmt) {
     if (!h || !valid_fmt(fmt)) return LQ_ERR_ARG;
     const int prec = fmt & 0xF;
-    if (h->p.Ls < 1 || (prec != LQ_F64 && prec != LQ_F32)) return LQ_ERR_ARG;
+    if (h->p.Ls < 1 || h->p.mobius || (prec != LQ_F64 && prec != LQ_F32)) return LQ_ERR_ARG;
     return LQ_OK;
 }
 

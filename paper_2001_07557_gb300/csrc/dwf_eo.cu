@@ -1,5 +1,6 @@
-// dwf_eo.cu -- the site-local inverse M5^{-1} of the even-odd preconditioned
-// domain-wall operator.
+// dwf_eo.cu -- the site-local (5th-dimension) kernels of the domain-wall
+// operators: the inverse M5^{-1} of the even-odd preconditioned form, and the
+// linear combinations with the shift S that build the Moebius operator.
 //
 // M5 is the part of D_dw that stays on a 4-d site (Shamir form, walls -mf):
 //   (M5 psi)(s) = a psi(s) - P- psi(s+1) - P+ psi(s-1),   a = 5 - M5.
@@ -71,7 +72,56 @@ __global__ void __launch_bounds__(256) m5inv_kernel(char* out, const char* in, i
     }
 }
 
+// out(s) = a u(s) + b (S u)(s) + c v(s) + d (S v)(s)   (S^dag for dag; v may be null)
+// with S psi(s) = P- psi(s+1) + P+ psi(s-1), walls -mf.  For planes of spins 0,1
+// (P+) S reads slice s-1, for spins 2,3 (P-) slice s+1; the dagger swaps them.
+// Fields: Ls slices at slice_stride bytes, each nblk parity blocks of Vh sites.
+// One thread per (block, plane, site) walks the slices.
+template <int P>
+__global__ void __launch_bounds__(256) m5_lincomb_kernel(char* out, const char* u, const char* v, int Vh, int nblk,
+                                                         size_t slice_stride, int Ls, double a_d, double b_d,
+                                                         double c_d, double d_d, double mf_d, int dag) {
+    using V = typename std::conditional<P == LQ_F64, double2, float4>::type;
+    using T = typename std::conditional<P == LQ_F64, double, float>::type;
+    constexpr int NPL = P == LQ_F64 ? 12 : 6;
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)nblk * NPL * Vh) return;
+    const int blk = (int)(idx / ((long)NPL * Vh));
+    const int rem = (int)(idx - (long)blk * NPL * Vh);
+    const int k = rem / Vh, i = rem - k * Vh;
+    const bool down = (k < NPL / 2) != (dag != 0);  // S reads slice s-1 (else s+1)
+    const size_t off = (size_t)blk * NPL * Vh * sizeof(V) + ((size_t)k * Vh + i) * sizeof(V);
+    const T a = (T)a_d, b = (T)b_d, c = (T)c_d, d = (T)d_d, mf = (T)mf_d;
+    auto at = [&](const char* f, int s) { return *reinterpret_cast<const V*>(f + (size_t)s * slice_stride + off); };
+    for (int s = 0; s < Ls; ++s) {
+        int sn = down ? s - 1 : s + 1;
+        T w = 1;
+        if (sn < 0) sn = Ls - 1, w = -mf;
+        if (sn >= Ls) sn = 0, w = -mf;
+        V r = axpby4<V, T>(a, at(u, s), b * w, at(u, sn));
+        if (v) r = axpby4<V, T>((T)1, r, (T)1, axpby4<V, T>(c, at(v, s), d * w, at(v, sn)));
+        *reinterpret_cast<V*>(out + (size_t)s * slice_stride + off) = r;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_m5_lincomb(int prec, void* out, const void* u, const void* v, int Vh, int nblk, size_t slice_stride,
+                              int Ls, double a, double b, double c, double d, double mf, bool dag, cudaStream_t st) {
+    const int npl = prec == LQ_F64 ? 12 : 6;
+    const long n = (long)nblk * npl * Vh;
+    const int grid = (int)((n + 255) / 256);
+    auto o = static_cast<char*>(out);
+    auto pu = static_cast<const char*>(u);
+    auto pv = static_cast<const char*>(v);
+    if (prec == LQ_F64)
+        m5_lincomb_kernel<LQ_F64><<<grid, 256, 0, st>>>(o, pu, pv, Vh, nblk, slice_stride, Ls, a, b, c, d, mf, dag);
+    else if (prec == LQ_F32)
+        m5_lincomb_kernel<LQ_F32><<<grid, 256, 0, st>>>(o, pu, pv, Vh, nblk, slice_stride, Ls, a, b, c, d, mf, dag);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
 
 cudaError_t launch_m5inv(int prec, void* out, const void* in, int Vh, size_t out_stride, size_t in_stride, int Ls,
                          double M5, double mf, bool dag, cudaStream_t st) {

@@ -20,7 +20,7 @@ struct lq_handle {
     struct Buf {
         void* ptr;
         size_t bytes;
-    } ws[24];         // workspace buffers, grown on demand
+    } ws[26];         // workspace buffers, grown on demand
     int hop_block[4]; // threads per block of the hop kernels, per precision
     const int* skip;  // per-rhs early-exit flags the solvers hand to the hop launches (else null)
     int skip_stride;
@@ -38,7 +38,7 @@ namespace lq {
 // workspace slots: conversions 0-2; solver vectors 3-7 (inner CG), 8-12 (FP64
 // residuals), 13-15 (defect-correction vectors), 16-17 (block CG), 20-23 (FP32
 // middle level of the three-precision solve); 18 lq_dot partials; 19 solver scalars
-enum { WS_IN = 0, WS_OUT = 1, WS_TMP = 2, WS_CG0 = 3, WS_DOT = 18, WS_CTL = 19 };
+enum { WS_IN = 0, WS_OUT = 1, WS_TMP = 2, WS_CG0 = 3, WS_DOT = 18, WS_CTL = 19, WS_MOB = 24 /* 24, 25 */ };
 
 inline int status_of(cudaError_t e) { return e == cudaSuccess ? LQ_OK : LQ_ERR_CUDA; }
 

@@ -61,6 +61,13 @@ cudaError_t launch_hop(int prec, const HopArgs& a, bool r12, bool dag, int epi, 
 // bytes.  In place allowed.  (dwf_eo.cu)
 cudaError_t launch_m5inv(int prec, void* out, const void* in, int Vh, size_t out_stride, size_t in_stride, int Ls,
                          double M5, double mf, bool dag, cudaStream_t st);
+
+// out(s) = a u(s) + b (S u)(s) + c v(s) + d (S v)(s), S psi(s) = P- psi(s+1) +
+// P+ psi(s-1) with walls -mf (dag: S^dag); v may be null.  Native FP64/FP32
+// 5-d fields: Ls slices at slice_stride bytes of nblk parity blocks.  out must
+// not overlap u or v.  (dwf_eo.cu)
+cudaError_t launch_m5_lincomb(int prec, void* out, const void* u, const void* v, int Vh, int nblk, size_t slice_stride,
+                              int Ls, double a, double b, double c, double d, double mf, bool dag, cudaStream_t st);
 cudaError_t launch_hop_f64(const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st);
 cudaError_t launch_hop_f32(const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st);
 cudaError_t launch_hop_f16(const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st);

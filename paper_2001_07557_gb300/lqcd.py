@@ -40,7 +40,8 @@ class LqError(RuntimeError):
 class lq_params(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int * 4), ("bc", ctypes.c_int * 4), ("mass", ctypes.c_double),
                 ("r", ctypes.c_double), ("Ls", ctypes.c_int), ("M5", ctypes.c_double), ("mf", ctypes.c_double),
-                ("compress12", ctypes.c_int)]
+                ("compress12", ctypes.c_int), ("mobius", ctypes.c_int), ("b5", ctypes.c_double),
+                ("c5", ctypes.c_double)]
 
 
 class lq_cg_params(ctypes.Structure):
@@ -118,12 +119,14 @@ def _check(rc, where):
     return rc
 
 
-def make_params(dims, bc=(1, 1, 1, -1), mass=0.0, r=1.0, Ls=0, M5=0.0, mf=0.0, compress12=False) -> lq_params:
+def make_params(dims, bc=(1, 1, 1, -1), mass=0.0, r=1.0, Ls=0, M5=0.0, mf=0.0, compress12=False, mobius=False,
+                b5=1.0, c5=0.0) -> lq_params:
     p = lq_params()
     p.dims = (ctypes.c_int * 4)(*[int(d) for d in dims])
     p.bc = (ctypes.c_int * 4)(*[int(b) for b in bc])
     p.mass, p.r, p.Ls, p.M5, p.mf = float(mass), float(r), int(Ls), float(M5), float(mf)
     p.compress12 = int(bool(compress12))
+    p.mobius, p.b5, p.c5 = int(bool(mobius)), float(b5), float(c5)
     return p
 
 

@@ -34,10 +34,10 @@ def native_buffer(h, prec, subset=lqcd.LQ_FULL, nrhs=1, five_d=False):
 
 class Handle:
     def __init__(self, dims, U, mass=0.1, bc=(1, 1, 1, -1), Ls=0, M5=0.0, mf=0.0, compress12=False,
-                 U_prec=lqcd.LQ_F64):
+                 U_prec=lqcd.LQ_F64, **kw):
         ensure_built()
         self.dims = dims
-        self.params = lqcd.make_params(dims, bc=bc, mass=mass, Ls=Ls, M5=M5, mf=mf, compress12=compress12)
+        self.params = lqcd.make_params(dims, bc=bc, mass=mass, Ls=Ls, M5=M5, mf=mf, compress12=compress12, **kw)
         self.U = dev(U, U_prec)
         self.h = lqcd.lq_create(self.params, self.U, U_prec)
 
