@@ -125,6 +125,10 @@ int lq_field_bytes(const lq_handle *h, int fmt, int subset, int nrhs, int five_d
  * native, precision change).  subset as in lq_field_bytes; five_d selects the
  * 5-d layout.  dst and src must not overlap.  Site-major formats are
  * LQ_F64 / LQ_F32; LQ_F16 / LQ_BF16 exist only as native formats.
+ * dst and src may be device or managed memory, or pinned host memory mapped
+ * into the unified address space (cudaHostAlloc): the conversion kernel then
+ * reads or writes host memory over the host link, fusing the transfer with
+ * the conversion.  A pointer the device cannot address is LQ_ERR_LAYOUT.
  */
 int lq_convert(lq_handle *h, void *dst, int dst_fmt, const void *src, int src_fmt, int subset, int nrhs,
                int five_d, void *stream);

@@ -476,11 +476,31 @@ int lq_field_bytes(const lq_handle* h, int fmt, int subset, int nrhs, int five_d
     return LQ_OK;
 }
 
+// Can kernels on the current device dereference p?  Device and managed memory,
+// and pinned host memory mapped into the unified address space, can; other
+// host memory only where the device reads pageable memory (coherent host link).
+static bool device_accessible(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return true;
+    if (at.type == cudaMemoryTypeHost) return at.devicePointer == p;
+    int dev = 0, pageable = 0;
+    return cudaGetDevice(&dev) == cudaSuccess &&
+           cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev) == cudaSuccess && pageable;
+}
+
 int lq_convert(lq_handle* h, void* dst, int dst_fmt, const void* src, int src_fmt, int subset, int nrhs, int five_d,
                void* stream) {
     if (!h || !dst || !src || !valid_fmt(dst_fmt) || !valid_fmt(src_fmt)) return LQ_ERR_ARG;
     if (subset < LQ_FULL || subset > LQ_ODD) return LQ_ERR_ARG;
     if (!aligned16(dst) || !aligned16(src)) return LQ_ERR_LAYOUT;
+    {
+        DeviceGuard dg(h->device);
+        if (!device_accessible(dst) || !device_accessible(src)) return LQ_ERR_LAYOUT;
+    }
     if (five_d) {
         if (h->p.Ls < 1) return LQ_ERR_ARG;
         subset = LQ_FULL;

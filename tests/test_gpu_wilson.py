@@ -306,3 +306,19 @@ def test_full_size_domain_wall(prec):
         lqcd.lq_convert(H.h, y, lqcd.LQ_F64, yn, nat, five_d=True)
         got = host(y)
     check(got, oracle.dwf_dslash(psi, U, dims, Ls, 1.8, 0.01), prec)
+
+
+def test_convert_reads_and_writes_pinned_host_memory():
+    """lq_convert with a pinned host source and destination: the conversion
+    kernels address host memory directly; the round trip is exact."""
+    dims = (4, 4, 4, 4)
+    V = int(np.prod(dims))
+    psi = inputs.gaussian_spinor(V, seed=2401)
+    with Handle(dims, field(dims, "unit")) as H:
+        hx = torch.from_numpy(psi.astype(np.complex64)).pin_memory()
+        hy = torch.empty_like(hx).pin_memory()
+        n = native_buffer(H.h, lqcd.LQ_F32)
+        lqcd.lq_convert(H.h, n, lqcd.LQ_NATIVE | lqcd.LQ_F32, hx, lqcd.LQ_F32)
+        lqcd.lq_convert(H.h, hy, lqcd.LQ_F32, n, lqcd.LQ_NATIVE | lqcd.LQ_F32)
+        torch.cuda.synchronize()
+        assert torch.equal(hy, hx)
