@@ -416,12 +416,22 @@ def main():
     }
 
     if rank == 0 and not args.no_extras:
+        z64 = torch.empty_like(x64)  # the timed step's output, for its error against the oracle
+        lqcd.lq_convert(h, z64, lqcd.LQ_F64, z, nat, lqcd.LQ_EVEN, stream=sh)
+        stream.synchronize()
+        step_out = z64.cpu().numpy()
+        del z64
         lqcd.lq_destroy(h)
         h = lqcd.lq_create(prm, torch.from_numpy(U).cuda(), lqcd.LQ_F64)
         line["cg"] = cg_compare(h, lqcd, torch, psi_e, prec)
         line["e2e"] = e2e(h, lqcd, torch, dims, psi_e, prec, args, world)
         line["per_precision"] = precision_table(h, lqcd, torch, psi_e, Vh, args, U, dims, mass)
-        line["cpu_baseline"] = cpu_baseline(dims, mass, U, psi_e, Vh)
+        line["cpu_baseline"], want = cpu_baseline(dims, mass, U, psi_e, Vh)
+        line["error_vs_oracle"] = {
+            "rel_norm": float(np.linalg.norm(step_out - want) / np.linalg.norm(want)),
+            "max_abs_over_max": float(np.max(np.abs(step_out - want)) / np.max(np.abs(want))),
+            "what": f"the timed step's output ({args.prec} storage) against the FP64 oracle's Mhat^dag Mhat "
+                    "of the same source"}
         line["configs"] = other_configs(lqcd, torch)
     lqcd.lq_destroy(h)
     if rank == 0:
@@ -523,8 +533,15 @@ def precision_table(h, lqcd, torch, psi_e, Vh, args, U, dims, mass):
             st.synchronize()
             ms = e0.elapsed_time(e1) / reps
             gbs = Vh * algorithmic_bytes_per_site(p, r12, False) / (ms * 1e-3) / 1e9
-            out[f"{pname}_r{12 if r12 else 18}"] = {"gflops": FLOP_PER_SITE * Vh / (ms * 1e-3) / 1e9,
-                                                    "ms": ms, "model_gbs": gbs, "frac_hbm": gbs / hbm}
+            y64 = torch.empty_like(x64)
+            lqcd.lq_convert(hh, y64, lqcd.LQ_F64, b, nat, lqcd.LQ_EVEN, stream=st)
+            st.synchronize()
+            if p == 0:
+                ref = y64  # the FP64 hop, itself within 1e-15 of the oracle in the parity tests
+            key = f"{pname}_r{12 if r12 else 18}"
+            out[key] = {"gflops": FLOP_PER_SITE * Vh / (ms * 1e-3) / 1e9, "ms": ms, "model_gbs": gbs,
+                        "frac_hbm": gbs / hbm,
+                        "rel_err_vs_fp64": float(torch.linalg.vector_norm(y64 - ref) / torch.linalg.vector_norm(ref))}
             lqcd.lq_destroy(hh)
     return out
 
@@ -1017,15 +1034,16 @@ def inputs_odd(psi_e):
 
 
 def cpu_baseline(dims, mass, U, psi_e, Vh):
-    """Repeat the oracle's Mhat^dag Mhat on the full lattice until >= 10 s (at most 6 times)."""
+    """Repeat the oracle's Mhat^dag Mhat on the full lattice until >= 10 s (at most 6 times); returns the
+    timing entry and the oracle's output."""
     cores = host_cores()
     total, n = 0.0, 0
     while total < 10.0 and n < 6:
-        dt, _ = oracle_normal_op(dims, mass, U, psi_e)
+        dt, out = oracle_normal_op(dims, mass, U, psi_e)
         total += dt
         n += 1
-    return {"value": 4 * FLOP_PER_SITE * Vh * n / total / 1e9, "unit": "GFlop/s", "cores": cores, "kind": "oracle",
-            "sample": f"{n} Mhat^dag Mhat applications on the full {list(dims)} lattice, {total:.1f} s"}
+    return ({"value": 4 * FLOP_PER_SITE * Vh * n / total / 1e9, "unit": "GFlop/s", "cores": cores, "kind": "oracle",
+             "sample": f"{n} Mhat^dag Mhat applications on the full {list(dims)} lattice, {total:.1f} s"}, out)
 
 
 if __name__ == "__main__":

@@ -523,7 +523,8 @@ cudaError_t launch_dot(const VecRef& a, const VecRef& b, int Vh, int nblk, int n
 cudaError_t launch_cg_update(const VecRef& x, const VecRef& p, const VecRef& r, const VecRef& q, int Vh, int nblk,
                              int nrhs, const Scratch& sc, CgScalars* st, cudaStream_t s) {
     dim3 grid(grid_x(Vh, nblk), nrhs);
-    // precision combinations used by the solvers: all equal, or x, r in FP32 with p, q in FP16/BF16
+    // precision combinations used by the solvers: all equal; x, r in FP32 with p, q in FP16/BF16;
+    // x in FP32 with r, p, q in FP16/BF16
     if (x.prec == LQ_F64 && p.prec == LQ_F64 && r.prec == LQ_F64 && q.prec == LQ_F64)
         cg_update_kernel<LQ_F64, LQ_F64, LQ_F64, LQ_F64><<<grid, kThreads, 0, s>>>(x, p, r, q, Vh, nblk, sc.partial, sc.tickets, st);
     else if (x.prec == LQ_F32 && r.prec == LQ_F32 && p.prec == q.prec) {
@@ -533,6 +534,10 @@ cudaError_t launch_cg_update(const VecRef& x, const VecRef& p, const VecRef& r, 
         case LQ_BF16: cg_update_kernel<LQ_F32, LQ_BF16, LQ_F32, LQ_BF16><<<grid, kThreads, 0, s>>>(x, p, r, q, Vh, nblk, sc.partial, sc.tickets, st); break;
         default: return cudaErrorInvalidValue;
         }
+    } else if (x.prec == LQ_F32 && r.prec == p.prec && p.prec == q.prec && p.prec == LQ_F16) {
+        cg_update_kernel<LQ_F32, LQ_F16, LQ_F16, LQ_F16><<<grid, kThreads, 0, s>>>(x, p, r, q, Vh, nblk, sc.partial, sc.tickets, st);
+    } else if (x.prec == LQ_F32 && r.prec == p.prec && p.prec == q.prec && p.prec == LQ_BF16) {
+        cg_update_kernel<LQ_F32, LQ_BF16, LQ_BF16, LQ_BF16><<<grid, kThreads, 0, s>>>(x, p, r, q, Vh, nblk, sc.partial, sc.tickets, st);
     } else {
         return cudaErrorInvalidValue;
     }
