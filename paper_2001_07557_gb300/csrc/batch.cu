@@ -13,7 +13,8 @@
 //
 // The solve is the FP64 defect correction of cg.cu (FP64 solution and true
 // residuals per lattice; inner CG with p, A p in the inner storage precision
-// and the iterate and residual in FP32), or a plain FP32 CG.
+// and the iterate and residual in FP32), with an FP32 middle level between
+// the two for FP16/BF16 inner precisions, or a plain FP32 CG.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -33,6 +34,7 @@ namespace lq {
 namespace {
 
 constexpr int kIters = 8;  // iterations per graph replay
+constexpr double kMiddleTolBatch = 1e-5;  // the FP32 middle level's target, as in cg.cu
 
 struct Tune {
     int mult;
@@ -72,6 +74,7 @@ struct Lat {
     size_t b64, b32, bp;  // bytes of one nrhs field in FP64, FP32, inner precision
     char *X64, *B64, *R64, *E, *RIN, *r, *p, *q, *t, *tmp, *tmp2;  // native fields
     char *q64, *t64, *tmp64;
+    char *RIN0, *EM, *q32, *t32, *tmp32;  // FP32 middle level (16-bit inner precisions)
 };
 
 int alloc_lat(Lat& L, int op, int nr, int ip) {
@@ -95,6 +98,22 @@ int alloc_lat(Lat& L, int op, int nr, int ip) {
         int rc = ensure_ws(h, slot++, w.n, &p);
         if (rc) return rc;
         *w.ptr = static_cast<char*>(p);
+    }
+    L.RIN0 = L.EM = L.q32 = L.t32 = L.tmp32 = nullptr;
+    if (ip == LQ_F16 || ip == LQ_BF16) {
+        const size_t half32 = (size_t)spinor_site_bytes(LQ_F32) * Vh * nr;
+        struct {
+            char** ptr;
+            size_t n;
+            int slot;
+        } mid[] = {{&L.RIN0, L.b32, 14}, {&L.EM, L.b32, 15}, {&L.q32, L.b32, 16}, {&L.t32, L.b32, 17},
+                   {&L.tmp32, half32, 20}};
+        for (auto& w : mid) {
+            void* p;
+            int rc = ensure_ws(h, w.slot, w.n, &p);
+            if (rc) return rc;
+            *w.ptr = static_cast<char*>(p);
+        }
     }
     return LQ_OK;
 }
@@ -161,7 +180,8 @@ extern "C" int lq_batch_cg_solve(lq_handle** hs, int nlat, void** xs, const void
         if ((rc = alloc_lat(lat[l], op, nr, ip))) return rc;
         const char* L;
         size_t lb;
-        if ((rc = get_links(hs[l], ip, &L, &lb, s)) || (mixed && (rc = get_links(hs[l], LQ_F64, &L, &lb, s))))
+        if ((rc = get_links(hs[l], ip, &L, &lb, s)) || (mixed && (rc = get_links(hs[l], LQ_F64, &L, &lb, s))) ||
+            (mixed && ip != LQ_F32 && (rc = get_links(hs[l], LQ_F32, &L, &lb, s))))
             return rc;
     }
     // solver state of all (lattice, rhs) segments: scalars, tables, partials (first handle's workspace)
@@ -399,6 +419,61 @@ extern "C" int lq_batch_cg_solve(lq_handle** hs, int nlat, void** xs, const void
         return LQ_OK;
     };
 
+    // FP32 middle level: e = sum of inner corrections with A e = RIN to `target` (relative, per
+    // segment); the FP32 residual RIN0 - A e of every lattice is formed with its own FP32 operator.
+    // On return E holds e (the outer loop adds it to the FP64 solution).
+    auto middle = [&](double target, double itol, int maxit, std::vector<int>& its, int* most_out) -> int {
+        std::vector<double> r0(nseg, 0.0), rn(nseg, 0.0), relm(nseg, 1.0);
+        for (int l = 0; l < nlat; ++l) {
+            Lat& L = lat[l];
+            if (cudaMemcpyAsync(L.RIN0, L.RIN, L.b32, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+                cudaMemsetAsync(L.EM, 0, L.b32, s) != cudaSuccess)
+                return LQ_ERR_CUDA;
+            int e = norms(l, L.RIN0, LQ_F32, &r0[l * nr]);
+            if (e) return e;
+        }
+        int used = 0, most = 0;
+        for (int pass = 0; pass < 8 && used < maxit; ++pass) {
+            double reach = 0.5;
+            for (int g = 0; g < nseg; ++g)
+                if (r0[g] > 0 && relm[g] > target) reach = std::min(reach, 0.5 * target / relm[g]);
+            int e = inner(std::max(itol, reach), maxit - used);
+            if (e) return e;
+            int m = 0;
+            for (int g = 0; g < nseg; ++g) {
+                its[g] += host_st[g].iter;
+                m = std::max(m, host_st[g].iter);
+            }
+            used += std::max(m, 1);
+            most += m;
+            bool done = true;
+            for (int l = 0; l < nlat; ++l) {
+                Lat& L = lat[l];
+                const size_t s32 = (size_t)L.nblk * spinor_site_bytes(LQ_F32) * L.h->g.Vh;
+                VecRef EMv{L.EM, LQ_F32, s32}, Ev{L.E, LQ_F32, s32}, R0{L.RIN0, LQ_F32, s32},
+                    Rv{L.RIN, LQ_F32, s32}, Q{L.q32, LQ_F32, s32};
+                if (launch_axpby(EMv, Ev, 1.0, 1.0, L.h->g.Vh, L.nblk, nr, s) != cudaSuccess) return LQ_ERR_CUDA;
+                if ((e = apply_normal_one(L, op, LQ_F32, L.q32, L.EM, L.t32, L.tmp32, nr, s))) return e;
+                if (launch_axpby(Rv, R0, 1.0, 0.0, L.h->g.Vh, L.nblk, nr, s) != cudaSuccess ||
+                    launch_axpby(Rv, Q, -1.0, 1.0, L.h->g.Vh, L.nblk, nr, s) != cudaSuccess)
+                    return LQ_ERR_CUDA;
+                if ((e = norms(l, L.RIN, LQ_F32, &rn[l * nr]))) return e;
+                for (int k = 0; k < nr; ++k) {
+                    const int g = l * nr + k;
+                    if (r0[g] > 0) its[g] += 1;  // the FP32 residual is one more operator application
+                    relm[g] = r0[g] > 0 ? std::sqrt(rn[k + l * nr] / r0[g]) : 0.0;
+                    done = done && relm[g] <= target;
+                }
+            }
+            if (done) break;
+        }
+        for (int l = 0; l < nlat; ++l)
+            if (cudaMemcpyAsync(lat[l].E, lat[l].EM, lat[l].b32, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                return LQ_ERR_CUDA;
+        *most_out = most;
+        return LQ_OK;
+    };
+
     if (!mixed) {
         // plain FP32 CG: b is RIN, the solution accumulates in E
         if ((rc = inner(cp->tol, cp->maxiter))) {
@@ -488,14 +563,24 @@ extern "C" int lq_batch_cg_solve(lq_handle** hs, int nlat, void** xs, const void
             double reach = 0.5;  // the smallest reduction every unfinished right-hand side still needs
             for (int g = 0; g < nseg; ++g)
                 if (!conv[g] && rel[g] > 0) reach = std::min(reach, 0.5 * cp->tol / rel[g]);
-            const double need = std::max(itol, reach);
-            if (rc || (rc = inner(need, cp->maxiter - total_inner))) break;
             int most = 0;
-            for (int g = 0; g < nseg; ++g) {
-                iters[g] += host_st[g].iter;
-                most = std::max(most, host_st[g].iter);
-                if (!conv[g]) outer[g] += 1;
+            if (ip == LQ_F32) {
+                const double need = std::max(itol, reach);
+                if (rc || (rc = inner(need, cp->maxiter - total_inner))) break;
+                for (int g = 0; g < nseg; ++g) {
+                    iters[g] += host_st[g].iter;
+                    most = std::max(most, host_st[g].iter);
+                }
+            } else {
+                // three precisions, as in cg.cu: an FP32 defect correction (FP32 residuals of every
+                // lattice) around the batched 16-bit inner CG takes each correction to FP32's reach,
+                // so the FP64 residuals above are needed about twice per solve
+                if (rc || (rc = middle(std::max(kMiddleTolBatch, reach), itol, cp->maxiter - total_inner,
+                                       iters, &most)))
+                    break;
             }
+            for (int g = 0; g < nseg; ++g)
+                if (!conv[g]) outer[g] += 1;
             total_inner += std::max(most, 1);
             for (int l = 0; l < nlat && rc == LQ_OK; ++l) {
                 Lat& L = lat[l];
