@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 SHAPES = [(4, 4, 4, 4), (6, 6, 6, 6), (4, 4, 8, 8), (8, 8, 8, 8)]
 
 
-@pytest.mark.parametrize("inner", [lqcd.LQ_F16, lqcd.LQ_F32])
+@pytest.mark.parametrize("inner", [lqcd.LQ_F16, lqcd.LQ_BF16, lqcd.LQ_F32])
 @pytest.mark.parametrize("op", [lqcd.LQ_OP_WILSON_EO_NORMAL, lqcd.LQ_OP_WILSON_NORMAL])
 def test_uneven_batch_mixed(inner, op):
     nr = 3
@@ -72,6 +72,35 @@ def test_batch_plain_fp32_and_argument_checks():
             assert rc == -1
         rc, _ = lqcd.lq_batch_cg_solve([Hs[0].h, Hs[0].h], xs, bs, cp, check=False)
         assert rc == -1
+    finally:
+        for H in Hs:
+            H.close()
+
+
+def test_uneven_batch_with_a_zero_right_hand_side():
+    """One right-hand side of one lattice is zero: it is finished from the start
+    (solution zero, no iterations), and the FP32 middle level of the others is
+    unaffected."""
+    nr, m = 2, 0.05
+    Hs, bs, xs = [], [], []
+    try:
+        for i, dims in enumerate(SHAPES[:3]):
+            V = int(np.prod(dims))
+            U = inputs.gauge_field(dims, "smooth", seed=1150 + i)
+            b = inputs.gaussian_spinor(V // 2, seed=2150 + i, nrhs=nr)
+            if i == 1:
+                b[0] = 0
+            Hs.append(Handle(dims, U, mass=m))
+            bs.append(dev(b))
+            xs.append(torch.full_like(bs[-1], 3.0))
+        cp = lqcd.make_cg_params(lqcd.LQ_OP_WILSON_EO_NORMAL, lqcd.LQ_CG_MIXED, lqcd.LQ_F64, nrhs=nr, tol=1e-10,
+                                 inner=lqcd.LQ_F16)
+        rc, st = lqcd.lq_batch_cg_solve([H.h for H in Hs], xs, bs, cp)
+        assert rc == 0
+        assert np.all(host(xs[1])[0] == 0) and st[1 * nr + 0].iters == 0
+        for g, s_ in enumerate(st):
+            if g != nr:
+                assert s_.true_rel_residual < 1e-10
     finally:
         for H in Hs:
             H.close()
