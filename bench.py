@@ -195,7 +195,7 @@ def hop_source_hash():
     import hashlib
 
     h = hashlib.sha256()
-    for f in ("hop_async.cuh", "lqcd_internal.cuh", "hop.cuh"):
+    for f in ("hop_async.cuh", "lqcd_internal.cuh", "hop.cuh", "pdl.cuh"):
         with open(os.path.join(ROOT, "paper_2001_07557_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

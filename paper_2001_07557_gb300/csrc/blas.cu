@@ -5,6 +5,7 @@
 // last block to finish (atomic ticket) sums the partials in a fixed order and
 // finalises the CG scalars on the device -- no host round trip per iteration.
 #include "blas.h"
+#include "pdl.cuh"
 
 namespace lq {
 
@@ -77,6 +78,7 @@ using Compute = typename ComputeT<Ps...>::type;
 template <int PA, int PB>
 __global__ void __launch_bounds__(kThreads) dot_kernel(VecRef a, VecRef b, int Vh, int nblk, double* scratch,
                                                        unsigned* tickets, CgScalars* st, double* out, int fin) {
+    pdl_enter();
     const int rhs = blockIdx.y;
     if (st && st[rhs].done) return;
     using T = Compute<PA, PB>;
@@ -114,6 +116,7 @@ __global__ void __launch_bounds__(kThreads) dot_kernel(VecRef a, VecRef b, int V
 template <int PX, int PP, int PR, int PQ>
 __global__ void __launch_bounds__(kThreads) cg_update_kernel(VecRef x, VecRef p, VecRef r, VecRef q, int Vh, int nblk,
                                                              double* scratch, unsigned* tickets, CgScalars* st) {
+    pdl_enter();
     const int rhs = blockIdx.y;
     CgScalars& s = st[rhs];
     if (s.done) return;
@@ -162,6 +165,7 @@ __global__ void __launch_bounds__(kThreads) cg_update_kernel(VecRef x, VecRef p,
 // p = r + beta p
 template <int PP, int PR>
 __global__ void __launch_bounds__(kThreads) cg_xpay_kernel(VecRef p, VecRef r, int Vh, int nblk, const CgScalars* st) {
+    pdl_enter();
     const int rhs = blockIdx.y;
     if (st[rhs].done) return;
     using T = Compute<PP, PR>;
@@ -184,6 +188,7 @@ __global__ void __launch_bounds__(kThreads) cg_xpay_kernel(VecRef p, VecRef r, i
 // y = a x + b y with host scalars (a applies to every rhs)
 template <int PY, int PX>
 __global__ void __launch_bounds__(kThreads) axpby_kernel(VecRef y, VecRef x, double ca, double cb, int Vh, int nblk) {
+    pdl_enter();
     const int rhs = blockIdx.y;
     const long n = (long)Vh * nblk;
     for (long j = (long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
@@ -206,6 +211,7 @@ __global__ void __launch_bounds__(kThreads) axpby_kernel(VecRef y, VecRef x, dou
 
 // CG start: rr = |r|^2 per rhs (already in out), set the scalars
 __global__ void cg_init_kernel(CgScalars* st, const double* rr, const double* bb, double tol, int maxiter, int nrhs) {
+    pdl_enter();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nrhs) return;
     CgScalars& s = st[k];
@@ -307,6 +313,7 @@ __device__ __forceinline__ void load_site(const char* base, size_t rhs_stride, i
 template <int P, bool NATIVE>
 __global__ void __launch_bounds__(kThreads) cdot_kernel(const char* a, const char* b, size_t rhs_stride, long nsites,
                                                         int Vh, double* scratch, unsigned* tickets, double* result) {
+    pdl_enter();
     const int rhs = blockIdx.y;
     double re = 0, im = 0;
     for (long j = (long)blockIdx.x * blockDim.x + threadIdx.x; j < nsites; j += (long)gridDim.x * blockDim.x) {
@@ -328,6 +335,7 @@ __global__ void __launch_bounds__(kThreads) cdot_kernel(const char* a, const cha
 }
 
 __global__ void hop_norm_finalize_kernel(const double* partial, int nwarps, CgScalars* st) {
+    pdl_enter();
     const int g = blockIdx.x;
     CgScalars& s = st[g];
     if (s.done) return;
@@ -361,6 +369,7 @@ __device__ __forceinline__ const char* seg_blk(const char* base, int b, int Vh) 
 
 template <int PP>
 __global__ void __launch_bounds__(kThreads) bdot_alpha_kernel(const BSeg* __restrict__ segs) {
+    pdl_enter();
     const BSeg& sg = segs[blockIdx.y];
     if (sg.st->done) return;
     using T = Compute<PP>;
@@ -392,6 +401,7 @@ __global__ void __launch_bounds__(kThreads) bdot_alpha_kernel(const BSeg* __rest
 
 template <int PX, int PP>
 __global__ void __launch_bounds__(kThreads) bupdate_kernel(const BSeg* __restrict__ segs) {
+    pdl_enter();
     const BSeg& sg = segs[blockIdx.y];
     CgScalars& s = *sg.st;
     if (s.done) return;
@@ -439,6 +449,7 @@ __global__ void __launch_bounds__(kThreads) bupdate_kernel(const BSeg* __restric
 
 template <int PP, int PR>
 __global__ void __launch_bounds__(kThreads) bxpay_kernel(const BSeg* __restrict__ segs) {
+    pdl_enter();
     const BSeg& sg = segs[blockIdx.y];
     if (sg.st->done) return;
     using T = Compute<PP, PR>;
@@ -483,7 +494,7 @@ int grid_x(int Vh, int nblk) {
     }
 
 cudaError_t launch_hop_norm_finalize(const double* partial, int nwarps, int ngroups, CgScalars* st, cudaStream_t s) {
-    hop_norm_finalize_kernel<<<ngroups, kThreads, 0, s>>>(partial, nwarps, st);
+    launch_pdl(hop_norm_finalize_kernel, ngroups, kThreads, 0, s, partial, nwarps, st);
     return cudaGetLastError();
 }
 
@@ -503,11 +514,11 @@ cudaError_t launch_cdot(int fmt, const void* a, const void* b, size_t rhs_stride
     const char* pa = static_cast<const char*>(a);
     const char* pb = static_cast<const char*>(b);
     if (native) {
-        LQ_P_SWITCH(prec, P, (cdot_kernel<P, true><<<grid, kThreads, 0, s>>>(pa, pb, rhs_stride, nsites, Vh, scratch, tickets, result)))
+        LQ_P_SWITCH(prec, P, (launch_pdl(cdot_kernel<P, true>, grid, kThreads, 0, s, pa, pb, rhs_stride, nsites, Vh, scratch, tickets, result)))
     } else if (prec == LQ_F64) {
-        cdot_kernel<LQ_F64, false><<<grid, kThreads, 0, s>>>(pa, pb, rhs_stride, nsites, Vh, scratch, tickets, result);
+        launch_pdl(cdot_kernel<LQ_F64, false>, grid, kThreads, 0, s, pa, pb, rhs_stride, nsites, Vh, scratch, tickets, result);
     } else {
-        cdot_kernel<LQ_F32, false><<<grid, kThreads, 0, s>>>(pa, pb, rhs_stride, nsites, Vh, scratch, tickets, result);
+        launch_pdl(cdot_kernel<LQ_F32, false>, grid, kThreads, 0, s, pa, pb, rhs_stride, nsites, Vh, scratch, tickets, result);
     }
     return cudaGetLastError();
 }
@@ -516,7 +527,7 @@ cudaError_t launch_dot(const VecRef& a, const VecRef& b, int Vh, int nblk, int n
                        CgScalars* st, double* out, int fin, cudaStream_t s) {
     dim3 grid(grid_x(Vh, nblk), nrhs);
     LQ_P_SWITCH(a.prec, PA, LQ_P_SWITCH(b.prec, PB,
-        (dot_kernel<PA, PB><<<grid, kThreads, 0, s>>>(a, b, Vh, nblk, sc.partial, sc.tickets, st, out, fin))))
+        (launch_pdl(dot_kernel<PA, PB>, grid, kThreads, 0, s, a, b, Vh, nblk, sc.partial, sc.tickets, st, out, fin))))
     return cudaGetLastError();
 }
 
@@ -526,18 +537,18 @@ cudaError_t launch_cg_update(const VecRef& x, const VecRef& p, const VecRef& r, 
     // precision combinations used by the solvers: all equal; x, r in FP32 with p, q in FP16/BF16;
     // x in FP32 with r, p, q in FP16/BF16
     if (x.prec == LQ_F64 && p.prec == LQ_F64 && r.prec == LQ_F64 && q.prec == LQ_F64)
-        cg_update_kernel<LQ_F64, LQ_F64, LQ_F64, LQ_F64><<<grid, kThreads, 0, s>>>(x, p, r, q, Vh, nblk, sc.partial, sc.tickets, st);
+        launch_pdl(cg_update_kernel<LQ_F64, LQ_F64, LQ_F64, LQ_F64>, grid, kThreads, 0, s, x, p, r, q, Vh, nblk, sc.partial, sc.tickets, st);
     else if (x.prec == LQ_F32 && r.prec == LQ_F32 && p.prec == q.prec) {
         switch (p.prec) {
-        case LQ_F32: cg_update_kernel<LQ_F32, LQ_F32, LQ_F32, LQ_F32><<<grid, kThreads, 0, s>>>(x, p, r, q, Vh, nblk, sc.partial, sc.tickets, st); break;
-        case LQ_F16: cg_update_kernel<LQ_F32, LQ_F16, LQ_F32, LQ_F16><<<grid, kThreads, 0, s>>>(x, p, r, q, Vh, nblk, sc.partial, sc.tickets, st); break;
-        case LQ_BF16: cg_update_kernel<LQ_F32, LQ_BF16, LQ_F32, LQ_BF16><<<grid, kThreads, 0, s>>>(x, p, r, q, Vh, nblk, sc.partial, sc.tickets, st); break;
+        case LQ_F32: launch_pdl(cg_update_kernel<LQ_F32, LQ_F32, LQ_F32, LQ_F32>, grid, kThreads, 0, s, x, p, r, q, Vh, nblk, sc.partial, sc.tickets, st); break;
+        case LQ_F16: launch_pdl(cg_update_kernel<LQ_F32, LQ_F16, LQ_F32, LQ_F16>, grid, kThreads, 0, s, x, p, r, q, Vh, nblk, sc.partial, sc.tickets, st); break;
+        case LQ_BF16: launch_pdl(cg_update_kernel<LQ_F32, LQ_BF16, LQ_F32, LQ_BF16>, grid, kThreads, 0, s, x, p, r, q, Vh, nblk, sc.partial, sc.tickets, st); break;
         default: return cudaErrorInvalidValue;
         }
     } else if (x.prec == LQ_F32 && r.prec == p.prec && p.prec == q.prec && p.prec == LQ_F16) {
-        cg_update_kernel<LQ_F32, LQ_F16, LQ_F16, LQ_F16><<<grid, kThreads, 0, s>>>(x, p, r, q, Vh, nblk, sc.partial, sc.tickets, st);
+        launch_pdl(cg_update_kernel<LQ_F32, LQ_F16, LQ_F16, LQ_F16>, grid, kThreads, 0, s, x, p, r, q, Vh, nblk, sc.partial, sc.tickets, st);
     } else if (x.prec == LQ_F32 && r.prec == p.prec && p.prec == q.prec && p.prec == LQ_BF16) {
-        cg_update_kernel<LQ_F32, LQ_BF16, LQ_BF16, LQ_BF16><<<grid, kThreads, 0, s>>>(x, p, r, q, Vh, nblk, sc.partial, sc.tickets, st);
+        launch_pdl(cg_update_kernel<LQ_F32, LQ_BF16, LQ_BF16, LQ_BF16>, grid, kThreads, 0, s, x, p, r, q, Vh, nblk, sc.partial, sc.tickets, st);
     } else {
         return cudaErrorInvalidValue;
     }
@@ -548,7 +559,7 @@ cudaError_t launch_cg_xpay(const VecRef& p, const VecRef& r, int Vh, int nblk, i
                            cudaStream_t s) {
     dim3 grid(grid_x(Vh, nblk), nrhs);
     LQ_P_SWITCH(p.prec, PP, LQ_P_SWITCH(r.prec, PR,
-        (cg_xpay_kernel<PP, PR><<<grid, kThreads, 0, s>>>(p, r, Vh, nblk, st))))
+        (launch_pdl(cg_xpay_kernel<PP, PR>, grid, kThreads, 0, s, p, r, Vh, nblk, st))))
     return cudaGetLastError();
 }
 
@@ -556,13 +567,13 @@ cudaError_t launch_axpby(const VecRef& y, const VecRef& x, double a, double b, i
                          cudaStream_t s) {
     dim3 grid(grid_x(Vh, nblk), nrhs);
     LQ_P_SWITCH(y.prec, PY, LQ_P_SWITCH(x.prec, PX,
-        (axpby_kernel<PY, PX><<<grid, kThreads, 0, s>>>(y, x, a, b, Vh, nblk))))
+        (launch_pdl(axpby_kernel<PY, PX>, grid, kThreads, 0, s, y, x, a, b, Vh, nblk))))
     return cudaGetLastError();
 }
 
 cudaError_t launch_bdot_alpha(const BSeg* segs, int nseg, int gx, int pp, cudaStream_t s) {
     dim3 grid(gx, nseg);
-    LQ_P_SWITCH(pp, PP, (bdot_alpha_kernel<PP><<<grid, kThreads, 0, s>>>(segs)))
+    LQ_P_SWITCH(pp, PP, (launch_pdl(bdot_alpha_kernel<PP>, grid, kThreads, 0, s, segs)))
     return cudaGetLastError();
 }
 
@@ -571,12 +582,12 @@ cudaError_t launch_bupdate(const BSeg* segs, int nseg, int gx, int px, int pp, c
     if (px != LQ_F32 && px != LQ_F64) return cudaErrorInvalidValue;
     if (px == LQ_F64) {
         if (pp != LQ_F64) return cudaErrorInvalidValue;
-        bupdate_kernel<LQ_F64, LQ_F64><<<grid, kThreads, 0, s>>>(segs);
+        launch_pdl(bupdate_kernel<LQ_F64, LQ_F64>, grid, kThreads, 0, s, segs);
     } else {
         switch (pp) {
-        case LQ_F32: bupdate_kernel<LQ_F32, LQ_F32><<<grid, kThreads, 0, s>>>(segs); break;
-        case LQ_F16: bupdate_kernel<LQ_F32, LQ_F16><<<grid, kThreads, 0, s>>>(segs); break;
-        case LQ_BF16: bupdate_kernel<LQ_F32, LQ_BF16><<<grid, kThreads, 0, s>>>(segs); break;
+        case LQ_F32: launch_pdl(bupdate_kernel<LQ_F32, LQ_F32>, grid, kThreads, 0, s, segs); break;
+        case LQ_F16: launch_pdl(bupdate_kernel<LQ_F32, LQ_F16>, grid, kThreads, 0, s, segs); break;
+        case LQ_BF16: launch_pdl(bupdate_kernel<LQ_F32, LQ_BF16>, grid, kThreads, 0, s, segs); break;
         default: return cudaErrorInvalidValue;
         }
     }
@@ -585,13 +596,13 @@ cudaError_t launch_bupdate(const BSeg* segs, int nseg, int gx, int px, int pp, c
 
 cudaError_t launch_bxpay(const BSeg* segs, int nseg, int gx, int pp, int pr, cudaStream_t s) {
     dim3 grid(gx, nseg);
-    LQ_P_SWITCH(pp, PP, LQ_P_SWITCH(pr, PR, (bxpay_kernel<PP, PR><<<grid, kThreads, 0, s>>>(segs))))
+    LQ_P_SWITCH(pp, PP, LQ_P_SWITCH(pr, PR, (launch_pdl(bxpay_kernel<PP, PR>, grid, kThreads, 0, s, segs))))
     return cudaGetLastError();
 }
 
 cudaError_t launch_cg_init(CgScalars* st, const double* rr, const double* bb, double tol, int maxiter, int nrhs,
                            cudaStream_t s) {
-    cg_init_kernel<<<(nrhs + 63) / 64, 64, 0, s>>>(st, rr, bb, tol, maxiter, nrhs);
+    launch_pdl(cg_init_kernel, (nrhs + 63) / 64, 64, 0, s, st, rr, bb, tol, maxiter, nrhs);
     return cudaGetLastError();
 }
 

@@ -26,6 +26,7 @@
 
 #include "blas.h"
 #include "blockcg.h"
+#include "pdl.cuh"
 
 namespace lq {
 
@@ -129,6 +130,7 @@ template <bool SAME>
 __global__ void __launch_bounds__(kGramThreads) block_gram_kernel(const float4* __restrict__ A,
                                                                   const float4* __restrict__ B, size_t stride4,
                                                                   long M, int N, double2* partial) {
+    pdl_enter();
     extern __shared__ float4 sm[];
     const size_t buf = (size_t)(SAME ? 1 : 2) * N * kPad;  // float4 per tile buffer
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -194,6 +196,7 @@ __global__ void __launch_bounds__(kGramThreads) block_gram_kernel(const float4* 
 // G = sum over blocks of the partials: one warp per entry, lanes stride over
 // the blocks, then a fixed shuffle tree (the same order on every call).
 __global__ void gram_final_kernel(const double2* partial, int nblk, int N, double2* G) {
+    pdl_enter();
     const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (e >= N * N) return;
     double x = 0.0, y = 0.0;
@@ -214,6 +217,7 @@ __global__ void gram_final_kernel(const double2* partial, int nblk, int N, doubl
 __global__ void __launch_bounds__(32 * ((kMaxBlockRhs + 1) / 2)) block_update_kernel(
     float4* __restrict__ X, const float4* __restrict__ P, float4* __restrict__ R, const float4* __restrict__ Q,
     size_t stride4, long M, int N, const float2* __restrict__ a) {
+    pdl_enter();
     extern __shared__ float4 sm[];
     float4* sP = sm;
     float4* sQ = sm + (size_t)N * kTE;
@@ -276,6 +280,7 @@ __global__ void __launch_bounds__(32 * ((kMaxBlockRhs + 1) / 2)) block_update_ke
 // shared memory before any of it is overwritten, and tiles are disjoint.
 __global__ void __launch_bounds__(32 * ((kMaxBlockRhs + 1) / 2)) block_pupdate_kernel(
     float4* __restrict__ P, const float4* __restrict__ R, size_t stride4, long M, int N, const float2* __restrict__ b) {
+    pdl_enter();
     extern __shared__ float4 sm[];
     float4* sP = sm;
     float2* sb = reinterpret_cast<float2*>(sm + (size_t)N * kTE);
@@ -413,12 +418,12 @@ int block_cg(const BlockCgOps& ops, char* X, const char* Bv, char* R, char* P, c
         // tile buffers; the final reduction reuses them ([8 warps][N][16] double2 fit in kGramStages buffers)
         const int nb = A == Bm ? g_same : g_pair;
         if (A == Bm)
-            block_gram_kernel<true><<<nb, kGramThreads, kGramStages * gtile, s>>>(f4(A), f4(Bm), stride4, M, N,
+            launch_pdl(block_gram_kernel<true>, nb, kGramThreads, kGramStages * gtile, s, f4(A), f4(Bm), stride4, M, N,
                                                                                  partial);
         else
-            block_gram_kernel<false><<<nb, kGramThreads, 2 * kGramStages * gtile, s>>>(f4(A), f4(Bm), stride4, M, N,
+            launch_pdl(block_gram_kernel<false>, nb, kGramThreads, 2 * kGramStages * gtile, s, f4(A), f4(Bm), stride4, M, N,
                                                                                       partial);
-        gram_final_kernel<<<(N * N + 7) / 8, 256, 0, s>>>(partial, nb, N, Gd);
+        launch_pdl(gram_final_kernel, (N * N + 7) / 8, 256, 0, s, partial, nb, N, Gd);
         if (cudaMemcpyAsync(hostbuf, Gd, sizeof(double2) * N * N, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return LQ_ERR_CUDA;
@@ -454,7 +459,7 @@ int block_cg(const BlockCgOps& ops, char* X, const char* Bv, char* R, char* P, c
         if (!chol_solve(delta, rho, alpha, N)) break;  // block lost rank: hand back to the outer loop
         if ((rc = upload(alpha))) return rc;
         // X += P alpha ; R -= Q alpha
-        block_update_kernel<<<g_upd, nthr, 2 * tile + mat, s>>>(w4(X), f4(P), w4(R), f4(Q), stride4, M, N, Md);
+        launch_pdl(block_update_kernel, g_upd, nthr, 2 * tile + mat, s, w4(X), f4(P), w4(R), f4(Q), stride4, M, N, Md);
         if ((rc = gram(R, R, rhonew))) return rc;
         if (!chol_solve(rho, rhonew, beta, N)) {
             ++it;
@@ -462,7 +467,7 @@ int block_cg(const BlockCgOps& ops, char* X, const char* Bv, char* R, char* P, c
         }
         if ((rc = upload(beta))) return rc;
         // P = R + P beta
-        block_pupdate_kernel<<<g_pup, nthr, tile + mat, s>>>(w4(P), f4(R), stride4, M, N, Md);
+        launch_pdl(block_pupdate_kernel, g_pup, nthr, tile + mat, s, w4(P), f4(R), stride4, M, N, Md);
         rho = rhonew;
     }
     *iters = it;

@@ -22,6 +22,7 @@
 #include <type_traits>
 
 #include "lqcd_kernels.h"
+#include "pdl.cuh"
 
 namespace lq {
 
@@ -44,6 +45,7 @@ __device__ __forceinline__ double2 axpby4<double2, double>(double a, double2 x, 
 template <int P>
 __global__ void __launch_bounds__(256) m5inv_kernel(char* out, const char* in, int Vh, size_t out_stride,
                                                     size_t in_stride, int Ls, double inv_a_d, double c_d, int dag) {
+    pdl_enter();
     using V = typename std::conditional<P == LQ_F64, double2, float4>::type;
     using T = typename std::conditional<P == LQ_F64, double, float>::type;
     constexpr int NPL = P == LQ_F64 ? 12 : 6;
@@ -81,6 +83,7 @@ template <int P>
 __global__ void __launch_bounds__(256) m5_lincomb_kernel(char* out, const char* u, const char* v, int Vh, int nblk,
                                                          size_t slice_stride, int Ls, double a_d, double b_d,
                                                          double c_d, double d_d, double mf_d, int dag) {
+    pdl_enter();
     using V = typename std::conditional<P == LQ_F64, double2, float4>::type;
     using T = typename std::conditional<P == LQ_F64, double, float>::type;
     constexpr int NPL = P == LQ_F64 ? 12 : 6;
@@ -115,9 +118,9 @@ cudaError_t launch_m5_lincomb(int prec, void* out, const void* u, const void* v,
     auto pu = static_cast<const char*>(u);
     auto pv = static_cast<const char*>(v);
     if (prec == LQ_F64)
-        m5_lincomb_kernel<LQ_F64><<<grid, 256, 0, st>>>(o, pu, pv, Vh, nblk, slice_stride, Ls, a, b, c, d, mf, dag);
+        launch_pdl(m5_lincomb_kernel<LQ_F64>, grid, 256, 0, st, o, pu, pv, Vh, nblk, slice_stride, Ls, a, b, c, d, mf, dag);
     else if (prec == LQ_F32)
-        m5_lincomb_kernel<LQ_F32><<<grid, 256, 0, st>>>(o, pu, pv, Vh, nblk, slice_stride, Ls, a, b, c, d, mf, dag);
+        launch_pdl(m5_lincomb_kernel<LQ_F32>, grid, 256, 0, st, o, pu, pv, Vh, nblk, slice_stride, Ls, a, b, c, d, mf, dag);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
@@ -133,10 +136,10 @@ cudaError_t launch_m5inv(int prec, void* out, const void* in, int Vh, size_t out
     const long n = (long)Vh * npl;
     const int grid = (int)((n + 255) / 256);
     if (prec == LQ_F64)
-        m5inv_kernel<LQ_F64><<<grid, 256, 0, st>>>(static_cast<char*>(out), static_cast<const char*>(in), Vh,
+        launch_pdl(m5inv_kernel<LQ_F64>, grid, 256, 0, st, static_cast<char*>(out), static_cast<const char*>(in), Vh,
                                                    out_stride, in_stride, Ls, 1.0 / a, c, dag);
     else if (prec == LQ_F32)
-        m5inv_kernel<LQ_F32><<<grid, 256, 0, st>>>(static_cast<char*>(out), static_cast<const char*>(in), Vh,
+        launch_pdl(m5inv_kernel<LQ_F32>, grid, 256, 0, st, static_cast<char*>(out), static_cast<const char*>(in), Vh,
                                                    out_stride, in_stride, Ls, 1.0 / a, c, dag);
     else
         return cudaErrorInvalidValue;

@@ -17,6 +17,7 @@
 #include <cstdint>
 
 #include "handle.h"
+#include "pdl.cuh"
 
 namespace lq {
 
@@ -28,6 +29,7 @@ namespace {
 template <int P>
 __global__ void face_copy_kernel(char* dst, const char* src, int vh_d, int vh_s, int e0_d, int e0_s, int n, int flip,
                                  double scale) {
+    pdl_enter();
     constexpr bool NORM = P == LQ_F16 || P == LQ_BF16;
     constexpr int NPL = P == LQ_F64 ? 12 : P == LQ_F32 ? 6 : 3;  // 16-byte planes per site
     const long units = 2L * NPL * n, total = units + (NORM ? 2L * n : 0);
@@ -109,10 +111,10 @@ int lq_face_copy(lq_handle* hd, void* dst, int t_dst, lq_handle* hs, const void*
     const char* s = static_cast<const char*>(src);
     const int vd = hd->g.Vh, vs = hs->g.Vh, e0d = t_dst * vh3, e0s = t_src * vh3, flip = (t_dst - t_src) & 1;
     switch (prec) {
-    case LQ_F64: face_copy_kernel<LQ_F64><<<grid, 256, 0, st>>>(d, s, vd, vs, e0d, e0s, vh3, flip, scale); break;
-    case LQ_F32: face_copy_kernel<LQ_F32><<<grid, 256, 0, st>>>(d, s, vd, vs, e0d, e0s, vh3, flip, scale); break;
-    case LQ_F16: face_copy_kernel<LQ_F16><<<grid, 256, 0, st>>>(d, s, vd, vs, e0d, e0s, vh3, flip, scale); break;
-    default: face_copy_kernel<LQ_BF16><<<grid, 256, 0, st>>>(d, s, vd, vs, e0d, e0s, vh3, flip, scale); break;
+    case LQ_F64: launch_pdl(face_copy_kernel<LQ_F64>, grid, 256, 0, st, d, s, vd, vs, e0d, e0s, vh3, flip, scale); break;
+    case LQ_F32: launch_pdl(face_copy_kernel<LQ_F32>, grid, 256, 0, st, d, s, vd, vs, e0d, e0s, vh3, flip, scale); break;
+    case LQ_F16: launch_pdl(face_copy_kernel<LQ_F16>, grid, 256, 0, st, d, s, vd, vs, e0d, e0s, vh3, flip, scale); break;
+    default: launch_pdl(face_copy_kernel<LQ_BF16>, grid, 256, 0, st, d, s, vd, vs, e0d, e0s, vh3, flip, scale); break;
     }
     return status_of(cudaGetLastError());
 }

@@ -13,11 +13,13 @@
 
 #include "lqcd_internal.cuh"
 #include "lqcd_kernels.h"
+#include "pdl.cuh"
 
 namespace lq {
 
 template <int P, bool R12, bool DAG, int EPI, bool RED>
 __global__ void __launch_bounds__(128) wilson_hop_kernel(const HopArgs a) {
+    pdl_enter();
     using T = typename Prec<P>::real;
     // grid.x = site block x rhs (rhs fastest: the right-hand sides, or 5th-dimension
     // slices, of one site tile run together and share each link through L2/L1);
@@ -187,7 +189,7 @@ cudaError_t launch_hop_prec(const HopArgs& a, bool r12, bool dag, int epi, int b
     dim3 blk(block);
     const bool red = a.red_partial != nullptr;
     if (red && epi == EPI_HOP) return cudaErrorInvalidValue;
-#define LQ_LAUNCH(R, D, E, RD) wilson_hop_kernel<P, R, D, E, RD><<<grid, blk, 0, st>>>(a)
+#define LQ_LAUNCH(R, D, E, RD) launch_pdl(wilson_hop_kernel<P, R, D, E, RD>, grid, blk, 0, st, a)
 #define LQ_EPI(R, D)                                                                           \
     switch (epi) {                                                                             \
     case EPI_HOP: LQ_LAUNCH(R, D, EPI_HOP, false); break;                                      \

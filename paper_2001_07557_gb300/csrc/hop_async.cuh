@@ -20,6 +20,7 @@
 
 #include "lqcd_internal.cuh"
 #include "lqcd_kernels.h"
+#include "pdl.cuh"
 
 namespace lq {
 
@@ -407,6 +408,7 @@ __global__ void __launch_bounds__(NT) wilson_hop_async_kernel(const HopArgs a) {
     }
     const int i = active ? i0 : end - 1;
     const int p = a.parity0 + blockIdx.y;
+    pdl_enter();  // every global access of the block comes after this (programmatic dependent launch)
     if (a.skip && a.skip[(EPI == EPI_DWF ? 0 : rhs) * a.skip_stride]) return;  // uniform per block
     cplx<T> o[12];
     hop_async_site<P, R12, DAG, EPI, NT, S>(a, i, rhs, p, smem, t, o);
@@ -441,9 +443,7 @@ cudaError_t launch_async_one(const HopArgs& a, cudaStream_t st) {
         configured = true;
     }
     const int nsite = a.nsite ? a.nsite : a.g.Vh;
-    dim3 grid(((nsite + NT - 1) / NT) * a.nrhs, a.nparity);
-    kern<<<grid, NT, smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(kern, dim3(((nsite + NT - 1) / NT) * a.nrhs, a.nparity), dim3(NT), smem, st, a);
 }
 
 // ---------------------------------------------------------------------------
