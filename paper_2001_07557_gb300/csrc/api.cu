@@ -46,6 +46,36 @@ int ensure_ws(lq_handle* h, int k, size_t bytes, void** out) {
     return LQ_OK;
 }
 
+int cached_graph_exec(lq_handle* h, const int key[4], cudaGraph_t graph, cudaGraphExec_t* exec) {
+    constexpr int kSlots = (int)(sizeof(h->graphs) / sizeof(h->graphs[0]));
+    lq_handle::GraphSlot* slot = nullptr;
+    for (auto& g : h->graphs)
+        if (g.exec && std::memcmp(g.key, key, sizeof(g.key)) == 0) slot = &g;
+    if (slot) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(slot->exec, graph, &info) == cudaSuccess) {
+            *exec = slot->exec;
+            return LQ_OK;
+        }
+        cudaGetLastError();  // a different topology: instantiate anew in this slot
+        cudaGraphExecDestroy(slot->exec);
+        slot->exec = nullptr;
+    } else {
+        slot = &h->graphs[h->graph_next];
+        h->graph_next = (h->graph_next + 1) % kSlots;
+        if (slot->exec) cudaGraphExecDestroy(slot->exec);
+        slot->exec = nullptr;
+    }
+    if (cudaGraphInstantiate(&slot->exec, graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        slot->exec = nullptr;
+        return LQ_ERR_CUDA;
+    }
+    std::memcpy(slot->key, key, sizeof(slot->key));
+    *exec = slot->exec;
+    return LQ_OK;
+}
+
 int get_links(lq_handle* h, int prec, const char** links, size_t* link_block, cudaStream_t st) {
     const bool r12 = link_r12(h, prec);
     void*& L = h->links[prec][r12];
@@ -457,6 +487,8 @@ int lq_destroy(lq_handle* h) {
             if (q) cudaFree(q);
     for (auto& b : h->ws)
         if (b.ptr) cudaFree(b.ptr);
+    for (auto& g : h->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
     if (h->solver_stream) cudaStreamDestroy(h->solver_stream);
     if (h->pinned) cudaFreeHost(h->pinned);
     delete h;

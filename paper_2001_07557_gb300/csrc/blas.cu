@@ -5,6 +5,9 @@
 // last block to finish (atomic ticket) sums the partials in a fixed order and
 // finalises the CG scalars on the device -- no host round trip per iteration.
 #include "blas.h"
+
+#include <algorithm>
+
 #include "pdl.cuh"
 
 namespace lq {
@@ -185,27 +188,33 @@ __global__ void __launch_bounds__(kThreads) cg_xpay_kernel(VecRef p, VecRef r, i
     }
 }
 
-// y = a x + b y with host scalars (a applies to every rhs)
+// y = a x + b y with host scalars (a applies to every rhs).  The arithmetic is
+// that of the output: FP64 for an FP64 y, else FP32 (an FP64 x is rounded to
+// FP32 on load; the stored result carries FP32 precision either way, and FP64
+// arithmetic runs at a small fraction of the FP32 rate on this GPU).
 template <int PY, int PX>
-__global__ void __launch_bounds__(kThreads) axpby_kernel(VecRef y, VecRef x, double ca, double cb, int Vh, int nblk) {
+__global__ void __launch_bounds__(kThreads) axpby_kernel(VecRef y, VecRef x, double ca_d, double cb_d, int Vh,
+                                                         int nblk) {
     pdl_enter();
+    using T = typename std::conditional<PY == LQ_F64, double, float>::type;
+    const T ca = (T)ca_d, cb = (T)cb_d;
     const int rhs = blockIdx.y;
     const long n = (long)Vh * nblk;
     for (long j = (long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
         const int bk = (int)(j / Vh), i = (int)(j - (long)bk * Vh);
-        cplx<double> ys[12], xs[12];
-        load_spinor<PX, double>(blk_ptr<PX, double>(x, rhs, bk, Vh), Vh, i, xs);
-        if (cb != 0.0) load_spinor<PY, double>(blk_ptr<PY, double>(y, rhs, bk, Vh), Vh, i, ys);
+        cplx<T> ys[12], xs[12];
+        load_spinor<PX, T>(blk_ptr<PX, T>(x, rhs, bk, Vh), Vh, i, xs);
+        if (cb_d != 0.0) load_spinor<PY, T>(blk_ptr<PY, T>(y, rhs, bk, Vh), Vh, i, ys);
         else {
 #pragma unroll
-            for (int k = 0; k < 12; ++k) ys[k] = {0.0, 0.0};
+            for (int k = 0; k < 12; ++k) ys[k] = {(T)0, (T)0};
         }
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             ys[k].re = ca * xs[k].re + cb * ys[k].re;
             ys[k].im = ca * xs[k].im + cb * ys[k].im;
         }
-        store_spinor<PY, double>(const_cast<char*>(blk_ptr<PY, double>(y, rhs, bk, Vh)), Vh, i, ys);
+        store_spinor<PY, T>(const_cast<char*>(blk_ptr<PY, T>(y, rhs, bk, Vh)), Vh, i, ys);
     }
 }
 
@@ -334,21 +343,37 @@ __global__ void __launch_bounds__(kThreads) cdot_kernel(const char* a, const cha
     }
 }
 
-__global__ void hop_norm_finalize_kernel(const double* partial, int nwarps, CgScalars* st) {
+// Sum of a group's warp partials (grid.y = group): each block adds a strided
+// share with kFinPer independent loads in flight per thread (the partials were
+// just written to L2 by the hop), then the last block to finish sums the block
+// partials in a fixed order and sets the CG scalars.
+constexpr int kFinThreads = 256, kFinPer = 8;
+
+__global__ void __launch_bounds__(kFinThreads) hop_norm_finalize_kernel(const double* partial, int nwarps,
+                                                                          CgScalars* st, double* scratch,
+                                                                          unsigned* tickets) {
     pdl_enter();
-    const int g = blockIdx.x;
+    const int g = blockIdx.y;
     CgScalars& s = st[g];
     if (s.done) return;
+    const double* p = partial + (size_t)g * nwarps;
+    const int stride = gridDim.x * kFinThreads;
+    double acc[kFinPer] = {};
+    int w = blockIdx.x * kFinThreads + threadIdx.x;
+    for (; w + (kFinPer - 1) * stride < nwarps; w += kFinPer * stride) {
+        double v[kFinPer];
+#pragma unroll
+        for (int u = 0; u < kFinPer; ++u) v[u] = __ldcg(p + w + u * stride);
+#pragma unroll
+        for (int u = 0; u < kFinPer; ++u) acc[u] += v[u];
+    }
+    for (; w < nwarps; w += stride) acc[0] += __ldcg(p + w);
     double t = 0;
-    for (int w = threadIdx.x; w < nwarps; w += blockDim.x) t += partial[(size_t)g * nwarps + w];
-    __shared__ double ws[kThreads / 32];
-    t = warp_sum(t);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) ws[wid] = t;
-    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kFinPer; ++u) t += acc[u];
+    double tot;
+    if (!reduce_last(t, scratch + (size_t)g * gridDim.x, tickets + g, gridDim.x, tot)) return;
     if (threadIdx.x == 0) {
-        double tot = 0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += ws[k];
         s.pAp = tot;
         if (!(tot > 0.0) || !isfinite(tot)) {
             s.done = 1;
@@ -493,8 +518,14 @@ int grid_x(int Vh, int nblk) {
     default: { constexpr int NAME = LQ_BF16; BODY; } break;       \
     }
 
-cudaError_t launch_hop_norm_finalize(const double* partial, int nwarps, int ngroups, CgScalars* st, cudaStream_t s) {
-    launch_pdl(hop_norm_finalize_kernel, ngroups, kThreads, 0, s, partial, nwarps, st);
+cudaError_t launch_hop_norm_finalize(const double* partial, int nwarps, int ngroups, CgScalars* st,
+                                     const Scratch& sc, int Vh, int nblk, cudaStream_t s) {
+    // blocks per group: one per kFinThreads * kFinPer partials, within the scratch
+    // entries per right-hand side that the vector kernels use (grid_x)
+    const int want = (nwarps + kFinThreads * kFinPer - 1) / (kFinThreads * kFinPer);
+    const int nb = std::max(1, std::min(want, grid_x(Vh, nblk)));
+    launch_pdl(hop_norm_finalize_kernel, dim3(nb, ngroups), kFinThreads, 0, s, partial, nwarps, st, sc.partial,
+               sc.tickets);
     return cudaGetLastError();
 }
 

@@ -55,6 +55,11 @@ cudaError_t launch_cg_xpay(const VecRef& p, const VecRef& r, int Vh, int nblk, i
                            cudaStream_t s);
 cudaError_t launch_axpby(const VecRef& y, const VecRef& x, double a, double b, int Vh, int nblk, int nrhs,
                          cudaStream_t s);
+// Sum the warp partials of the last fused-norm hop (ngroups groups of nwarps
+// each) in a fixed order and set pAp and alpha of each group.  The second level
+// of the sum uses sc (scratch entries per group as for vectors of Vh x nblk sites).
+cudaError_t launch_hop_norm_finalize(const double* partial, int nwarps, int ngroups, CgScalars* st,
+                                     const Scratch& sc, int Vh, int nblk, cudaStream_t s);
 // Complex dot <a, b> per rhs of nsites sites each (site-major or native fmt);
 // scratch: 2 * kMaxGrid * nrhs doubles, tickets: nrhs zeros; result: 2 * nrhs doubles (device).
 constexpr int kMaxGrid = 152 * 8;

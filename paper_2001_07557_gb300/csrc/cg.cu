@@ -215,7 +215,7 @@ int run_cg(lq_handle* h, const OpGeom& og, const Ctl& c, int pp, const VecRef& e
         rc = apply_normal(h, og, pp, v.q.ptr, v.p.ptr, v.t.ptr, v.tmp.ptr, s, &c);
         if (rc) break;
         if (launch_hop_norm_finalize(c.hop_partial, hop_warps(h, og), og.op == LQ_OP_DWF_NORMAL ? 1 : og.nrhs, c.st,
-                                     s) != cudaSuccess) {
+                                     c.sc, Vh, og.nblk, s) != cudaSuccess) {
             rc = LQ_ERR_CUDA;
             break;
         }
@@ -226,7 +226,8 @@ int run_cg(lq_handle* h, const OpGeom& og, const Ctl& c, int pp, const VecRef& e
     cudaError_t ce = cudaStreamEndCapture(s, &graph);
     h->skip = nullptr;
     if (rc == LQ_OK && ce != cudaSuccess) rc = LQ_ERR_CUDA;
-    if (rc == LQ_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) rc = LQ_ERR_CUDA;
+    const int key[4] = {og.op, pp, pr, og.nrhs};
+    if (rc == LQ_OK) rc = cached_graph_exec(h, key, graph, &exec);
     const int max_launches = maxiter / kItersPerGraph + 2;
     for (int it = 0; rc == LQ_OK && it < max_launches; ++it) {
         if (cudaGraphLaunch(exec, s) != cudaSuccess ||
@@ -239,8 +240,7 @@ int run_cg(lq_handle* h, const OpGeom& og, const Ctl& c, int pp, const VecRef& e
         for (int k = 0; k < og.nrhs; ++k) all = all && c.host[k].done;
         if (all) break;
     }
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
+    if (graph) cudaGraphDestroy(graph);  // the executable graph stays with the handle
     cudaGetLastError();
     return rc;
 }

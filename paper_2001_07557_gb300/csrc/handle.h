@@ -31,6 +31,14 @@ struct lq_handle {
     cudaStream_t solver_stream;  // private non-blocking stream the solvers capture into graphs
     void* pinned;                // pinned host buffer the solvers poll their scalars into
     size_t pinned_bytes;
+    // executable CG iteration graphs kept across solves, one per solver shape
+    // (key: operator, search-direction and residual precisions, right-hand
+    // sides); each solve captures afresh and updates the kept graph's parameters
+    struct GraphSlot {
+        int key[4];
+        cudaGraphExec_t exec;
+    } graphs[6];
+    int graph_next;  // slot the next new shape replaces
 };
 
 namespace lq {
@@ -41,6 +49,12 @@ namespace lq {
 enum { WS_IN = 0, WS_OUT = 1, WS_TMP = 2, WS_CG0 = 3, WS_DOT = 18, WS_CTL = 19, WS_MOB = 24 /* 24, 25 */ };
 
 inline int status_of(cudaError_t e) { return e == cudaSuccess ? LQ_OK : LQ_ERR_CUDA; }
+
+// An executable graph for `graph`, the capture of a solver shape `key`: the
+// handle's kept graph of that shape with its parameters updated from `graph`
+// (cudaGraphExecUpdate), or a new instantiation stored in a slot.  The handle
+// owns the result; the caller still destroys `graph`.
+int cached_graph_exec(lq_handle* h, const int key[4], cudaGraph_t graph, cudaGraphExec_t* exec);
 
 // Make sure workspace k holds at least `bytes`; returns LQ_OK / LQ_ERR_NOMEM.
 int ensure_ws(lq_handle* h, int k, size_t bytes, void** out);

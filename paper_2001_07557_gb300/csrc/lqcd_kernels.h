@@ -50,9 +50,6 @@ inline size_t hop_red_warps(int Vh, int nparity, int slices) {
     return (size_t)((Vh + kHopThreads - 1) / kHopThreads) * (kHopThreads / 32) * nparity * slices;
 }
 
-// Sum the warp partials of the last fused-norm hop (ngroups groups of
-// nwarps each) in a fixed order and set pAp and alpha of each group.
-cudaError_t launch_hop_norm_finalize(const double* partial, int nwarps, int ngroups, CgScalars* st, cudaStream_t s);
 
 cudaError_t launch_hop(int prec, const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st);
 
