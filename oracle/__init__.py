@@ -89,6 +89,15 @@ def _configure(L):
     L.orc_dwf_eo_prepare.restype = i
     L.orc_dwf_eo_reconstruct.argtypes = [p, p, p, p, i4, i4, i, d, d]
     L.orc_dwf_eo_reconstruct.restype = i
+    L.orc_dwf_mobius_m5.argtypes = [p, p, ctypes.c_long, i, d, d, d, d, i]
+    L.orc_dwf_mobius_m5_inv.argtypes = [p, p, ctypes.c_long, i, d, d, d, d, i]
+    L.orc_dwf_mobius_m5_inv.restype = i
+    L.orc_dwf_mobius_schur.argtypes = [p, p, p, i4, i4, i, d, d, d, d, i]
+    L.orc_dwf_mobius_schur.restype = i
+    L.orc_dwf_mobius_eo_prepare.argtypes = [p, p, p, i4, i4, i, d, d, d, d]
+    L.orc_dwf_mobius_eo_prepare.restype = i
+    L.orc_dwf_mobius_eo_reconstruct.argtypes = [p, p, p, p, i4, i4, i, d, d, d, d]
+    L.orc_dwf_mobius_eo_reconstruct.restype = i
     return L
 
 
@@ -251,6 +260,57 @@ def dwf_eo_reconstruct(x5e, eta5, U, dims, Ls, M5, mf, bc=(1, 1, 1, -1)):
     out = np.empty_like(eta5)
     rc = lib().orc_dwf_eo_reconstruct(_ptr(out), _ptr(x5e), _ptr(eta5), _ptr(U), _i4(dims), _i4(bc), int(Ls),
                                       M5, mf)
+    assert rc == OK, rc
+    return out
+
+
+def dwf_mobius_m5(psi5, Ls, M5, mf, b5, c5, dagger=False):
+    """The 4-d-site-local part of the Moebius operator, (4 - M5)(b5 + c5 S) + 1 - S
+    (dagger: S -> S^dag), on a 5-d field [Ls][n][4][3] of any site subset."""
+    psi5 = _c(psi5)
+    out = np.empty_like(psi5)
+    lib().orc_dwf_mobius_m5(_ptr(out), _ptr(psi5), int(psi5.size // (12 * Ls)), int(Ls), M5, mf, b5, c5,
+                            int(dagger))
+    return out
+
+
+def dwf_mobius_m5_inv(psi5, Ls, M5, mf, b5, c5, dagger=False):
+    """The inverse of dwf_mobius_m5 (dagger: of its adjoint) by dense Gaussian elimination."""
+    psi5 = _c(psi5)
+    out = np.empty_like(psi5)
+    rc = lib().orc_dwf_mobius_m5_inv(_ptr(out), _ptr(psi5), int(psi5.size // (12 * Ls)), int(Ls), M5, mf, b5, c5,
+                                     int(dagger))
+    assert rc == OK, rc
+    return out
+
+
+def dwf_mobius_schur(psi5e, U, dims, Ls, M5, mf, b5, c5, bc=(1, 1, 1, -1), dagger=False):
+    """Moebius Mhat = M5_M - M_eo M5_M^{-1} M_oe, M_eo = -1/2 H_eo (b5 + c5 S) (dagger: its
+    adjoint) on an even 5-d half field [Ls][V/2][4][3]."""
+    psi5e, U = _c(psi5e), _c(U)
+    out = np.empty_like(psi5e)
+    rc = lib().orc_dwf_mobius_schur(_ptr(out), _ptr(psi5e), _ptr(U), _i4(dims), _i4(bc), int(Ls), M5, mf, b5, c5,
+                                    int(dagger))
+    assert rc == OK, rc
+    return out
+
+
+def dwf_mobius_eo_prepare(eta5, U, dims, Ls, M5, mf, b5, c5, bc=(1, 1, 1, -1)):
+    """Moebius eta_hat_e = eta_e - M_eo M5_M^{-1} eta_o for a full 5-d source [Ls][V][4][3]."""
+    eta5, U = _c(eta5), _c(U)
+    out = np.empty((Ls, _vol(dims) // 2, 4, 3), dtype=np.complex128)
+    rc = lib().orc_dwf_mobius_eo_prepare(_ptr(out), _ptr(eta5), _ptr(U), _i4(dims), _i4(bc), int(Ls), M5, mf, b5,
+                                         c5)
+    assert rc == OK, rc
+    return out
+
+
+def dwf_mobius_eo_reconstruct(x5e, eta5, U, dims, Ls, M5, mf, b5, c5, bc=(1, 1, 1, -1)):
+    """The full Moebius 5-d solution: psi_e = x_e, psi_o = M5_M^{-1} (eta_o - M_oe x_e)."""
+    x5e, eta5, U = _c(x5e), _c(eta5), _c(U)
+    out = np.empty_like(eta5)
+    rc = lib().orc_dwf_mobius_eo_reconstruct(_ptr(out), _ptr(x5e), _ptr(eta5), _ptr(U), _i4(dims), _i4(bc),
+                                             int(Ls), M5, mf, b5, c5)
     assert rc == OK, rc
     return out
 

@@ -47,6 +47,12 @@
  *    the source eta_hat_e = eta_e - M_eo M5^{-1} eta_o and the odd half of the
  *    solution psi_o = M5^{-1} (eta_o - M_oe psi_e).  M5^{-1} is applied by
  *    Gaussian elimination of M5's dense (4 Ls) x (4 Ls) spin-slice matrix.
+ *  - The same Schur decomposition of the Moebius operator.  With B = b5 + c5 S,
+ *    D_M = D_W(-M5) B + 1 - S splits into the site-local part
+ *      M5_M = (4 - M5) B + 1 - S
+ *    and the parity-changing parts M_eo = -1/2 H_eo B, M_oe = -1/2 H_oe B
+ *    (B acts first, before the hop); Mhat, the prepared source and the
+ *    reconstruction take the formulas above with M5 -> M5_M.
  *  - The lattice-wide SU(3) product of the paper's matrix-matrix benchmark
  *    (Sec. 3.3, Fig. 4a-c): C(x) = A(x) B(x) for 3x3 complex matrices stored
  *    [x][row][col] as {re, im} pairs, each entry summed over k = 0, 1, 2 in
@@ -409,11 +415,15 @@ void orc_dwf_m5(cplx *out, const cplx *in, long nsites, int Ls, double M5, doubl
     }
 }
 
-/* out = M5^{-1} in (dagger: (M5^dag)^{-1}).  M5 is the same (4 Ls) x (4 Ls)
-   matrix on the (slice, spin) index of every site and colour: it is built from
-   orc_dwf_m5 applied to unit vectors, factorised once by Gaussian elimination
-   with partial pivoting, and solved for every (site, colour). */
-int orc_dwf_m5_inv(cplx *out, const cplx *in, long nsites, int Ls, double M5, double mf, int dagger)
+/* A site-local 5-d operator: out = A in on [Ls][nsites][4][3], parameters prm. */
+typedef void (*site_op_fn)(cplx *out, const cplx *in, long nsites, int Ls, const double *prm, int dagger);
+
+/* out = A^{-1} in for a site-local operator A that is the same (4 Ls) x (4 Ls)
+   matrix on the (slice, spin) index of every site and colour: the matrix is
+   built from A applied to unit vectors, factorised once by Gaussian
+   elimination with partial pivoting, and solved for every (site, colour). */
+static int site_op_inv(cplx *out, const cplx *in, long nsites, int Ls, site_op_fn op, const double *prm,
+                       int dagger)
 {
     if (Ls < 1 || Ls > 64) return ORC_ERR_ARG;
     const int n = 4 * Ls;
@@ -422,11 +432,11 @@ int orc_dwf_m5_inv(cplx *out, const cplx *in, long nsites, int Ls, double M5, do
     cplx *col = malloc((size_t)Ls * SITE_DOF * sizeof(cplx));
     int *piv = malloc((size_t)n * sizeof(int));
     if (!A || !e || !col || !piv) { free(A); free(e); free(col); free(piv); return ORC_ERR_NOMEM; }
-    /* column j = (s', b) of A: M5 applied to the unit vector at slice s', spin b, colour 0 (one site) */
+    /* column j = (s', b) of A: the operator applied to the unit vector at slice s', spin b, colour 0 (one site) */
     for (int j = 0; j < n; ++j) {
         memset(e, 0, (size_t)Ls * SITE_DOF * sizeof(cplx));
         e[(j / 4) * SITE_DOF + (j % 4) * 3] = 1.0;
-        orc_dwf_m5(col, e, 1, Ls, M5, mf, dagger);
+        op(col, e, 1, Ls, prm, dagger);
         for (int i = 0; i < n; ++i) A[i * n + j] = col[(i / 4) * SITE_DOF + (i % 4) * 3];
     }
     /* LU with partial pivoting, in place */
@@ -466,6 +476,18 @@ int orc_dwf_m5_inv(cplx *out, const cplx *in, long nsites, int Ls, double M5, do
     free(col);
     free(piv);
     return ORC_OK;
+}
+
+static void shamir_m5_op(cplx *out, const cplx *in, long nsites, int Ls, const double *prm, int dagger)
+{
+    orc_dwf_m5(out, in, nsites, Ls, prm[0], prm[1], dagger);
+}
+
+/* out = M5^{-1} in (dagger: (M5^dag)^{-1}). */
+int orc_dwf_m5_inv(cplx *out, const cplx *in, long nsites, int Ls, double M5, double mf, int dagger)
+{
+    const double prm[2] = {M5, mf};
+    return site_op_inv(out, in, nsites, Ls, shamir_m5_op, prm, dagger);
 }
 
 /* -1/2 H between parities on every slice of a 5-d half field [Ls][V/2][4][3]. */
@@ -553,6 +575,127 @@ int orc_dwf_eo_reconstruct(cplx *psi, const cplx *xe, const cplx *eta, const cpl
         split_parity(t, psi, d, Ls, 1, 1);
     }
     free(t);
+    free(eo);
+    return rc;
+}
+
+/* -------------------------------------- Moebius domain wall, even-odd (4-d) */
+
+/* With D_W = (4 - M5) - H/2 (H the 4-d hop between parities) and B = b5 + c5 S,
+   the Moebius operator D_M = D_W B + 1 - S splits by 4-d parity into
+     the site-local part     M5_M = (4 - M5) B + 1 - S,
+     the parity-changing part M_eo = -H_eo B / 2,  M_oe = -H_oe B / 2,
+   and Mhat = M5_M - M_eo M5_M^{-1} M_oe on the even sites.  The adjoints take
+   S -> S^dag and H -> H^dag (H_eo^dag = (H^dag)_oe), with B^dag = b5 + c5 S^dag
+   moved to the left of the hop. */
+
+/* out = B in (dagger: B^dag); out and in distinct */
+static void mobius_b(cplx *out, const cplx *in, long nsites, int Ls, double mf, double b5, double c5, int dagger)
+{
+    long n5 = (long)Ls * nsites * SITE_DOF;
+    dwf_shift(out, in, nsites, Ls, mf, dagger);
+    for (long i = 0; i < n5; ++i) out[i] = b5 * in[i] + c5 * out[i];
+}
+
+/* out = M5_M in (dagger: M5_M^dag) on 5-d fields [Ls][nsites][4][3] of any site subset. */
+void orc_dwf_mobius_m5(cplx *out, const cplx *in, long nsites, int Ls, double M5, double mf, double b5,
+                       double c5, int dagger)
+{
+    long n5 = (long)Ls * nsites * SITE_DOF;
+    dwf_shift(out, in, nsites, Ls, mf, dagger); /* out = S in */
+    for (long i = 0; i < n5; ++i) out[i] = (4.0 - M5) * (b5 * in[i] + c5 * out[i]) + in[i] - out[i];
+}
+
+static void mobius_m5_op(cplx *out, const cplx *in, long nsites, int Ls, const double *prm, int dagger)
+{
+    orc_dwf_mobius_m5(out, in, nsites, Ls, prm[0], prm[1], prm[2], prm[3], dagger);
+}
+
+/* out = M5_M^{-1} in (dagger: (M5_M^dag)^{-1}). */
+int orc_dwf_mobius_m5_inv(cplx *out, const cplx *in, long nsites, int Ls, double M5, double mf, double b5,
+                          double c5, int dagger)
+{
+    const double prm[4] = {M5, mf, b5, c5};
+    return site_op_inv(out, in, nsites, Ls, mobius_m5_op, prm, dagger);
+}
+
+/* Mhat in_e (dagger: Mhat^dag) on even 5-d half fields. */
+int orc_dwf_mobius_schur(cplx *out, const cplx *in, const cplx *U, const int d[4], const int bc[4], int Ls,
+                         double M5, double mf, double b5, double c5, int dagger)
+{
+    long Vh = orc_volume(d) / 2, n5 = (long)Ls * Vh * SITE_DOF;
+    if (Ls < 1 || Ls > 64) return ORC_ERR_ARG;
+    cplx *t = malloc((size_t)n5 * sizeof(cplx)), *u = malloc((size_t)n5 * sizeof(cplx));
+    if (!t || !u) { free(t); free(u); return ORC_ERR_NOMEM; }
+    int rc;
+    if (!dagger) {
+        mobius_b(u, in, Vh, Ls, mf, b5, c5, 0);                                    /* u_e = B in_e              */
+        rc = dwf_hop_eo(t, u, U, d, bc, Ls, 0, 1);                                  /* t_o = M_oe in_e           */
+        if (rc == ORC_OK) rc = orc_dwf_mobius_m5_inv(u, t, Vh, Ls, M5, mf, b5, c5, 0); /* u_o = M5^-1 t_o       */
+        if (rc == ORC_OK) {
+            mobius_b(t, u, Vh, Ls, mf, b5, c5, 0);                                  /* t_o = B u_o               */
+            rc = dwf_hop_eo(u, t, U, d, bc, Ls, 0, 0);                              /* u_e = M_eo M5^-1 M_oe in_e */
+        }
+    } else {
+        rc = dwf_hop_eo(u, in, U, d, bc, Ls, 1, 1);                                 /* u_o = -H_eo^dag in_e / 2  */
+        if (rc == ORC_OK) {
+            mobius_b(t, u, Vh, Ls, mf, b5, c5, 1);                                  /* t_o = M_eo^dag in_e       */
+            rc = orc_dwf_mobius_m5_inv(u, t, Vh, Ls, M5, mf, b5, c5, 1);            /* u_o = M5^-dag t_o         */
+        }
+        if (rc == ORC_OK) rc = dwf_hop_eo(t, u, U, d, bc, Ls, 1, 0);                /* t_e = -H_oe^dag u_o / 2   */
+        if (rc == ORC_OK) mobius_b(u, t, Vh, Ls, mf, b5, c5, 1);                    /* u_e = M_oe^dag u_o        */
+    }
+    if (rc == ORC_OK) {
+        orc_dwf_mobius_m5(out, in, Vh, Ls, M5, mf, b5, c5, dagger);                 /* out = M5_M in_e           */
+        for (long i = 0; i < n5; ++i) out[i] -= u[i];
+    }
+    free(t);
+    free(u);
+    return rc;
+}
+
+/* bhat_e = eta_e - M_eo M5_M^{-1} eta_o (eta a full 5-d field, bhat_e an even half field). */
+int orc_dwf_mobius_eo_prepare(cplx *bhat, const cplx *eta, const cplx *U, const int d[4], const int bc[4], int Ls,
+                              double M5, double mf, double b5, double c5)
+{
+    long Vh = orc_volume(d) / 2, n5 = (long)Ls * Vh * SITE_DOF;
+    cplx *eo = malloc((size_t)n5 * sizeof(cplx)), *u = malloc((size_t)n5 * sizeof(cplx));
+    if (!eo || !u) { free(eo); free(u); return ORC_ERR_NOMEM; }
+    split_parity(eo, eta, d, Ls, 1, 0);
+    split_parity(bhat, eta, d, Ls, 0, 0);
+    int rc = orc_dwf_mobius_m5_inv(u, eo, Vh, Ls, M5, mf, b5, c5, 0); /* u_o = M5_M^-1 eta_o */
+    if (rc == ORC_OK) {
+        mobius_b(eo, u, Vh, Ls, mf, b5, c5, 0);                         /* B u_o               */
+        rc = dwf_hop_eo(u, eo, U, d, bc, Ls, 0, 0);                     /* M_eo M5_M^-1 eta_o  */
+    }
+    if (rc == ORC_OK)
+        for (long i = 0; i < n5; ++i) bhat[i] -= u[i];
+    free(eo);
+    free(u);
+    return rc;
+}
+
+/* psi (full 5-d field) from its even half x_e: psi_o = M5_M^{-1} (eta_o - M_oe x_e). */
+int orc_dwf_mobius_eo_reconstruct(cplx *psi, const cplx *xe, const cplx *eta, const cplx *U, const int d[4],
+                                  const int bc[4], int Ls, double M5, double mf, double b5, double c5)
+{
+    long Vh = orc_volume(d) / 2, n5 = (long)Ls * Vh * SITE_DOF;
+    cplx *t = malloc((size_t)n5 * sizeof(cplx)), *u = malloc((size_t)n5 * sizeof(cplx));
+    cplx *eo = malloc((size_t)n5 * sizeof(cplx));
+    if (!t || !u || !eo) { free(t); free(u); free(eo); return ORC_ERR_NOMEM; }
+    split_parity(eo, eta, d, Ls, 1, 0);                                  /* eta_o                 */
+    mobius_b(t, xe, Vh, Ls, mf, b5, c5, 0);                              /* t_e = B x_e           */
+    int rc = dwf_hop_eo(u, t, U, d, bc, Ls, 0, 1);                       /* u_o = M_oe x_e        */
+    if (rc == ORC_OK) {
+        for (long i = 0; i < n5; ++i) eo[i] -= u[i];
+        rc = orc_dwf_mobius_m5_inv(t, eo, Vh, Ls, M5, mf, b5, c5, 0);   /* t_o = M5_M^-1 (...)  */
+    }
+    if (rc == ORC_OK) {
+        split_parity((cplx *)xe, psi, d, Ls, 0, 1);
+        split_parity(t, psi, d, Ls, 1, 1);
+    }
+    free(t);
+    free(u);
     free(eo);
     return rc;
 }

@@ -45,10 +45,19 @@ MUTANTS = [
      "for (long i = 0; i < n5; ++i) u[i] = (c5 + b5) * t[i] - in[i];", ["mobius"]),
     ("domain-wall Schur complement sign", "for (long i = 0; i < n5; ++i) out[i] -= t[i];",
      "for (long i = 0; i < n5; ++i) out[i] += t[i];", ["dwf_eo"]),
-    ("domain-wall M5 inverse ignores the dagger", "orc_dwf_m5(col, e, 1, Ls, M5, mf, dagger);",
-     "orc_dwf_m5(col, e, 1, Ls, M5, mf, 0);", ["dwf_eo"]),
+    ("domain-wall M5 inverse ignores the dagger", "op(col, e, 1, Ls, prm, dagger);", "op(col, e, 1, Ls, prm, 0);",
+     ["dwf_eo"]),
     ("domain-wall source preparation with the wrong sign", "for (long i = 0; i < n5; ++i) bhat[i] -= eo[i];",
      "for (long i = 0; i < n5; ++i) bhat[i] += eo[i];", ["dwf_eo"]),
+    ("Moebius M5_M with the shift's sign flipped",
+     "out[i] = (4.0 - M5) * (b5 * in[i] + c5 * out[i]) + in[i] - out[i];",
+     "out[i] = (4.0 - M5) * (b5 * in[i] + c5 * out[i]) + in[i] + out[i];", ["mobius_eo"]),
+    ("Moebius Schur complement with B^dag in M_oe", "mobius_b(u, in, Vh, Ls, mf, b5, c5, 0);",
+     "mobius_b(u, in, Vh, Ls, mf, b5, c5, 1);", ["mobius_eo"]),
+    ("Moebius source preparation without B", "mobius_b(eo, u, Vh, Ls, mf, b5, c5, 0);",
+     "memcpy(eo, u, (size_t)n5 * sizeof(cplx));", ["mobius_eo"]),
+    ("Moebius reconstruction with the wrong sign", "for (long i = 0; i < n5; ++i) eo[i] -= u[i];",
+     "for (long i = 0; i < n5; ++i) eo[i] += u[i];", ["mobius_eo"]),
     ("SU(3) product with B transposed", "t += a[3 * i + k] * b[3 * k + j];", "t += a[3 * i + k] * b[3 * j + k];",
      ["su3"]),
     ("SU(3) product in the wrong order", "t += a[3 * i + k] * b[3 * k + j];", "t += b[3 * i + k] * a[3 * k + j];",
@@ -74,6 +83,9 @@ def run_pin(kind, orc):
         pins.test_mobius_reduces_to_shamir_and_its_c5_term_is_dw_times_s(orc)
     elif kind == "dwf_eo":
         pins.test_dwf_eo_schur_solve_matches_full_solve(orc)
+    elif kind == "mobius_eo":
+        pins.test_mobius_m5_is_the_zero_link_operator(orc)
+        pins.test_mobius_eo_schur_solve_matches_full_solve(orc)
     elif kind == "su3":
         pins.test_su3_mul_matches_numpy_and_group_closure(orc)
 

@@ -443,6 +443,60 @@ def test_dwf_eo_cg_small(orc):
     assert rel(orc.apply_normal(orc.OP_DWF_EO, x, U, prm), b) < 1e-9
 
 
+def test_mobius_m5_is_the_zero_link_operator(orc):
+    """The Moebius site-local part M5_M equals D_M with all links zero (the 4-d
+    hop vanishes), for several (b5, c5) and the dagger; its inverse inverts it.
+    Catches a wrong diagonal (4 - M5) b5 + 1, a wrong shift coefficient
+    (4 - M5) c5 - 1, or S in place of S^dag."""
+    dims, Ls, M5, mf = (2, 2, 2, 4), 5, 1.8, 0.07
+    V = 32
+    U0 = np.zeros((V, 4, 3, 3), dtype=complex)
+    psi = inputs.gaussian_spinor(V, seed=41, nrhs=Ls)
+    for b5, c5 in [(1.0, 0.0), (1.5, 0.5), (2.0, 1.0), (0.8, -0.3)]:
+        for dag in (False, True):
+            want = orc.dwf_mobius_dslash(psi, U0, dims, Ls, M5, mf, b5, c5, dagger=dag)
+            m5 = orc.dwf_mobius_m5(psi, Ls, M5, mf, b5, c5, dagger=dag)
+            assert rel(m5, want) < 1e-15
+            assert rel(orc.dwf_mobius_m5_inv(m5, Ls, M5, mf, b5, c5, dagger=dag), psi) < 1e-13
+
+
+def test_mobius_eo_schur_solve_matches_full_solve(orc):
+    """Solving D_M psi = eta for the Moebius operator through its even-odd Schur
+    complement (prepared source, dense solve of Mhat, reconstruction of the odd
+    half) gives numpy's dense solve of the full D_M, whose own pins tie it to
+    D_W and the Shamir operator; the daggered Mhat is the adjoint of Mhat, and
+    Mhat equals the Schur complement numpy forms from the blocks of the dense
+    D_M.  Catches B applied after the hop instead of before, a missing B in
+    M_eo or M_oe, a wrong M5_M, and sign errors in the three formulas."""
+    dims, Ls, M5, mf, b5, c5 = (2, 2, 2, 4), 4, 1.8, 0.05, 1.5, 0.5
+    V = 32
+    n = Ls * V * 12
+    U = inputs.gauge_field(dims, "random", seed=42)
+    eta = inputs.gaussian_spinor(V, seed=43, nrhs=Ls)
+    D = dense_map(lambda v: orc.dwf_mobius_dslash(v.reshape(Ls, V, 4, 3), U, dims, Ls, M5, mf, b5, c5), n)
+    psi = np.linalg.solve(D, eta.ravel()).reshape(Ls, V, 4, 3)
+    M = dense_map(lambda v: orc.dwf_mobius_schur(v.reshape(Ls, V // 2, 4, 3), U, dims, Ls, M5, mf, b5, c5), n // 2)
+    bhat = orc.dwf_mobius_eo_prepare(eta, U, dims, Ls, M5, mf, b5, c5)
+    xe = np.linalg.solve(M, bhat.ravel()).reshape(Ls, V // 2, 4, 3)
+    assert rel(orc.dwf_mobius_eo_reconstruct(xe, eta, U, dims, Ls, M5, mf, b5, c5), psi) < 1e-12
+    # the Schur complement of the dense operator's parity blocks
+    x = coords(dims)
+    par = (x.sum(axis=1) % 2).astype(int)
+    idx = np.arange(n).reshape(Ls, V, 12)
+    ev = idx[:, par == 0, :].ravel()
+    od = idx[:, par == 1, :].ravel()
+    schur = D[np.ix_(ev, ev)] - D[np.ix_(ev, od)] @ np.linalg.solve(D[np.ix_(od, od)], D[np.ix_(od, ev)])
+    assert np.max(np.abs(M - schur)) < 1e-12 * np.max(np.abs(schur))
+    Md = dense_map(lambda v: orc.dwf_mobius_schur(v.reshape(Ls, V // 2, 4, 3), U, dims, Ls, M5, mf, b5, c5,
+                                                  dagger=True), n // 2)
+    assert np.max(np.abs(Md - M.conj().T)) < 1e-13 * np.max(np.abs(M))
+    # b5 = 1, c5 = 0 is the Shamir Schur complement (a separate code path)
+    pe = inputs.gaussian_spinor(V // 2, seed=44, nrhs=Ls)
+    for dag in (False, True):
+        assert rel(orc.dwf_mobius_schur(pe, U, dims, Ls, M5, mf, 1.0, 0.0, dagger=dag),
+                   orc.dwf_schur(pe, U, dims, Ls, M5, mf, dagger=dag)) < 1e-14
+
+
 # ------------------------------------------------------------ SU(3) x SU(3)
 
 
