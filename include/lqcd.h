@@ -93,7 +93,7 @@ typedef struct {
     double M5;       /* domain-wall height */
     double mf;       /* domain-wall quark mass */
     int compress12;  /* 1: links stored as their first two rows, row 3 = conj(row1 x row2) */
-    int mobius;      /* 0: Shamir domain wall; 1: Moebius with b5, c5 (FP64/FP32 fields, no even-odd form):
+    int mobius;      /* 0: Shamir domain wall; 1: Moebius with b5, c5 (FP64/FP32 fields):
                         D_M = (b5 D_W(-M5) + 1) + (c5 D_W(-M5) - 1) S,  S psi(s) = P- psi(s+1) + P+ psi(s-1)
                         (walls -mf); b5 = 1, c5 = 0 is the Shamir operator */
     double b5, c5;   /* Moebius coefficients (read only when mobius = 1) */
@@ -165,8 +165,13 @@ int dwf_dslash_apply(lq_handle *h, void *out, const void *in, int fmt, int dagge
  * and lq_convert handle it as subset LQ_EVEN with nrhs = Ls.  A full 5-d field
  * is the five_d layout above.  fmt: LQ_F64 or LQ_F32, site-major or native
  * (FP16/BF16: LQ_ERR_ARG).  All three are asynchronous on `stream` and
- * reject overlapping buffers (LQ_ERR_ARG); they need lq_params.Ls >= 1 and the
- * Shamir form (lq_params.mobius = 0).
+ * reject overlapping buffers (LQ_ERR_ARG); they need lq_params.Ls >= 1.
+ * For the Moebius operator (lq_params.mobius = 1), with B = b5 + c5 S, the
+ * same three formulas hold with M5 replaced by the site-local part
+ *   M5_M = ((4 - M5) b5 + 1) + ((4 - M5) c5 - 1) S
+ * and M_eo = -1/2 H_eo B, M_oe = -1/2 H_oe B (B acts before the hop).  A
+ * singular M5_M ((4 - M5) b5 + 1 = 0, or 1 + mf g^Ls = 0 with
+ * g = (1 - (4 - M5) c5) / ((4 - M5) b5 + 1)) is LQ_ERR_ARG.
  *
  * dwf_schur_apply: out_e = Mhat in_e (dagger != 0: Mhat^dag in_e), 5-d half fields.
  * dwf_eo_prepare: bhat_e = eta_e - M_eo M5^{-1} eta_o from a full 5-d source eta.

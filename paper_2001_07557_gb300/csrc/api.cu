@@ -274,10 +274,147 @@ int native_dwf(lq_handle* h, int prec, char* out, const char* in, bool dag, cuda
     a.nrhs = h->p.Ls;
     a.Ls = h->p.Ls;
     a.mf = h->p.mf;
+    a.c_shift = -1.0;
     a.c_hop = -0.5;
     a.c_diag = 5.0 - h->p.M5;
     set_red(a, h);
     return status_of(launch_hop(prec, a, link_r12(h, prec), dag, EPI_DWF, h->hop_block[prec], st));
+}
+
+// Even-odd Moebius domain wall.  With B = b5 + c5 S the operator D_M = D_W(-M5) B + 1 - S
+// splits by 4-d parity into the site-local part M5_M = alpha + beta S,
+//   alpha = (4 - M5) b5 + 1,  beta = (4 - M5) c5 - 1,
+// and M_eo = -1/2 H_eo B, M_oe = -1/2 H_oe B (B acts before the hop).  B and M5_M
+// are polynomials in S, so they commute, and one sweep applies T = B M5_M^{-1}:
+//   Mhat in_e     = M5_M in_e + 1/2 H_eo T (-1/2 H_oe B in_e)
+//     chi = B in_e (5th-dimension pass);  tmp = -1/2 H_oe chi;  tmp = T tmp;
+//     out = alpha in + beta S in + 1/2 H_eo tmp   (one domain-wall hop launch)
+//   Mhat^dag in_e = M5_M^dag in_e + B^dag 1/2 H^dag_eo T^dag (-1/2 H^dag_oe in_e)
+//     tmp = -1/2 H^dag_oe in;  tmp = T^dag tmp;  chi = 1/2 H^dag_eo tmp;
+//     out = b5 chi + c5 S^dag chi + alpha in + beta S^dag in   (one 5th-dimension pass)
+static bool mobius_site(const lq_handle* h, double* alpha, double* beta) {
+    const double d4 = 4.0 - h->p.M5;
+    *alpha = d4 * h->p.b5 + 1.0;
+    *beta = d4 * h->p.c5 - 1.0;
+    double p, g, c;
+    return m5inv_coeffs(*alpha, *beta, h->p.mf, h->p.Ls, &p, &g, &c);
+}
+
+static int native_dwf_mobius_schur(lq_handle* h, int prec, char* out_e, const char* in_e, char* tmp, bool dag,
+                                   cudaStream_t st) {
+    const int Ls = h->p.Ls;
+    const size_t blk = native_block_bytes(h, prec);
+    const double b5 = h->p.b5, c5 = h->p.c5, mf = h->p.mf;
+    double alpha, beta;
+    if (!mobius_site(h, &alpha, &beta)) return LQ_ERR_ARG;
+    void* chi;
+    int rc = ensure_ws(h, WS_MOB, blk * (size_t)Ls, &chi);
+    if (rc) return rc;
+    char* c = static_cast<char*>(chi);
+    HopArgs a1;
+    if (!dag && launch_m5_lincomb(prec, c, in_e, nullptr, h->g.Vh, 1, blk, Ls, b5, c5, 0, 0, mf, false, st) !=
+                    cudaSuccess)
+        return LQ_ERR_CUDA;
+    if ((rc = prep_wilson_block(h, prec, tmp, dag ? in_e : c, 1, Ls, -0.5, &a1, st))) return rc;
+    a1.skip_stride = 0;  // the slices of one system share the system's skip flag
+    if ((rc = status_of(launch_hop(prec, a1, link_r12(h, prec), dag, EPI_HOP, h->hop_block[prec], st)))) return rc;
+    if (launch_m5inv_general(prec, tmp, tmp, h->g.Vh, blk, blk, Ls, alpha, beta, mf, true, b5, c5, dag, st) !=
+        cudaSuccess)
+        return LQ_ERR_CUDA;
+    if (dag) {
+        if ((rc = prep_wilson_block(h, prec, c, tmp, 0, Ls, 0.5, &a1, st))) return rc;
+        a1.skip_stride = 0;
+        if ((rc = status_of(launch_hop(prec, a1, link_r12(h, prec), true, EPI_HOP, h->hop_block[prec], st))))
+            return rc;
+        return launch_m5_lincomb(prec, out_e, c, in_e, h->g.Vh, 1, blk, Ls, b5, c5, alpha, beta, mf, true, st) ==
+                       cudaSuccess
+                   ? LQ_OK
+                   : LQ_ERR_CUDA;
+    }
+    const char* L;
+    size_t lb;
+    if ((rc = get_links(h, prec, &L, &lb, st))) return rc;
+    HopArgs a = base_args(h, L, lb);
+    a.in[0] = tmp;
+    a.x[0] = in_e;
+    a.out[0] = out_e;
+    a.in_rhs = a.out_rhs = a.x_rhs = blk;
+    a.parity0 = 0;
+    a.nparity = 1;
+    a.nrhs = Ls;
+    a.Ls = Ls;
+    a.mf = mf;
+    a.c_shift = beta;
+    a.c_hop = 0.5;
+    a.c_diag = alpha;
+    set_red(a, h);
+    return status_of(launch_hop(prec, a, link_r12(h, prec), false, EPI_DWF, h->hop_block[prec], st));
+}
+
+// bhat_e = eta_e - M_eo M5_M^{-1} eta_o = eta_e + 1/2 H_eo T eta_o
+static int native_dwf_mobius_prepare(lq_handle* h, int prec, char* bhat_e, const char* eta, char* tmp,
+                                     cudaStream_t st) {
+    const int Ls = h->p.Ls;
+    const size_t blk = native_block_bytes(h, prec);
+    double alpha, beta;
+    if (!mobius_site(h, &alpha, &beta)) return LQ_ERR_ARG;
+    if (launch_m5inv_general(prec, tmp, eta + blk, h->g.Vh, blk, 2 * blk, Ls, alpha, beta, h->p.mf, true, h->p.b5,
+                             h->p.c5, false, st) != cudaSuccess)
+        return LQ_ERR_CUDA;
+    const char* L;
+    size_t lb;
+    int rc = get_links(h, prec, &L, &lb, st);
+    if (rc) return rc;
+    HopArgs a = base_args(h, L, lb);
+    a.in[0] = tmp;
+    a.x[0] = eta;
+    a.out[0] = bhat_e;
+    a.in_rhs = a.out_rhs = blk;
+    a.x_rhs = 2 * blk;
+    a.parity0 = 0;
+    a.nparity = 1;
+    a.nrhs = Ls;
+    a.c_hop = 0.5;
+    a.c_diag = 1.0;
+    a.skip = nullptr;  // a source preparation is never skipped
+    return status_of(launch_hop(prec, a, link_r12(h, prec), false, EPI_DIAG, h->hop_block[prec], st));
+}
+
+// psi_e = x_e;  psi_o = M5_M^{-1} (eta_o - M_oe x_e) = M5_M^{-1} (eta_o + 1/2 H_oe B x_e)
+static int native_dwf_mobius_reconstruct(lq_handle* h, int prec, char* psi, const char* x_e, const char* eta,
+                                         cudaStream_t st) {
+    const int Ls = h->p.Ls;
+    const size_t blk = native_block_bytes(h, prec);
+    double alpha, beta;
+    if (!mobius_site(h, &alpha, &beta)) return LQ_ERR_ARG;
+    void* chi;
+    int rc = ensure_ws(h, WS_MOB, blk * (size_t)Ls, &chi);
+    if (rc) return rc;
+    if (launch_m5_lincomb(prec, chi, x_e, nullptr, h->g.Vh, 1, blk, Ls, h->p.b5, h->p.c5, 0, 0, h->p.mf, false, st) !=
+        cudaSuccess)
+        return LQ_ERR_CUDA;
+    const char* L;
+    size_t lb;
+    if ((rc = get_links(h, prec, &L, &lb, st))) return rc;
+    HopArgs a = base_args(h, L, lb);
+    a.in[1] = static_cast<const char*>(chi);
+    a.x[1] = eta + blk;
+    a.out[1] = psi + blk;
+    a.in_rhs = blk;
+    a.out_rhs = a.x_rhs = 2 * blk;
+    a.parity0 = 1;
+    a.nparity = 1;
+    a.nrhs = Ls;
+    a.c_hop = 0.5;
+    a.c_diag = 1.0;
+    a.skip = nullptr;
+    if ((rc = status_of(launch_hop(prec, a, link_r12(h, prec), false, EPI_DIAG, h->hop_block[prec], st))))
+        return rc;
+    if (launch_m5inv_general(prec, psi + blk, psi + blk, h->g.Vh, 2 * blk, 2 * blk, Ls, alpha, beta, h->p.mf, false,
+                             1.0, 0.0, false, st) != cudaSuccess ||
+        cudaMemcpy2DAsync(psi, 2 * blk, x_e, blk, blk, Ls, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return LQ_ERR_CUDA;
+    return LQ_OK;
 }
 
 // Even-odd domain wall: Mhat = M5 - M_eo M5^{-1} M_oe with M_eo = -1/2 H_eo on
@@ -288,6 +425,7 @@ int native_dwf(lq_handle* h, int prec, char* out, const char* in, bool dag, cuda
 // The dagger uses the daggered hop, (M5^dag)^{-1} and M5^dag.
 int native_dwf_schur(lq_handle* h, int prec, char* out_e, const char* in_e, char* tmp, bool dag, cudaStream_t st) {
     if (prec != LQ_F64 && prec != LQ_F32) return LQ_ERR_ARG;
+    if (h->p.mobius) return native_dwf_mobius_schur(h, prec, out_e, in_e, tmp, dag, st);
     const int Ls = h->p.Ls;
     const size_t blk = native_block_bytes(h, prec);
     HopArgs a1;
@@ -310,6 +448,7 @@ int native_dwf_schur(lq_handle* h, int prec, char* out_e, const char* in_e, char
     a.nrhs = Ls;
     a.Ls = Ls;
     a.mf = h->p.mf;
+    a.c_shift = -1.0;
     a.c_hop = 0.5;
     a.c_diag = 5.0 - h->p.M5;
     set_red(a, h);
@@ -319,6 +458,7 @@ int native_dwf_schur(lq_handle* h, int prec, char* out_e, const char* in_e, char
 // bhat_e = eta_e - M_eo M5^{-1} eta_o = eta_e + 1/2 H_eo M5^{-1} eta_o  (eta a full 5-d field)
 int native_dwf_prepare(lq_handle* h, int prec, char* bhat_e, const char* eta, char* tmp, cudaStream_t st) {
     if (prec != LQ_F64 && prec != LQ_F32) return LQ_ERR_ARG;
+    if (h->p.mobius) return native_dwf_mobius_prepare(h, prec, bhat_e, eta, tmp, st);
     const int Ls = h->p.Ls;
     const size_t blk = native_block_bytes(h, prec);
     if (launch_m5inv(prec, tmp, eta + blk, h->g.Vh, blk, 2 * blk, Ls, h->p.M5, h->p.mf, false, st) != cudaSuccess)
@@ -345,6 +485,7 @@ int native_dwf_prepare(lq_handle* h, int prec, char* bhat_e, const char* eta, ch
 // psi_e = x_e;  psi_o = M5^{-1} (eta_o - M_oe x_e) = M5^{-1} (eta_o + 1/2 H_oe x_e)
 int native_dwf_reconstruct(lq_handle* h, int prec, char* psi, const char* x_e, const char* eta, cudaStream_t st) {
     if (prec != LQ_F64 && prec != LQ_F32) return LQ_ERR_ARG;
+    if (h->p.mobius) return native_dwf_mobius_reconstruct(h, prec, psi, x_e, eta, st);
     const int Ls = h->p.Ls;
     const size_t blk = native_block_bytes(h, prec);
     const char* L;
@@ -604,11 +745,11 @@ int dwf_dslash_apply(lq_handle* h, void* out, const void* in, int fmt, int dagge
     return LQ_OK;
 }
 
-// Even-odd domain wall: argument checks shared by the three calls (FP64/FP32 only).
+// Even-odd domain wall (Shamir or Moebius): argument checks shared by the three calls (FP64/FP32 only).
 static int dwf_eo_args(lq_handle* h, int fmt) {
     if (!h || !valid_fmt(fmt)) return LQ_ERR_ARG;
     const int prec = fmt & 0xF;
-    if (h->p.Ls < 1 || h->p.mobius || (prec != LQ_F64 && prec != LQ_F32)) return LQ_ERR_ARG;
+    if (h->p.Ls < 1 || (prec != LQ_F64 && prec != LQ_F32)) return LQ_ERR_ARG;
     return LQ_OK;
 }
 

@@ -193,6 +193,10 @@ int run_cg(lq_handle* h, const OpGeom& og, const Ctl& c, int pp, const VecRef& e
         const size_t f5 = og.bytes(h, pp);
         if ((rc = ensure_ws(h, WS_MOB, f5, &w)) || (rc = ensure_ws(h, WS_MOB + 1, f5, &w))) return rc;
     }
+    if (og.op == LQ_OP_DWF_EO_NORMAL && h->p.mobius) {    // and the even-odd Moebius operator's one half field
+        void* w;
+        if ((rc = ensure_ws(h, WS_MOB, og.bytes(h, pp), &w))) return rc;
+    }
     const int Vh = h->g.Vh;
     if (cudaMemsetAsync(e.ptr, 0, og.bytes(h, px), s) != cudaSuccess) return LQ_ERR_CUDA;
     if (pr == px ? cudaMemcpyAsync(v.r.ptr, rhs.ptr, og.bytes(h, px), cudaMemcpyDeviceToDevice, s) != cudaSuccess
@@ -367,8 +371,8 @@ extern "C" int cg_solve(lq_handle* h, void* x, const void* b, const lq_cg_params
         subset = LQ_FULL;
         break;
     case LQ_OP_DWF_EO_NORMAL:
-        // Ls even half fields; the site-local inverse M5^{-1} exists for FP64/FP32 fields and the Shamir form only
-        if (h->p.Ls < 1 || h->p.mobius || cp->nrhs != 1 || (fprec != LQ_F64 && fprec != LQ_F32)) return LQ_ERR_ARG;
+        // Ls even half fields; the site-local inverse M5^{-1} exists for FP64/FP32 fields
+        if (h->p.Ls < 1 || cp->nrhs != 1 || (fprec != LQ_F64 && fprec != LQ_F32)) return LQ_ERR_ARG;
         if (cp->mode != LQ_CG_PLAIN && cp->inner != LQ_F32) return LQ_ERR_ARG;
         og.nblk = h->p.Ls;
         subset = LQ_EVEN;

@@ -19,6 +19,7 @@
 // the call may run in place.  O(Ls) work per component, bandwidth-bound.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <type_traits>
 
 #include "lqcd_kernels.h"
@@ -42,9 +43,17 @@ __device__ __forceinline__ double2 axpby4<double2, double>(double a, double2 x, 
 }
 
 // P = LQ_F32: 6 planes of float4 (2 complex) per site; LQ_F64: 12 planes of double2.
-template <int P>
+// The general site-local matrix alpha + beta S (Shamir M5: alpha = 5 - M5, beta = -1)
+// divided by alpha is 1 - g L + corner, g = -beta / alpha: the sweep is
+// z(s) = p x(s) + g z(s-1) with p = 1 / alpha, the correction weights w_j = g^(j+1)
+// and c = mf / (1 + mf g^Ls).  WITH_B also applies B = b5 + c5 S to the result
+// (B commutes with the inverse, both being polynomials in S): S reads the slice
+// before s in the sweep's order, and across the wall it reads y at the sweep's
+// end, which is y_last = z_end - c g^Ls z_end, known after the first sweep.
+template <int P, bool WITH_B>
 __global__ void __launch_bounds__(256) m5inv_kernel(char* out, const char* in, int Vh, size_t out_stride,
-                                                    size_t in_stride, int Ls, double inv_a_d, double c_d, int dag) {
+                                                    size_t in_stride, int Ls, double p_d, double g_d, double c_d,
+                                                    double b5_d, double c5_d, double mf_d, int dag) {
     pdl_enter();
     using V = typename std::conditional<P == LQ_F64, double2, float4>::type;
     using T = typename std::conditional<P == LQ_F64, double, float>::type;
@@ -53,24 +62,37 @@ __global__ void __launch_bounds__(256) m5inv_kernel(char* out, const char* in, i
     if (idx >= (long)Vh * NPL) return;
     const int k = (int)(idx / Vh), i = (int)(idx - (long)k * Vh);  // plane-major: a warp reads 32 sites of a plane
     const bool fwd = (k < NPL / 2) != (dag != 0);  // spins 0,1 sweep upwards in s unless daggered
-    const T inv_a = (T)inv_a_d, c = (T)c_d;
+    const T pc = (T)p_d, g = (T)g_d, c = (T)c_d;
     const char* src = in + ((size_t)k * Vh + i) * sizeof(V);
     char* dst = out + ((size_t)k * Vh + i) * sizeof(V);
     auto slice = [&](int j) { return fwd ? j : Ls - 1 - j; };
     V z = {};
+    T w = g;
     for (int j = 0; j < Ls; ++j) {
         const V x = *reinterpret_cast<const V*>(src + (size_t)slice(j) * in_stride);
-        z = axpby4<V, T>(inv_a, x, inv_a, z);
+        z = axpby4<V, T>(pc, x, g, z);
+        if (WITH_B && j + 1 < Ls) w *= g;
     }
     const V zend = z;
+    V prev = {};
+    if constexpr (WITH_B) prev = axpby4<V, T>((T)1, zend, -c * w, zend);  // y at the sweep's last slice
+    const T b5 = (T)b5_d, c5 = (T)c5_d;
+    T cw = -(T)mf_d * c5;  // S across the wall: -mf
     z = V{};
-    T w = inv_a;
+    w = g;
     for (int j = 0; j < Ls; ++j) {
         const int s = slice(j);
         const V x = *reinterpret_cast<const V*>(src + (size_t)s * in_stride);
-        z = axpby4<V, T>(inv_a, x, inv_a, z);
-        *reinterpret_cast<V*>(dst + (size_t)s * out_stride) = axpby4<V, T>((T)1, z, -c * w, zend);
-        w *= inv_a;
+        z = axpby4<V, T>(pc, x, g, z);
+        const V y = axpby4<V, T>((T)1, z, -c * w, zend);
+        if constexpr (WITH_B) {
+            *reinterpret_cast<V*>(dst + (size_t)s * out_stride) = axpby4<V, T>(b5, y, cw, prev);
+            prev = y;
+            cw = c5;
+        } else {
+            *reinterpret_cast<V*>(dst + (size_t)s * out_stride) = y;
+        }
+        w *= g;
     }
 }
 
@@ -136,13 +158,55 @@ cudaError_t launch_m5inv(int prec, void* out, const void* in, int Vh, size_t out
     const long n = (long)Vh * npl;
     const int grid = (int)((n + 255) / 256);
     if (prec == LQ_F64)
-        launch_pdl(m5inv_kernel<LQ_F64>, grid, 256, 0, st, static_cast<char*>(out), static_cast<const char*>(in), Vh,
-                                                   out_stride, in_stride, Ls, 1.0 / a, c, dag);
+        launch_pdl(m5inv_kernel<LQ_F64, false>, grid, 256, 0, st, static_cast<char*>(out), static_cast<const char*>(in),
+                   Vh, out_stride, in_stride, Ls, 1.0 / a, 1.0 / a, c, 1.0, 0.0, mf, dag);
     else if (prec == LQ_F32)
-        launch_pdl(m5inv_kernel<LQ_F32>, grid, 256, 0, st, static_cast<char*>(out), static_cast<const char*>(in), Vh,
-                                                   out_stride, in_stride, Ls, 1.0 / a, c, dag);
+        launch_pdl(m5inv_kernel<LQ_F32, false>, grid, 256, 0, st, static_cast<char*>(out), static_cast<const char*>(in),
+                   Vh, out_stride, in_stride, Ls, 1.0 / a, 1.0 / a, c, 1.0, 0.0, mf, dag);
     else
         return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+bool m5inv_coeffs(double alpha, double beta, double mf, int Ls, double* p, double* g, double* c) {
+    if (!(alpha != 0.0) || Ls < 1) return false;
+    *p = 1.0 / alpha;
+    *g = -beta / alpha;
+    double gL = 1.0;
+    for (int s = 0; s < Ls; ++s) gL *= *g;
+    const double den = 1.0 + mf * gL;
+    if (!(den != 0.0) || !std::isfinite(*p) || !std::isfinite(den)) return false;
+    *c = mf / den;
+    return true;
+}
+
+cudaError_t launch_m5inv_general(int prec, void* out, const void* in, int Vh, size_t out_stride, size_t in_stride,
+                                 int Ls, double alpha, double beta, double mf, bool with_b, double b5, double c5,
+                                 bool dag, cudaStream_t st) {
+    double p, g, c;
+    if (!m5inv_coeffs(alpha, beta, mf, Ls, &p, &g, &c)) return cudaErrorInvalidValue;
+    const int npl = prec == LQ_F64 ? 12 : 6;
+    const long n = (long)Vh * npl;
+    const int grid = (int)((n + 255) / 256);
+    auto o = static_cast<char*>(out);
+    auto x = static_cast<const char*>(in);
+    if (prec == LQ_F64) {
+        if (with_b)
+            launch_pdl(m5inv_kernel<LQ_F64, true>, grid, 256, 0, st, o, x, Vh, out_stride, in_stride, Ls, p, g, c, b5, c5,
+                       mf, dag);
+        else
+            launch_pdl(m5inv_kernel<LQ_F64, false>, grid, 256, 0, st, o, x, Vh, out_stride, in_stride, Ls, p, g, c, 1.0,
+                       0.0, mf, dag);
+    } else if (prec == LQ_F32) {
+        if (with_b)
+            launch_pdl(m5inv_kernel<LQ_F32, true>, grid, 256, 0, st, o, x, Vh, out_stride, in_stride, Ls, p, g, c, b5, c5,
+                       mf, dag);
+        else
+            launch_pdl(m5inv_kernel<LQ_F32, false>, grid, 256, 0, st, o, x, Vh, out_stride, in_stride, Ls, p, g, c, 1.0,
+                       0.0, mf, dag);
+    } else {
+        return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

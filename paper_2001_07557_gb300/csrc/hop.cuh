@@ -145,15 +145,15 @@ __global__ void __launch_bounds__(128) wilson_hop_kernel(const HopArgs a) {
     }
     if constexpr (EPI == EPI_DWF) {
         // P+ = upper spins (gamma_5 = diag(1,1,-1,-1)).  Non-dagger: upper from
-        // s-1, lower from s+1; dagger swaps.  Coefficient -1, or +mf across the wall.
+        // s-1, lower from s+1; dagger swaps.  Coefficient c_shift (Shamir: -1), times -mf across the wall.
         const int Ls = a.Ls;
         const int s = rhs;
         const int s_up = DAG ? (s + 1 == Ls ? 0 : s + 1) : (s == 0 ? Ls - 1 : s - 1);
         const int s_dn = DAG ? (s == 0 ? Ls - 1 : s - 1) : (s + 1 == Ls ? 0 : s + 1);
         const bool wrap_up = DAG ? (s + 1 == Ls) : (s == 0);
         const bool wrap_dn = DAG ? (s == 0) : (s + 1 == Ls);
-        const T c_up = wrap_up ? (T)a.mf : (T)-1;
-        const T c_dn = wrap_dn ? (T)a.mf : (T)-1;
+        const T c_up = wrap_up ? (T)(-a.c_shift * a.mf) : (T)a.c_shift;
+        const T c_dn = wrap_dn ? (T)(-a.c_shift * a.mf) : (T)a.c_shift;
         cplx<T> su[12], sd[12];
         load_spinor<P, T>(a.x[p] + (size_t)s_up * a.x_rhs, g.Vh, i, su);
         load_spinor<P, T>(a.x[p] + (size_t)s_dn * a.x_rhs, g.Vh, i, sd);

@@ -289,8 +289,8 @@ __device__ __forceinline__ void hop_async_site(const HopArgs& a, int i, int rhs,
         s_dn = DAG ? (sl == 0 ? Ls - 1 : sl - 1) : (sl + 1 == Ls ? 0 : sl + 1);
         const bool wrap_up = DAG ? (sl + 1 == Ls) : (sl == 0);
         const bool wrap_dn = DAG ? (sl == 0) : (sl + 1 == Ls);
-        c_up = wrap_up ? (T)a.mf : (T)-1;
-        c_dn = wrap_dn ? (T)a.mf : (T)-1;
+        c_up = wrap_up ? (T)(-a.c_shift * a.mf) : (T)a.c_shift;
+        c_dn = wrap_dn ? (T)(-a.c_shift * a.mf) : (T)a.c_shift;
         // only P+ psi(s_up) (spins 0,1) and P- psi(s_dn) (spins 2,3) are needed
         async_half_spinor<P, R12, NT, true>(extra + St::SPIN_BYTES, a.x[p] + (size_t)s_up * a.x_rhs, g.Vh, i, t);
         async_half_spinor<P, R12, NT, false>(extra + St::SPIN_BYTES + St::HALF_BYTES,

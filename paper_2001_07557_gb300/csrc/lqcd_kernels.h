@@ -30,6 +30,9 @@ struct HopArgs {
     double c_hop, c_diag;
     int Ls;
     double mf;
+    // domain-wall epilogue: coefficient of (S x)(s) = P+ x(s_up) + P- x(s_dn), walls
+    // -mf (the Shamir operator's site-local part takes -1; set at every EPI_DWF launch)
+    double c_shift;
     const int* skip;  // optional per-rhs flags (skip[rhs * skip_stride]): a set flag ends the block at once
     int skip_stride;
     // optional fused |out|^2 per right-hand side (one group for the domain wall):
@@ -58,6 +61,16 @@ cudaError_t launch_hop(int prec, const HopArgs& a, bool r12, bool dag, int epi, 
 // bytes.  In place allowed.  (dwf_eo.cu)
 cudaError_t launch_m5inv(int prec, void* out, const void* in, int Vh, size_t out_stride, size_t in_stride, int Ls,
                          double M5, double mf, bool dag, cudaStream_t st);
+
+// The general site-local inverse (alpha + beta S)^{-1} (dag: with S^dag), times
+// B = b5 + c5 S (or S^dag) when with_b.  Same layouts as launch_m5inv; in place
+// allowed.  m5inv_coeffs gives false when the matrix is singular (alpha = 0 or
+// 1 + mf (-beta/alpha)^Ls = 0); the launcher then returns cudaErrorInvalidValue
+// without launching.  (dwf_eo.cu)
+bool m5inv_coeffs(double alpha, double beta, double mf, int Ls, double* p, double* g, double* c);
+cudaError_t launch_m5inv_general(int prec, void* out, const void* in, int Vh, size_t out_stride, size_t in_stride,
+                                 int Ls, double alpha, double beta, double mf, bool with_b, double b5, double c5,
+                                 bool dag, cudaStream_t st);
 
 // out(s) = a u(s) + b (S u)(s) + c v(s) + d (S v)(s), S psi(s) = P- psi(s+1) +
 // P+ psi(s-1) with walls -mf (dag: S^dag); v may be null.  Native FP64/FP32
