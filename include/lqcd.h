@@ -304,6 +304,42 @@ int dslash_apply_slices(lq_handle *h, void *out, const void *in, int fmt, int t0
 int lq_face_copy(lq_handle *hd, void *dst, int t_dst, lq_handle *hs, const void *src, int t_src, int fmt, double scale,
                  void *stream);
 
+/*
+ * Spin-projected faces: the exchange of lq_face_copy at half the bytes.  A hop
+ * reads a ghost slice only through the time-direction projector, (1 + S gamma_t)
+ * with S = +1 for the ghost below the slab and S = -1 for the ghost above it
+ * (D^dag: the opposite signs).  In the chiral basis gamma_t = [[0, 1], [1, 0]],
+ * (1 + S gamma_t) psi = [h; S h] with h = psi_up + S psi_dn, 2 spins x 3 colours,
+ * so only h has to travel (the halo exchange of Sec. 3.2 would send it between
+ * ranks; here a cudaMemcpyAsync between two wire buffers stands in for it).
+ *
+ * Wire layout (the only format on the wire; both sides are native fields of
+ * precision fmt & 0xF): two blocks, one per spatial parity (x0 + x1 + x2) mod 2,
+ * of V3/2 sites (V3 = L0 L1 L2) in the slice's run order.  Per block: FP64
+ * 6 planes of 16 B, FP32 3 planes of 16 B, FP16/BF16 3 planes of 8 B followed
+ * by one FP32 norm per site.  Because the wire is indexed by spatial parity,
+ * sender and receiver slices may differ by any distance.
+ *
+ * lq_face_wire_bytes: bytes of one wire buffer for h's slices (L0 L1 L2 / 2
+ *   sites per block) in format fmt.
+ * lq_face_pack: wire = scale * h of time slice t_src of src (a full native
+ *   field of h's lattice) for projector sign S = sign (+1 or -1).  scale is
+ *   +1, or -1 across the global antiperiodic time boundary.
+ * lq_face_unpack: time slice t_dst of dst (a full native field of h's
+ *   lattice) = the ghost spinor chi = [h/2; S h/2] (FP16/BF16: [h; S h] with
+ *   the norm halved), whose projection chi_up + S chi_dn is h exactly: a hop
+ *   that reads the ghost through (1 + S gamma_t) then reproduces the
+ *   single-domain result bit for bit.  The other spin components of the
+ *   ghost are not those of psi; only a hop through the same projector may
+ *   read it.
+ * Both: the field must be native (LQ_ERR_LAYOUT otherwise) and 16-byte
+ * aligned, as must the wire (LQ_ERR_LAYOUT); sign not +-1, t out of range or
+ * an overlap of field and wire is LQ_ERR_ARG.  Asynchronous on `stream`.
+ */
+int lq_face_wire_bytes(const lq_handle *h, int fmt, size_t *bytes);
+int lq_face_pack(lq_handle *h, void *wire, const void *src, int t_src, int fmt, int sign, double scale, void *stream);
+int lq_face_unpack(lq_handle *h, void *dst, int t_dst, const void *wire, int fmt, int sign, void *stream);
+
 /* ---------------------------------------------------- SU(3) x SU(3) */
 
 /*

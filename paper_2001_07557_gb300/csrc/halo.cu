@@ -5,7 +5,12 @@
 //     slices only, so that the interior of a slab can be computed while its
 //     faces are in flight;
 //   * lq_face_copy: one time slice of a native field into a slice of another
-//     field, times +-1 (the antiperiodic phase at the global time boundary).
+//     field, times +-1 (the antiperiodic phase at the global time boundary);
+//   * lq_face_pack / lq_face_unpack: the same exchange with spin-projected
+//     faces.  A hop reads a ghost slice only through the time-direction
+//     projector (1 + S gamma_t), so only h = psi_up + S psi_dn (2 spins x 3
+//     colours, half of the spinor) has to move; the receiver rebuilds a ghost
+//     spinor chi with (1 + S gamma_t) chi = (1 + S gamma_t) psi bit for bit.
 // In the native layout, time slice t of a lattice is the run of checkerboard
 // sites [t V3/2, (t+1) V3/2) (V3 = L0 L1 L2, even) of every plane of both
 // parity blocks, with the same order of sites inside the run.  A face
@@ -15,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "handle.h"
 #include "pdl.cuh"
@@ -58,6 +64,173 @@ __global__ void face_copy_kernel(char* dst, const char* src, int vh_d, int vh_s,
         float* d = reinterpret_cast<float*>(dst + (size_t)p * site_bytes * vh_d + 48 * (size_t)vh_d);
         d[e0_d + e] = (float)scale * s[e0_s + e];
     }
+}
+
+// Spin-projected faces.  In the chiral basis gamma_t = [[0, 1], [1, 0]], so
+// (1 + S gamma_t) psi = [h; S h] with h = psi_up + S psi_dn: h[j] = s[j] + S s[6 + j]
+// (complex index = spin * 3 + colour), computed with the same additions as the
+// hop's own projection.  The wire holds h for the V3/2 sites of each spatial
+// parity sp = (x0 + x1 + x2) mod 2, in the slice's run order; the site parity
+// block of slice t is sp ^ (t & 1).  Wire planes per spatial-parity block of n
+// sites: FP64 6 x 16 B, FP32 3 x 16 B, FP16/BF16 3 x 8 B plus an FP32 norm.
+// The ghost gets chi = [h / 2; S h / 2] (FP16/BF16: chi = [h; S h] with the
+// norm halved), so the hop's projection of chi, chi_up + S chi_dn, is exactly h.
+template <int P>
+struct Wire {
+    static constexpr bool NORM = P == LQ_F16 || P == LQ_BF16;
+    static constexpr int UNIT = NORM ? 8 : 16;           // bytes of one plane element
+    static constexpr int NPL = P == LQ_F64 ? 6 : 3;      // planes of h
+    static constexpr int SITE = NPL * UNIT + (NORM ? 4 : 0);
+};
+
+template <int P, int S>
+__global__ void face_pack_kernel(char* wire, const char* src, int vh, int t, int n, double scale) {
+    pdl_enter();
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= 2 * n) return;
+    const int sp = u / n, e = u - sp * n;
+    const int p = sp ^ (t & 1);
+    const int i = t * n + e;
+    char* w = wire + (size_t)sp * Wire<P>::SITE * n;
+    if constexpr (P == LQ_F64 || P == LQ_F32) {
+        using T = typename std::conditional<P == LQ_F64, double, float>::type;
+        cplx<T> s[12];
+        load_spinor<P, T>(src + (size_t)p * Prec<P>::spinor_bytes * vh, vh, i, s);
+        cplx<T> h[6];
+        const T c = (T)scale;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            const cplx<T> a = cadds<S>(s[j], s[6 + j]);
+            h[j] = {c * a.re, c * a.im};
+        }
+        if constexpr (P == LQ_F64) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) reinterpret_cast<double2*>(w)[(size_t)k * n + e] = make_double2(h[k].re, h[k].im);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                reinterpret_cast<float4*>(w)[(size_t)k * n + e] =
+                    make_float4(h[2 * k].re, h[2 * k].im, h[2 * k + 1].re, h[2 * k + 1].im);
+        }
+    } else {
+        const char* blk = src + (size_t)p * Prec<P>::spinor_bytes * vh;
+        const uint4* q = reinterpret_cast<const uint4*>(blk);
+        uint32_t s[12];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint4 v = q[(size_t)k * vh + i];
+            s[4 * k] = v.x, s[4 * k + 1] = v.y, s[4 * k + 2] = v.z, s[4 * k + 3] = v.w;
+        }
+        uint32_t h[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) h[j] = h2_adds<P, S>(s[j], s[6 + j]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) reinterpret_cast<uint2*>(w)[(size_t)k * n + e] = make_uint2(h[2 * k], h[2 * k + 1]);
+        const float nrm = reinterpret_cast<const float*>(blk + (size_t)48 * vh)[i];
+        reinterpret_cast<float*>(w + (size_t)24 * n)[e] = (float)scale * nrm;
+    }
+}
+
+template <int P, int S>
+__global__ void face_unpack_kernel(char* dst, const char* wire, int vh, int t, int n) {
+    pdl_enter();
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= 2 * n) return;
+    const int sp = u / n, e = u - sp * n;
+    const int p = sp ^ (t & 1);
+    const int i = t * n + e;
+    const char* w = wire + (size_t)sp * Wire<P>::SITE * n;
+    char* blk = dst + (size_t)p * Prec<P>::spinor_bytes * vh;
+    if constexpr (P == LQ_F64 || P == LQ_F32) {
+        using T = typename std::conditional<P == LQ_F64, double, float>::type;
+        cplx<T> h[6];
+        if constexpr (P == LQ_F64) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const double2 v = reinterpret_cast<const double2*>(w)[(size_t)k * n + e];
+                h[k] = {v.x, v.y};
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float4 v = reinterpret_cast<const float4*>(w)[(size_t)k * n + e];
+                h[2 * k] = {v.x, v.y};
+                h[2 * k + 1] = {v.z, v.w};
+            }
+        }
+        cplx<T> s[12];
+        const T half = (T)0.5, sh = (T)(0.5 * S);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            s[j] = {half * h[j].re, half * h[j].im};
+            s[6 + j] = {sh * h[j].re, sh * h[j].im};
+        }
+        store_spinor<P, T>(blk, vh, i, s);
+    } else {
+        uint32_t s[12];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint2 v = reinterpret_cast<const uint2*>(w)[(size_t)k * n + e];
+            s[2 * k] = v.x, s[2 * k + 1] = v.y;
+        }
+#pragma unroll
+        for (int j = 0; j < 6; ++j) s[6 + j] = S > 0 ? s[j] : s[j] ^ 0x80008000u;  // S h: flip both sign bits
+        uint4* q = reinterpret_cast<uint4*>(blk);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) q[(size_t)k * vh + i] = make_uint4(s[4 * k], s[4 * k + 1], s[4 * k + 2], s[4 * k + 3]);
+        const float nrm = reinterpret_cast<const float*>(w + (size_t)24 * n)[e];
+        reinterpret_cast<float*>(blk + (size_t)48 * vh)[i] = 0.5f * nrm;
+    }
+}
+
+template <int P>
+cudaError_t launch_face(bool pack, char* field, char* wire, int vh, int t, int n, int sign, double scale,
+                        cudaStream_t st) {
+    const int grid = (2 * n + 255) / 256;
+    if (pack) {
+        const char* src = field;
+        if (sign > 0) launch_pdl(face_pack_kernel<P, 1>, grid, 256, 0, st, wire, src, vh, t, n, scale);
+        else launch_pdl(face_pack_kernel<P, -1>, grid, 256, 0, st, wire, src, vh, t, n, scale);
+    } else {
+        const char* w = wire;
+        if (sign > 0) launch_pdl(face_unpack_kernel<P, 1>, grid, 256, 0, st, field, w, vh, t, n);
+        else launch_pdl(face_unpack_kernel<P, -1>, grid, 256, 0, st, field, w, vh, t, n);
+    }
+    return cudaGetLastError();
+}
+
+size_t wire_bytes(int prec, int n) {
+    switch (prec) {
+    case LQ_F64: return (size_t)2 * n * Wire<LQ_F64>::SITE;
+    case LQ_F32: return (size_t)2 * n * Wire<LQ_F32>::SITE;
+    case LQ_F16: return (size_t)2 * n * Wire<LQ_F16>::SITE;
+    default: return (size_t)2 * n * Wire<LQ_BF16>::SITE;
+    }
+}
+
+int face_projected(lq_handle* h, bool pack, void* field, void* wire, int t, int fmt, int sign, double scale,
+                   void* stream) {
+    if (!h || !field || !wire || !valid_fmt(fmt)) return LQ_ERR_ARG;
+    if (!(fmt & LQ_NATIVE)) return LQ_ERR_LAYOUT;
+    if (sign != 1 && sign != -1) return LQ_ERR_ARG;
+    if (t < 0 || t >= h->p.dims[3]) return LQ_ERR_ARG;
+    if (!aligned16(field) || !aligned16(wire)) return LQ_ERR_LAYOUT;
+    const int prec = fmt & 0xF;
+    const int n = h->p.dims[0] * h->p.dims[1] * h->p.dims[2] / 2;
+    if (overlap(field, field_bytes(h, fmt, LQ_FULL, 1), wire, wire_bytes(prec, n))) return LQ_ERR_ARG;
+    DeviceGuard dg(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char* f = static_cast<char*>(field);
+    char* w = static_cast<char*>(wire);
+    const int vh = h->g.Vh;
+    cudaError_t e;
+    switch (prec) {
+    case LQ_F64: e = launch_face<LQ_F64>(pack, f, w, vh, t, n, sign, scale, st); break;
+    case LQ_F32: e = launch_face<LQ_F32>(pack, f, w, vh, t, n, sign, scale, st); break;
+    case LQ_F16: e = launch_face<LQ_F16>(pack, f, w, vh, t, n, sign, scale, st); break;
+    default: e = launch_face<LQ_BF16>(pack, f, w, vh, t, n, sign, scale, st); break;
+    }
+    return status_of(e);
 }
 
 bool same_space_dims(const lq_handle* a, const lq_handle* b) {
@@ -117,6 +290,20 @@ int lq_face_copy(lq_handle* hd, void* dst, int t_dst, lq_handle* hs, const void*
     default: launch_pdl(face_copy_kernel<LQ_BF16>, grid, 256, 0, st, d, s, vd, vs, e0d, e0s, vh3, flip, scale); break;
     }
     return status_of(cudaGetLastError());
+}
+
+int lq_face_wire_bytes(const lq_handle* h, int fmt, size_t* bytes) {
+    if (!h || !bytes || !valid_fmt(fmt)) return LQ_ERR_ARG;
+    *bytes = wire_bytes(fmt & 0xF, h->p.dims[0] * h->p.dims[1] * h->p.dims[2] / 2);
+    return LQ_OK;
+}
+
+int lq_face_pack(lq_handle* h, void* wire, const void* src, int t_src, int fmt, int sign, double scale, void* stream) {
+    return face_projected(h, true, const_cast<void*>(src), wire, t_src, fmt, sign, scale, stream);
+}
+
+int lq_face_unpack(lq_handle* h, void* dst, int t_dst, const void* wire, int fmt, int sign, void* stream) {
+    return face_projected(h, false, dst, const_cast<void*>(wire), t_dst, fmt, sign, 1.0, stream);
 }
 
 }  // extern "C"

@@ -27,7 +27,7 @@ STATUS = {0: "LQ_OK", -1: "LQ_ERR_ARG", -2: "LQ_ERR_LAYOUT", -3: "LQ_ERR_CUDA", 
 # every function the header declares
 EXPORTS = ["lq_create", "lq_destroy", "lq_field_bytes", "lq_convert", "dslash_apply", "dslash_dag_apply",
            "dwf_dslash_apply", "dwf_schur_apply", "dwf_eo_prepare", "dwf_eo_reconstruct", "lq_dot", "lq_dot_noalloc", "cg_solve", "lq_batch_cg_solve", "dslash_apply_slices",
-           "lq_face_copy", "lq_su3_mul", "lq_wait_timeouts", "lq_test_stalled_wait", "lq_status_string"]
+           "lq_face_copy", "lq_face_wire_bytes", "lq_face_pack", "lq_face_unpack", "lq_su3_mul", "lq_wait_timeouts", "lq_test_stalled_wait", "lq_status_string"]
 LQ_DOT_NOALLOC_MAX_RHS = 32
 
 
@@ -83,6 +83,9 @@ def lib():
                                         ctypes.POINTER(lq_cg_params), ctypes.POINTER(lq_cg_stats), vp]
         L.dslash_apply_slices.argtypes = [vp, vp, vp, i, i, i, i, vp]
         L.lq_face_copy.argtypes = [vp, vp, i, vp, vp, i, i, ctypes.c_double, vp]
+        L.lq_face_wire_bytes.argtypes = [vp, i, ctypes.POINTER(ctypes.c_size_t)]
+        L.lq_face_pack.argtypes = [vp, vp, vp, i, i, i, ctypes.c_double, vp]
+        L.lq_face_unpack.argtypes = [vp, vp, i, vp, i, i, vp]
         L.lq_su3_mul.argtypes = [vp, vp, vp, ctypes.c_long, i, vp]
         L.lq_wait_timeouts.argtypes = [ctypes.POINTER(ctypes.c_uint)]
         L.lq_test_stalled_wait.argtypes = []
@@ -253,3 +256,22 @@ def lq_face_copy(hd, dst, t_dst, hs, src, t_src, fmt, scale=1.0, stream=None):
     """Time slice t_src of src (hs's lattice) times scale into slice t_dst of dst (hd's lattice)."""
     _check(lib().lq_face_copy(hd, _ptr(dst), int(t_dst), hs, _ptr(src), int(t_src), fmt, float(scale),
                               _stream(stream)), "lq_face_copy")
+
+
+def lq_face_wire_bytes(h, fmt):
+    """Bytes of one spin-projected face buffer of h's time slices in format fmt."""
+    n = ctypes.c_size_t(0)
+    _check(lib().lq_face_wire_bytes(h, fmt, ctypes.byref(n)), "lq_face_wire_bytes")
+    return n.value
+
+
+def lq_face_pack(h, wire, src, t_src, fmt, sign, scale=1.0, stream=None):
+    """wire = scale * (psi_up + sign psi_dn) on time slice t_src of the native field src."""
+    _check(lib().lq_face_pack(h, _ptr(wire), _ptr(src), int(t_src), fmt, int(sign), float(scale), _stream(stream)),
+           "lq_face_pack")
+
+
+def lq_face_unpack(h, dst, t_dst, wire, fmt, sign, stream=None):
+    """Time slice t_dst of the native field dst = the ghost spinor rebuilt from wire for projector sign `sign`."""
+    _check(lib().lq_face_unpack(h, _ptr(dst), int(t_dst), _ptr(wire), fmt, int(sign), _stream(stream)),
+           "lq_face_unpack")
