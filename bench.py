@@ -584,8 +584,9 @@ def _time(fn, st, reps, torch):
     return e0.elapsed_time(e1) / reps
 
 
-def mrhs_hops(lqcd, torch, st, hbm, U, reps, variants=((False, 1), (True, 1), (False, 2))):
-    """24^3x48, m = 0.02: the full-lattice hop on 12 point sources in one launch."""
+def mrhs_hops(lqcd, torch, st, hbm, U, reps, variants=((False, 1), (True, 1), (False, 2), (False, 3))):
+    """24^3x48, m = 0.02: the full-lattice hop on 12 point sources in one launch, on the CUDA
+    cores (the default); FP16/BF16 also with the tensor-core kernel."""
     from paper_2001_07557_gb300 import inputs
 
     dims = (24, 24, 24, 48)
@@ -598,15 +599,19 @@ def mrhs_hops(lqcd, torch, st, hbm, U, reps, variants=((False, 1), (True, 1), (F
         nb = lqcd.lq_field_bytes(h, nat, lqcd.LQ_FULL, 12)
         a_, b_ = (torch.empty(nb, dtype=torch.uint8, device="cuda") for _ in range(2))
         lqcd.lq_convert(h, a_, nat, pts, lqcd.LQ_F32, lqcd.LQ_FULL, 12, stream=st)
-        pname = {1: "f32", 2: "f16"}[hp]
+        pname = {1: "f32", 2: "f16", 3: "bf16"}[hp]
         del pts
-        ms = _time(lambda: lqcd.dslash_apply(h, b_, a_, nat, lqcd.LQ_FULL, nrhs=12, stream=st), st, reps, torch)
-        link = 4 * {(1, True): 48, (1, False): 72, (2, False): 36}[(hp, r12)]
-        byts = V * (link + 12 * 2 * {1: 96, 2: 52}[hp])
-        res[f"hop_{pname}_12rhs_r{12 if r12 else 18}"] = {
-            "gflops": FLOP_PER_SITE * V * 12 / (ms * 1e-3) / 1e9, "ms": ms,
-            "model_gbs": byts / (ms * 1e-3) / 1e9, "frac_hbm": byts / (ms * 1e-3) / 1e9 / hbm,
-            "bytes_model": "links once per site (4 x link) + 12 x (in + out)"}
+        link = 4 * {(1, True): 48, (1, False): 72, (2, False): 36, (3, False): 36}[(hp, r12)]
+        byts = V * (link + 12 * 2 * {1: 96, 2: 52, 3: 52}[hp])
+        kinds = [(lqcd.LQ_HOP_CUDA_CORES, "")] + ([(lqcd.LQ_HOP_TENSOR_CORES, "_tensor_cores")] if hp > 1 else [])
+        for kind, suffix in kinds:
+            lqcd.lq_set_hop_kernel(h, kind)
+            ms = _time(lambda: lqcd.dslash_apply(h, b_, a_, nat, lqcd.LQ_FULL, nrhs=12, stream=st), st, reps, torch)
+            res[f"hop_{pname}_12rhs_r{12 if r12 else 18}{suffix}"] = {
+                "gflops": FLOP_PER_SITE * V * 12 / (ms * 1e-3) / 1e9, "ms": ms,
+                "model_gbs": byts / (ms * 1e-3) / 1e9, "frac_hbm": byts / (ms * 1e-3) / 1e9 / hbm,
+                "bytes_model": "links once per site (4 x link) + 12 x (in + out)",
+                "kernel": "tensor cores (mma.sync m16n8k8)" if kind == lqcd.LQ_HOP_TENSOR_CORES else "CUDA cores"}
         lqcd.lq_destroy(h)
         del a_, b_
     return res

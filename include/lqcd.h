@@ -145,6 +145,24 @@ int dslash_apply(lq_handle *h, void *out, const void *in, int fmt, int parity, i
 int dslash_dag_apply(lq_handle *h, void *out, const void *in, int fmt, int parity, int nrhs, void *stream);
 
 /*
+ * lq_set_hop_kernel: which kernel computes the Wilson hops of this handle.
+ * The paper's kernels are CUDA-core code (Sec. 3.3); the tensor-core variant
+ * is this library's own.  LQ_HOP_CUDA_CORES (the default): the CUDA-core hop.
+ * LQ_HOP_TENSOR_CORES: a launch of at least 8 right-hand sides with FP16/BF16
+ * storage and 18-real links, over whole parity blocks and with a Wilson
+ * epilogue, runs its SU(3) x half-spinor products on the tensor cores (one
+ * 16x8x8 MMA with FP32 accumulation per site, direction and group of 8
+ * right-hand sides); every other launch keeps the CUDA-core hop.  The two
+ * agree to the rounding of FP32 sums.  On GB300 the tensor-core variant is
+ * the slower of the two (24^3 x 48, 12 right-hand sides, FP16: 1.1 ms against
+ * 0.42 ms), so it is not the default.  Takes effect for launches made after
+ * the call (a solver captures it when it starts); other kind values are
+ * LQ_ERR_ARG.
+ */
+enum { LQ_HOP_CUDA_CORES = 0, LQ_HOP_TENSOR_CORES = 1 };
+int lq_set_hop_kernel(lq_handle *h, int kind);
+
+/*
  * dwf_dslash_apply: domain-wall operator D_dw (dagger != 0: D_dw^dag) on one
  * 5-d field of Ls slices (lq_params.Ls), layout by fmt as above: Shamir, or
  * Moebius when lq_params.mobius = 1 (then FP64/FP32 only, LQ_ERR_ARG else).

@@ -109,6 +109,7 @@ static HopArgs base_args(lq_handle* h, const char* links, size_t lb) {
     a.g = h->g;
     a.skip = h->skip;
     a.skip_stride = h->skip_stride;
+    a.mma = h->hop_kernel == LQ_HOP_TENSOR_CORES ? 1 : 0;
     return a;
 }
 
@@ -596,6 +597,7 @@ int lq_create(lq_handle** hp, const lq_params* p, const void* U, int U_prec, voi
     h->g.mL1 = div_magic(p->dims[1]);
     h->g.mL2 = div_magic(p->dims[2]);
     for (int k = 0; k < 4; ++k) h->hop_block[k] = kHopThreads;
+    h->hop_kernel = LQ_HOP_CUDA_CORES;
     if (cudaGetDevice(&h->device) != cudaSuccess) {
         delete h;
         return LQ_ERR_CUDA;
@@ -873,6 +875,12 @@ int lq_dot(lq_handle* h, double* result, const void* a, const void* b, int fmt, 
     unsigned* tickets = reinterpret_cast<unsigned*>(partial + 2 * kMaxGrid * (size_t)nrhs);
     if (cudaMemsetAsync(tickets, 0, sizeof(unsigned) * nrhs, st) != cudaSuccess) return LQ_ERR_CUDA;
     return status_of(launch_cdot(fmt, a, b, site_bytes * nsites, nsites, h->g.Vh, nrhs, partial, tickets, result, st));
+}
+
+int lq_set_hop_kernel(lq_handle* h, int kind) {
+    if (!h || (kind != LQ_HOP_CUDA_CORES && kind != LQ_HOP_TENSOR_CORES)) return LQ_ERR_ARG;
+    h->hop_kernel = kind;
+    return LQ_OK;
 }
 
 const char* lq_status_string(int status) {

@@ -22,6 +22,7 @@ struct lq_handle {
         size_t bytes;
     } ws[26];         // workspace buffers, grown on demand
     int hop_block[4]; // threads per block of the hop kernels, per precision
+    int hop_kernel;   // LQ_HOP_CUDA_CORES (default) or LQ_HOP_TENSOR_CORES (lq_set_hop_kernel)
     const int* skip;  // per-rhs early-exit flags the solvers hand to the hop launches (else null)
     int skip_stride;
     // fused |K p|^2 for the next operator output (the K of K^dag K), else null

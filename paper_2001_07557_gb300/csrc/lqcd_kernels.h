@@ -33,6 +33,9 @@ struct HopArgs {
     // domain-wall epilogue: coefficient of (S x)(s) = P+ x(s_up) + P- x(s_dn), walls
     // -mf (the Shamir operator's site-local part takes -1; set at every EPI_DWF launch)
     double c_shift;
+    // 1: a launch of at least 8 right-hand sides in FP16/BF16 with 18-real links runs
+    // its SU(3) products on the tensor cores (hop_mma.cuh); 0: CUDA cores only
+    int mma;
     const int* skip;  // optional per-rhs flags (skip[rhs * skip_stride]): a set flag ends the block at once
     int skip_stride;
     // optional fused |out|^2 per right-hand side (one group for the domain wall):

@@ -26,7 +26,7 @@ STATUS = {0: "LQ_OK", -1: "LQ_ERR_ARG", -2: "LQ_ERR_LAYOUT", -3: "LQ_ERR_CUDA", 
 
 # every function the header declares
 EXPORTS = ["lq_create", "lq_destroy", "lq_field_bytes", "lq_convert", "dslash_apply", "dslash_dag_apply",
-           "dwf_dslash_apply", "dwf_schur_apply", "dwf_eo_prepare", "dwf_eo_reconstruct", "lq_dot", "lq_dot_noalloc", "cg_solve", "lq_batch_cg_solve", "dslash_apply_slices",
+           "lq_set_hop_kernel", "dwf_dslash_apply", "dwf_schur_apply", "dwf_eo_prepare", "dwf_eo_reconstruct", "lq_dot", "lq_dot_noalloc", "cg_solve", "lq_batch_cg_solve", "dslash_apply_slices",
            "lq_face_copy", "lq_face_wire_bytes", "lq_face_pack", "lq_face_unpack", "lq_su3_mul", "lq_wait_timeouts", "lq_test_stalled_wait", "lq_status_string"]
 LQ_DOT_NOALLOC_MAX_RHS = 32
 
@@ -83,6 +83,7 @@ def lib():
                                         ctypes.POINTER(lq_cg_params), ctypes.POINTER(lq_cg_stats), vp]
         L.dslash_apply_slices.argtypes = [vp, vp, vp, i, i, i, i, vp]
         L.lq_face_copy.argtypes = [vp, vp, i, vp, vp, i, i, ctypes.c_double, vp]
+        L.lq_set_hop_kernel.argtypes = [vp, i]
         L.lq_face_wire_bytes.argtypes = [vp, i, ctypes.POINTER(ctypes.c_size_t)]
         L.lq_face_pack.argtypes = [vp, vp, vp, i, i, i, ctypes.c_double, vp]
         L.lq_face_unpack.argtypes = [vp, vp, i, vp, i, i, vp]
@@ -256,6 +257,15 @@ def lq_face_copy(hd, dst, t_dst, hs, src, t_src, fmt, scale=1.0, stream=None):
     """Time slice t_src of src (hs's lattice) times scale into slice t_dst of dst (hd's lattice)."""
     _check(lib().lq_face_copy(hd, _ptr(dst), int(t_dst), hs, _ptr(src), int(t_src), fmt, float(scale),
                               _stream(stream)), "lq_face_copy")
+
+
+LQ_HOP_CUDA_CORES, LQ_HOP_TENSOR_CORES = 0, 1
+
+
+def lq_set_hop_kernel(h, kind):
+    """LQ_HOP_CUDA_CORES (default), or LQ_HOP_TENSOR_CORES: the tensor-core hop for launches of
+    >= 8 FP16/BF16 right-hand sides with 18-real links."""
+    _check(lib().lq_set_hop_kernel(h, int(kind)), "lq_set_hop_kernel")
 
 
 def lq_face_wire_bytes(h, fmt):
