@@ -239,6 +239,23 @@ int lq_dot(lq_handle *h, double *result, const void *a, const void *b, int fmt, 
 int lq_dot_noalloc(lq_handle *h, double *result, const void *a, const void *b, int fmt, int subset, int nrhs,
                    int five_d, void *stream);
 
+/*
+ * lq_index_faults: the record of the index-checked build.  A library built with
+ * -DLQ_INDEX_CHECK (paper_2001_07557_gb300/build.py, build(checked=True), which
+ * writes liblqcd_checked.so) compares every neighbour index its hop kernels
+ * compute with the parity block before using it; an index out of range is
+ * counted, the first one kept, and the access redirected to site 0, so the
+ * check cannot fault.  The paper has no counterpart: this is a testing aid that
+ * stands in for a device memory checker.
+ *   count    receives the indices out of range since the previous call, on the
+ *            current device (the call clears the record; it synchronises the device)
+ *   first    (may be null) the first such index, -1 if none
+ *   checked  (may be null) 1 for the index-checked build, 0 for the normal one,
+ *            whose count is always 0
+ * Returns LQ_ERR_ARG for a null count, LQ_ERR_CUDA if the record cannot be read.
+ */
+int lq_index_faults(unsigned long long *count, long long *first, int *checked);
+
 /* ------------------------------------------------------------------- CG */
 
 enum {

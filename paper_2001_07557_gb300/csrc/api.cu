@@ -7,6 +7,7 @@
 
 #include "blas.h"
 #include "handle.h"
+#include "trace.h"
 
 namespace lq {
 
@@ -569,6 +570,7 @@ int wilson_apply(lq_handle* h, void* out, const void* in, int fmt, int parity, i
 extern "C" {
 
 int lq_create(lq_handle** hp, const lq_params* p, const void* U, int U_prec, void* stream) {
+    lq::TraceRange trace_("lqcd/create");
     if (!hp || !p || !U) return LQ_ERR_ARG;
     *hp = nullptr;
     if (U_prec != LQ_F64 && U_prec != LQ_F32) return LQ_ERR_ARG;
@@ -669,6 +671,7 @@ static bool device_accessible(const void* p) {
 
 int lq_convert(lq_handle* h, void* dst, int dst_fmt, const void* src, int src_fmt, int subset, int nrhs, int five_d,
                void* stream) {
+    lq::TraceRange trace_("lqcd/convert");
     if (!h || !dst || !src || !valid_fmt(dst_fmt) || !valid_fmt(src_fmt)) return LQ_ERR_ARG;
     if (subset < LQ_FULL || subset > LQ_ODD) return LQ_ERR_ARG;
     if (!aligned16(dst) || !aligned16(src)) return LQ_ERR_LAYOUT;
@@ -709,14 +712,17 @@ int lq_convert(lq_handle* h, void* dst, int dst_fmt, const void* src, int src_fm
 }
 
 int dslash_apply(lq_handle* h, void* out, const void* in, int fmt, int parity, int nrhs, void* stream) {
+    lq::TraceRange trace_("lqcd/dslash");
     return wilson_apply(h, out, in, fmt, parity, nrhs, static_cast<cudaStream_t>(stream), false);
 }
 
 int dslash_dag_apply(lq_handle* h, void* out, const void* in, int fmt, int parity, int nrhs, void* stream) {
+    lq::TraceRange trace_("lqcd/dslash_dag");
     return wilson_apply(h, out, in, fmt, parity, nrhs, static_cast<cudaStream_t>(stream), true);
 }
 
 int dwf_dslash_apply(lq_handle* h, void* out, const void* in, int fmt, int dagger, void* stream) {
+    lq::TraceRange trace_("lqcd/dwf_dslash");
     if (!h || !out || !in || !valid_fmt(fmt)) return LQ_ERR_ARG;
     if (h->p.Ls < 1) return LQ_ERR_ARG;
     if (!aligned16(out) || !aligned16(in)) return LQ_ERR_LAYOUT;
@@ -756,6 +762,7 @@ static int dwf_eo_args(lq_handle* h, int fmt) {
 }
 
 int dwf_schur_apply(lq_handle* h, void* out, const void* in, int fmt, int dagger, void* stream) {
+    lq::TraceRange trace_("lqcd/dwf_schur");
     int rc = dwf_eo_args(h, fmt);
     if (rc) return rc;
     if (!out || !in) return LQ_ERR_ARG;
@@ -786,6 +793,7 @@ int dwf_schur_apply(lq_handle* h, void* out, const void* in, int fmt, int dagger
 }
 
 int dwf_eo_prepare(lq_handle* h, void* bhat_e, const void* eta, int fmt, void* stream) {
+    lq::TraceRange trace_("lqcd/dwf_eo_prepare");
     int rc = dwf_eo_args(h, fmt);
     if (rc) return rc;
     if (!bhat_e || !eta) return LQ_ERR_ARG;
@@ -815,6 +823,7 @@ int dwf_eo_prepare(lq_handle* h, void* bhat_e, const void* eta, int fmt, void* s
 }
 
 int dwf_eo_reconstruct(lq_handle* h, void* psi, const void* x_e, const void* eta, int fmt, void* stream) {
+    lq::TraceRange trace_("lqcd/dwf_eo_reconstruct");
     int rc = dwf_eo_args(h, fmt);
     if (rc) return rc;
     if (!psi || !x_e || !eta) return LQ_ERR_ARG;
@@ -849,6 +858,7 @@ int dwf_eo_reconstruct(lq_handle* h, void* psi, const void* x_e, const void* eta
 
 int lq_dot(lq_handle* h, double* result, const void* a, const void* b, int fmt, int subset, int nrhs, int five_d,
            void* stream) {
+    lq::TraceRange trace_("lqcd/dot");
     if (!h || !result || !a || !b || !valid_fmt(fmt)) return LQ_ERR_ARG;
     if (subset < LQ_FULL || subset > LQ_ODD) return LQ_ERR_ARG;
     if (!aligned16(a) || !aligned16(b) || (reinterpret_cast<uintptr_t>(result) & 7u)) return LQ_ERR_LAYOUT;
@@ -875,6 +885,27 @@ int lq_dot(lq_handle* h, double* result, const void* a, const void* b, int fmt, 
     unsigned* tickets = reinterpret_cast<unsigned*>(partial + 2 * kMaxGrid * (size_t)nrhs);
     if (cudaMemsetAsync(tickets, 0, sizeof(unsigned) * nrhs, st) != cudaSuccess) return LQ_ERR_CUDA;
     return status_of(launch_cdot(fmt, a, b, site_bytes * nsites, nsites, h->g.Vh, nrhs, partial, tickets, result, st));
+}
+
+int lq_index_faults(unsigned long long* count, long long* first, int* checked) {
+    if (!count) return LQ_ERR_ARG;
+#ifdef LQ_INDEX_CHECK
+    const int on = 1;
+#else
+    const int on = 0;
+#endif
+    if (checked) *checked = on;
+    if (first) *first = -1;
+    unsigned long long total = 0;
+    for (auto rd : {index_faults_f64, index_faults_f32, index_faults_f16, index_faults_bf16}) {
+        long long f = -1;
+        const unsigned long long c = rd(&f);
+        if (c == ~0ull) return LQ_ERR_CUDA;
+        if (c && first && *first < 0) *first = f;
+        total += c;
+    }
+    *count = total;
+    return LQ_OK;
 }
 
 int lq_set_hop_kernel(lq_handle* h, int kind) {

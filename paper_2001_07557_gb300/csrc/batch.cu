@@ -28,6 +28,7 @@
 
 #include "blas.h"
 #include "handle.h"
+#include "trace.h"
 
 namespace lq {
 
@@ -137,6 +138,7 @@ using namespace lq;
 
 extern "C" int lq_batch_cg_solve(lq_handle** hs, int nlat, void** xs, const void** bs, const lq_cg_params* cp,
                                  lq_cg_stats* stats, void* stream) {
+    lq::TraceRange trace_("lqcd/batch_cg_solve");
     if (!hs || !xs || !bs || !cp || !stats || nlat < 1 || nlat > 64) return LQ_ERR_ARG;
     if (cp->op != LQ_OP_WILSON_NORMAL && cp->op != LQ_OP_WILSON_EO_NORMAL) return LQ_ERR_ARG;
     if (cp->nrhs < 1 || cp->nrhs > 64 || cp->maxiter < 1 || !(cp->tol > 0) || !valid_fmt(cp->fmt)) return LQ_ERR_ARG;

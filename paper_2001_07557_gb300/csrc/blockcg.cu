@@ -27,6 +27,7 @@
 #include "blas.h"
 #include "blockcg.h"
 #include "pdl.cuh"
+#include "trace.h"
 
 namespace lq {
 
@@ -389,6 +390,7 @@ bool chol_solve(const std::vector<cd>& H, const std::vector<cd>& Y, std::vector<
 
 int block_cg(const BlockCgOps& ops, char* X, const char* Bv, char* R, char* P, char* Q, size_t stride, long nsites,
              int N, double tol, int maxiter, void* ws, double2* hostbuf, cudaStream_t s, int* iters) {
+    lq::TraceRange trace_("lqcd/cg/block");
     if (N < 1 || N > kMaxBlockRhs || stride % 16 != 0) return LQ_ERR_ARG;
     const long M = nsites * (spinor_site_bytes(LQ_F32) / 16);  // float4 per column
     const size_t stride4 = stride / 16;

@@ -22,6 +22,7 @@
 #include "blas.h"
 #include "blockcg.h"
 #include "handle.h"
+#include "trace.h"
 
 namespace lq {
 
@@ -178,6 +179,7 @@ int cg_vectors(lq_handle* h, const OpGeom& og, int px, int pp, int slot0, CgVecs
 // On return c.host holds the final scalars of every rhs.
 int run_cg(lq_handle* h, const OpGeom& og, const Ctl& c, int pp, const VecRef& e, const VecRef& rhs, double tol,
            int maxiter, int slot0, cudaStream_t s) {
+    lq::TraceRange trace_("lqcd/cg/inner");
     const int px = e.prec;
     // with FP16/BF16 search directions the residual is kept in the same 16-bit storage
     // (FP32 arithmetic, per-site norms): the update and xpay then move 19% fewer bytes
@@ -252,6 +254,7 @@ int run_cg(lq_handle* h, const OpGeom& og, const Ctl& c, int pp, const VecRef& e
 // |b - A x| / |b| per rhs in FP64 (x64, b64 native FP64)
 int true_residual(lq_handle* h, const OpGeom& og, const Ctl& c, const VecRef& x64, const VecRef& b64, int slot0,
                   double* rel, cudaStream_t s) {
+    lq::TraceRange trace_("lqcd/cg/true_residual");
     CgVecs v;
     int rc = cg_vectors(h, og, LQ_F64, LQ_F64, slot0, &v);
     if (rc) return rc;
@@ -287,6 +290,7 @@ constexpr double kMiddleTol = 1e-5;
 // with FP32 hops.  iters[k] accumulates operator applications.
 int solve_fp32_middle(lq_handle* h, const OpGeom& og, const Ctl& c, int ip, const VecRef& e, const VecRef& rhs,
                       double target, double itol, int maxiter, cudaStream_t s, int* iters, int* most_out) {
+    lq::TraceRange trace_("lqcd/cg/fp32_middle");
     const int Vh = h->g.Vh, nr = og.nrhs;
     void *rp, *dp, *qp, *tp, *tmpp;
     int rc;
@@ -350,6 +354,7 @@ using namespace lq;
 
 extern "C" int cg_solve(lq_handle* h, void* x, const void* b, const lq_cg_params* cp, lq_cg_stats* stats,
                         void* stream) {
+    lq::TraceRange trace_("lqcd/cg_solve");
     if (!h || !x || !b || !cp || !stats) return LQ_ERR_ARG;
     if (!valid_fmt(cp->fmt) || cp->nrhs < 1 || cp->maxiter < 1 || !(cp->tol > 0)) return LQ_ERR_ARG;
     if (!aligned16(x) || !aligned16(b)) return LQ_ERR_LAYOUT;

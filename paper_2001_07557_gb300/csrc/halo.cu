@@ -24,6 +24,7 @@
 
 #include "handle.h"
 #include "pdl.cuh"
+#include "trace.h"
 
 namespace lq {
 
@@ -245,6 +246,7 @@ using namespace lq;
 extern "C" {
 
 int dslash_apply_slices(lq_handle* h, void* out, const void* in, int fmt, int t0, int t1, int dagger, void* stream) {
+    lq::TraceRange trace_("lqcd/dslash_slices");
     if (!h || !out || !in || !valid_fmt(fmt)) return LQ_ERR_ARG;
     if (!(fmt & LQ_NATIVE)) return LQ_ERR_LAYOUT;
     if (t0 < 0 || t1 > h->p.dims[3] || t0 >= t1) return LQ_ERR_ARG;
@@ -267,6 +269,7 @@ int dslash_apply_slices(lq_handle* h, void* out, const void* in, int fmt, int t0
 
 int lq_face_copy(lq_handle* hd, void* dst, int t_dst, lq_handle* hs, const void* src, int t_src, int fmt,
                  double scale, void* stream) {
+    lq::TraceRange trace_("lqcd/face_copy");
     if (!hd || !hs || !dst || !src || !valid_fmt(fmt)) return LQ_ERR_ARG;
     if (!(fmt & LQ_NATIVE)) return LQ_ERR_LAYOUT;
     if (!same_space_dims(hd, hs)) return LQ_ERR_ARG;
@@ -299,10 +302,12 @@ int lq_face_wire_bytes(const lq_handle* h, int fmt, size_t* bytes) {
 }
 
 int lq_face_pack(lq_handle* h, void* wire, const void* src, int t_src, int fmt, int sign, double scale, void* stream) {
+    lq::TraceRange trace_("lqcd/face_pack");
     return face_projected(h, true, const_cast<void*>(src), wire, t_src, fmt, sign, scale, stream);
 }
 
 int lq_face_unpack(lq_handle* h, void* dst, int t_dst, const void* wire, int fmt, int sign, void* stream) {
+    lq::TraceRange trace_("lqcd/face_unpack");
     return face_projected(h, false, dst, const_cast<void*>(wire), t_dst, fmt, sign, 1.0, stream);
 }
 

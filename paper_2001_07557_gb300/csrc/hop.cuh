@@ -66,6 +66,8 @@ __global__ void __launch_bounds__(128) wilson_hop_kernel(const HopArgs a) {
         for (int mu = 0; mu < 4; ++mu) {
             sf[mu] = sf[mu] && (g.bc[mu] < 0);
             sb[mu] = sb[mu] && (g.bc[mu] < 0);
+            nf[mu] = check_site(nf[mu], g.Vh);
+            nb[mu] = check_site(nb[mu], g.Vh);
         }
     }
 

@@ -261,6 +261,8 @@ __device__ __forceinline__ void hop_async_site(const HopArgs& a, int i, int rhs,
         for (int mu = 0; mu < 4; ++mu) {
             sf[mu] = sf[mu] && (g.bc[mu] < 0);
             sb[mu] = sb[mu] && (g.bc[mu] < 0);
+            nf[mu] = check_site(nf[mu], g.Vh);
+            nb[mu] = check_site(nb[mu], g.Vh);
         }
     }
     const char* __restrict__ Lp = a.links + (size_t)(p * 4) * a.link_block;

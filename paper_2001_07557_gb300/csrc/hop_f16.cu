@@ -6,6 +6,7 @@
 #include "hop_mma.cuh"
 
 namespace lq {
+LQ_INDEX_FAULTS_READER(index_faults_f16)
 cudaError_t launch_hop_f16(const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st) {
     (void)block;
     if (hop_mma_applies(a, r12, epi)) return launch_hop_mma<LQ_F16>(a, dag, epi, st);

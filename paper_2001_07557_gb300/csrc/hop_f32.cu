@@ -3,6 +3,7 @@
 #include "hop_async.cuh"
 
 namespace lq {
+LQ_INDEX_FAULTS_READER(index_faults_f32)
 cudaError_t launch_hop_f32(const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st) {
     (void)block;
     return launch_hop_async<LQ_F32>(a, r12, dag, epi, st);

@@ -180,8 +180,8 @@ __global__ void __launch_bounds__(mma::kThreads, MINB) wilson_hop_mma_kernel(con
         }
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) {
-            nbr[lane * 8 + 2 * mu] = nf[mu];
-            nbr[lane * 8 + 2 * mu + 1] = nb[mu];
+            nbr[lane * 8 + 2 * mu] = check_site(nf[mu], Vh);
+            nbr[lane * 8 + 2 * mu + 1] = check_site(nb[mu], Vh);
         }
         sgn[lane] = bits;
     }

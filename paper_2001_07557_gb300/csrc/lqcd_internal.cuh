@@ -66,6 +66,42 @@ struct CgScalars {
     int status;    // LQ_OK / LQ_ERR_BREAKDOWN / LQ_ERR_NOT_CONVERGED / LQ_ERR_NAN
 };
 
+// ------------------------------------------------------ index-checked build
+// Built with -DLQ_INDEX_CHECK (build.build(checked=True)), the hop kernels
+// compare every neighbour and site index they compute with the parity block
+// before using it.  An index out of range is counted in the translation unit's
+// counter (the first one kept) and replaced by 0, so that the check itself
+// cannot fault; lq_index_faults reads and clears the counters.  The normal
+// build compiles the check away.  (It stands in for a memory checker, which
+// this build does not run on the GPU.)
+#ifdef LQ_INDEX_CHECK
+static __device__ unsigned long long lq_index_fault_count;
+static __device__ long long lq_index_fault_first;
+__device__ __forceinline__ int check_site(int i, int n) {
+    if ((unsigned)i < (unsigned)n) return i;
+    if (atomicAdd(&lq_index_fault_count, 1ull) == 0ull) lq_index_fault_first = i;
+    return 0;
+}
+// host reader of this translation unit's counter: returns the count (~0 on a CUDA
+// error), sets *first to the first bad index when the count is not zero, clears it
+#define LQ_INDEX_FAULTS_READER(name)                                                          \
+    unsigned long long name(long long* first) {                                               \
+        unsigned long long c = 0;                                                             \
+        long long f = -1;                                                                     \
+        const unsigned long long z = 0;                                                       \
+        if (cudaMemcpyFromSymbol(&c, lq_index_fault_count, sizeof(c)) != cudaSuccess ||       \
+            cudaMemcpyFromSymbol(&f, lq_index_fault_first, sizeof(f)) != cudaSuccess ||       \
+            cudaMemcpyToSymbol(lq_index_fault_count, &z, sizeof(z)) != cudaSuccess)           \
+            return ~0ull;                                                                     \
+        if (first && c) *first = f;                                                           \
+        return c;                                                                             \
+    }
+#else
+__device__ __forceinline__ int check_site(int i, int) { return i; }
+#define LQ_INDEX_FAULTS_READER(name) \
+    unsigned long long name(long long*) { return 0; }
+#endif
+
 // ------------------------------------------------------------------ complex
 
 template <typename T>

@@ -81,6 +81,12 @@ cudaError_t launch_m5inv_general(int prec, void* out, const void* in, int Vh, si
 // not overlap u or v.  (dwf_eo.cu)
 cudaError_t launch_m5_lincomb(int prec, void* out, const void* u, const void* v, int Vh, int nblk, size_t slice_stride,
                               int Ls, double a, double b, double c, double d, double mf, bool dag, cudaStream_t st);
+// index-checked build: out-of-range indices counted by the hop translation units
+// since the last read (cleared by the read); ~0 on a CUDA error
+unsigned long long index_faults_f64(long long* first);
+unsigned long long index_faults_f32(long long* first);
+unsigned long long index_faults_f16(long long* first);
+unsigned long long index_faults_bf16(long long* first);
 cudaError_t launch_hop_f64(const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st);
 cudaError_t launch_hop_f32(const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st);
 cudaError_t launch_hop_f16(const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st);

@@ -22,6 +22,7 @@
 #include <cstdint>
 
 #include "lqcd.h"
+#include "trace.h"
 
 namespace lq {
 
@@ -226,6 +227,7 @@ bool overlaps(const void* p, const void* q, size_t bytes) {
 extern "C" {
 
 int lq_su3_mul(void* C, const void* A, const void* B, long n, int fmt, void* stream) {
+    lq::TraceRange trace_("lqcd/su3_mul");
     if (n < 0 || (fmt != LQ_F64 && fmt != LQ_F32)) return LQ_ERR_ARG;
     if (n == 0) return LQ_OK;
     if (!A || !B || !C) return LQ_ERR_ARG;

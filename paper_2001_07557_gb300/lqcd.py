@@ -13,7 +13,9 @@ import ctypes
 import os
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "liblqcd.so")
+# LQCD_LIBRARY names another build of the same library (the index-checked
+# liblqcd_checked.so of build.build(checked=True)); by default the in-tree build
+LIB_PATH = os.environ.get("LQCD_LIBRARY") or os.path.join(_PKG, "liblqcd.so")
 
 LQ_OK = 0
 LQ_F64, LQ_F32, LQ_F16, LQ_BF16 = 0, 1, 2, 3
@@ -27,7 +29,7 @@ STATUS = {0: "LQ_OK", -1: "LQ_ERR_ARG", -2: "LQ_ERR_LAYOUT", -3: "LQ_ERR_CUDA", 
 # every function the header declares
 EXPORTS = ["lq_create", "lq_destroy", "lq_field_bytes", "lq_convert", "dslash_apply", "dslash_dag_apply",
            "lq_set_hop_kernel", "dwf_dslash_apply", "dwf_schur_apply", "dwf_eo_prepare", "dwf_eo_reconstruct", "lq_dot", "lq_dot_noalloc", "cg_solve", "lq_batch_cg_solve", "dslash_apply_slices",
-           "lq_face_copy", "lq_face_wire_bytes", "lq_face_pack", "lq_face_unpack", "lq_su3_mul", "lq_wait_timeouts", "lq_test_stalled_wait", "lq_status_string"]
+           "lq_face_copy", "lq_face_wire_bytes", "lq_face_pack", "lq_face_unpack", "lq_su3_mul", "lq_wait_timeouts", "lq_test_stalled_wait", "lq_index_faults", "lq_status_string"]
 LQ_DOT_NOALLOC_MAX_RHS = 32
 
 
@@ -84,6 +86,8 @@ def lib():
         L.dslash_apply_slices.argtypes = [vp, vp, vp, i, i, i, i, vp]
         L.lq_face_copy.argtypes = [vp, vp, i, vp, vp, i, i, ctypes.c_double, vp]
         L.lq_set_hop_kernel.argtypes = [vp, i]
+        L.lq_index_faults.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_longlong),
+                                      ctypes.POINTER(i)]
         L.lq_face_wire_bytes.argtypes = [vp, i, ctypes.POINTER(ctypes.c_size_t)]
         L.lq_face_pack.argtypes = [vp, vp, vp, i, i, i, ctypes.c_double, vp]
         L.lq_face_unpack.argtypes = [vp, vp, i, vp, i, i, vp]
@@ -266,6 +270,13 @@ def lq_set_hop_kernel(h, kind):
     """LQ_HOP_CUDA_CORES (default), or LQ_HOP_TENSOR_CORES: the tensor-core hop for launches of
     >= 8 FP16/BF16 right-hand sides with 18-real links."""
     _check(lib().lq_set_hop_kernel(h, int(kind)), "lq_set_hop_kernel")
+
+
+def lq_index_faults():
+    """(count, first, checked): out-of-range hop indices since the last call (index-checked build)."""
+    c, f, k = ctypes.c_ulonglong(0), ctypes.c_longlong(-1), ctypes.c_int(0)
+    _check(lib().lq_index_faults(ctypes.byref(c), ctypes.byref(f), ctypes.byref(k)), "lq_index_faults")
+    return c.value, f.value, k.value
 
 
 def lq_face_wire_bytes(h, fmt):
