@@ -201,10 +201,22 @@ __device__ __forceinline__ void smem_words_link(const unsigned char* stage, int 
     w[8] = *reinterpret_cast<const uint32_t*>(stage + St::LKT_OFF + t * 4);
 }
 
+// Whether the diagonal input rides with direction 0 through shared memory.  The
+// FP16/BF16 hop reads it from global memory in the epilogue instead: a staged
+// copy costs it a block of residency per SM (5 instead of 6), and on 32^4 its
+// Schur step is 3% faster without (36.6 -> 35.4 us per hop); FP32 (2 stages,
+// not limited by shared memory) is faster staged, most on L2-resident lattices
+// (16^3 x 32: 8.7 against 9.6 us).  The domain-wall epilogue stages its three
+// spinor inputs.
+template <int P, int EPI>
+__host__ __device__ constexpr bool stage_x() {
+    return EPI == EPI_DWF || (EPI == EPI_DIAG && !Prec<P>::has_norm);
+}
+
 template <int P, bool R12, int NT, int EPI>
 constexpr int async_smem_bytes(int S) {
     using St = AsyncStage<P, R12, NT>;
-    return S * St::BYTES + (EPI >= EPI_DIAG ? St::SPIN_BYTES : 0) + (EPI == EPI_DWF ? 2 * St::HALF_BYTES : 0);
+    return S * St::BYTES + (stage_x<P, EPI>() ? St::SPIN_BYTES : 0) + (EPI == EPI_DWF ? 2 * St::HALF_BYTES : 0);
 }
 
 // launch configuration per storage precision: threads per block, stages.
@@ -281,7 +293,7 @@ __device__ __forceinline__ void hop_async_site(const HopArgs& a, int i, int rhs,
     issue(0);
     int s_up = 0, s_dn = 0;
     T c_up = 0, c_dn = 0;
-    if constexpr (EPI >= EPI_DIAG) {
+    if constexpr (stage_x<P, EPI>()) {
         async_spinor<P, R12, NT>(extra, a.x[p] + (size_t)rhs * a.x_rhs, g.Vh, i, t);
     }
     if constexpr (EPI == EPI_DWF) {
@@ -366,7 +378,8 @@ __device__ __forceinline__ void hop_async_site(const HopArgs& a, int i, int rhs,
     if constexpr (EPI >= EPI_DIAG) {
         cplx<T> xs[12];
         T nx;
-        smem_spinor<P, R12, NT>(extra, t, xs, nx);
+        if constexpr (stage_x<P, EPI>()) smem_spinor<P, R12, NT>(extra, t, xs, nx);
+        else load_spinor_raw<P, T>(a.x[p] + (size_t)rhs * a.x_rhs, g.Vh, i, xs, nx);
         const T cd = (T)a.c_diag * nx;
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
