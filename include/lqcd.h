@@ -155,7 +155,7 @@ int dslash_dag_apply(lq_handle *h, void *out, const void *in, int fmt, int parit
  * right-hand sides); every other launch keeps the CUDA-core hop.  The two
  * agree to the rounding of FP32 sums.  On GB300 the tensor-core variant is
  * the slower of the two (24^3 x 48, 12 right-hand sides, FP16: 1.1 ms against
- * 0.42 ms), so it is not the default.  Takes effect for launches made after
+ * 0.40 ms), so it is not the default.  Takes effect for launches made after
  * the call (a solver captures it when it starts); other kind values are
  * LQ_ERR_ARG.
  */
