@@ -119,6 +119,37 @@ __device__ __forceinline__ void smem_half_spinor(const unsigned char* slot, int 
     }
 }
 
+// the upper (spins 0,1) or lower (spins 2,3) half of a spinor straight from its
+// native block, in the order of smem_half_spinor (unscaled values + norm)
+template <int P, bool UPPER>
+__device__ __forceinline__ void load_half_spinor_raw(const char* __restrict__ blk, int Vh, int i, cplx<float> (&s)[6],
+                                                     float& nrm) {
+    if constexpr (P == LQ_F32) {
+        const float4* q = reinterpret_cast<const float4*>(blk);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float4 v = __ldg(q + (size_t)(UPPER ? k : 3 + k) * Vh + i);
+            s[2 * k] = {v.x, v.y};
+            s[2 * k + 1] = {v.z, v.w};
+        }
+        nrm = 1.f;
+    } else {
+        std::integral_constant<int, P> tag;
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(blk) + (size_t)(UPPER ? 0 : 2) * Vh + i);
+        const uint2 w = __ldg(reinterpret_cast<const uint2*>(blk + ((size_t)Vh + i) * 16) + (UPPER ? 0 : 1));
+        const float2 q0 = h2f(v.x, tag), q1 = h2f(v.y, tag), q2 = h2f(v.z, tag), q3 = h2f(v.w, tag);
+        const float2 r0 = h2f(w.x, tag), r1 = h2f(w.y, tag);
+        const int a = UPPER ? 0 : 2, b = UPPER ? 4 : 0;  // where the 16-byte and the 8-byte parts go
+        s[a + 0] = {q0.x, q0.y};
+        s[a + 1] = {q1.x, q1.y};
+        s[a + 2] = {q2.x, q2.y};
+        s[a + 3] = {q3.x, q3.y};
+        s[b + 0] = {r0.x, r0.y};
+        s[b + 1] = {r1.x, r1.y};
+        nrm = __ldg(reinterpret_cast<const float*>(blk + (size_t)48 * Vh) + i);
+    }
+}
+
 // read one staged spinor back (unscaled values + norm)
 template <int P, bool R12, int NT>
 __device__ __forceinline__ void smem_spinor(const unsigned char* slot, int t, cplx<float> (&s)[12], float& nrm) {
@@ -210,13 +241,13 @@ __device__ __forceinline__ void smem_words_link(const unsigned char* stage, int 
 // spinor inputs.
 template <int P, int EPI>
 __host__ __device__ constexpr bool stage_x() {
-    return EPI == EPI_DWF || (EPI == EPI_DIAG && !Prec<P>::has_norm);
+    return EPI == EPI_DIAG && !Prec<P>::has_norm;
 }
 
 template <int P, bool R12, int NT, int EPI>
 constexpr int async_smem_bytes(int S) {
     using St = AsyncStage<P, R12, NT>;
-    return S * St::BYTES + (stage_x<P, EPI>() ? St::SPIN_BYTES : 0) + (EPI == EPI_DWF ? 2 * St::HALF_BYTES : 0);
+    return S * St::BYTES + (stage_x<P, EPI>() ? St::SPIN_BYTES : 0);
 }
 
 // launch configuration per storage precision: threads per block, stages.
@@ -229,12 +260,14 @@ struct AsyncCfg {
     static constexpr int S = (P == LQ_F32) ? 2 : 3;
 };
 
-// stages of the domain-wall variant: its three extra spinor slots cost shared
-// memory, and two stages keep more blocks resident per SM (measured on
-// 16^4 x 16: FP32 112 -> 98 us, FP16 72 -> 60 us against 3 and 4 stages)
+// stages of every variant.  The domain-wall epilogue reads its three extra
+// spinor inputs (psi(s) and the halves of psi(s -+ 1)) from global memory, where
+// they are mostly L2 hits (the slices of a site tile run together), instead of
+// staging them: on 16^4 x 16 that took FP32 from 96 to 87 us (5 blocks per SM
+// instead of 3); FP16 stayed at 59 us with 2 or 3 stages.
 template <int P, int EPI>
 constexpr int async_stages() {
-    return EPI == EPI_DWF ? 2 : AsyncCfg<P>::S;
+    return AsyncCfg<P>::S;
 }
 
 // One output site (checkerboard index i < Vh, right-hand side rhs, parity p):
@@ -305,10 +338,6 @@ __device__ __forceinline__ void hop_async_site(const HopArgs& a, int i, int rhs,
         const bool wrap_dn = DAG ? (sl == 0) : (sl + 1 == Ls);
         c_up = wrap_up ? (T)(-a.c_shift * a.mf) : (T)a.c_shift;
         c_dn = wrap_dn ? (T)(-a.c_shift * a.mf) : (T)a.c_shift;
-        // only P+ psi(s_up) (spins 0,1) and P- psi(s_dn) (spins 2,3) are needed
-        async_half_spinor<P, R12, NT, true>(extra + St::SPIN_BYTES, a.x[p] + (size_t)s_up * a.x_rhs, g.Vh, i, t);
-        async_half_spinor<P, R12, NT, false>(extra + St::SPIN_BYTES + St::HALF_BYTES,
-                                             a.x[p] + (size_t)s_dn * a.x_rhs, g.Vh, i, t);
     }
     __pipeline_commit();
 #pragma unroll
@@ -390,8 +419,9 @@ __device__ __forceinline__ void hop_async_site(const HopArgs& a, int i, int rhs,
     if constexpr (EPI == EPI_DWF) {
         cplx<T> su[6], sd[6];
         T nu, nd;
-        smem_half_spinor<P, R12, NT, true>(extra + St::SPIN_BYTES, t, su, nu);
-        smem_half_spinor<P, R12, NT, false>(extra + St::SPIN_BYTES + St::HALF_BYTES, t, sd, nd);
+        // only P+ psi(s_up) (spins 0,1) and P- psi(s_dn) (spins 2,3) are needed
+        load_half_spinor_raw<P, true>(a.x[p] + (size_t)s_up * a.x_rhs, g.Vh, i, su, nu);
+        load_half_spinor_raw<P, false>(a.x[p] + (size_t)s_dn * a.x_rhs, g.Vh, i, sd, nd);
         const T cu = c_up * nu, cdn = c_dn * nd;
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
