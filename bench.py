@@ -38,8 +38,8 @@ METRIC = "Dslash GFlop/s & % HBM roofline; mixed vs FP64 CG time to 1e-10 residu
 PREC_NAMES = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
 CONFIGS = {
     # name: dims, mass, link seed
-    "c3_32x4": ((32, 32, 32, 32), 0.01, 1002),
-    "c2_16x3x32": ((16, 16, 16, 32), 0.05, 1001),
+    "wilson_eo_32x4": ((32, 32, 32, 32), 0.01, 1002),
+    "wilson_eo_16x3x32": ((16, 16, 16, 32), 0.05, 1001),
 }
 
 
@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c3_32x4", choices=sorted(CONFIGS))
+    ap.add_argument("--config", default="wilson_eo_32x4", choices=sorted(CONFIGS))
     ap.add_argument("--prec", default="f16", choices=sorted(PREC_NAMES))
     ap.add_argument("--compress12", type=int, default=0)
     ap.add_argument("--su3-only", action="store_true",
@@ -828,14 +828,14 @@ def other_configs(lqcd, torch):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     rc, stt = lqcd.cg_solve(h, x, b, cp, check=False)
-    out["c1_4x4_fp64_cg"] = {"status": rc, "seconds": time.perf_counter() - t0, "iters": stt[0].iters,
+    out["wilson_4x4_fp64_cg"] = {"status": rc, "seconds": time.perf_counter() - t0, "iters": stt[0].iters,
                              "true_rel_residual": stt[0].true_rel_residual}
     import oracle  # CPU-baseline leg: the oracle timed on the host cores beside each GPU figure
 
     cores = host_cores()
     prm = oracle.params(dims, mass=0.1)
     dt, (xo, it, _, _) = oracle_timed(oracle.cg, oracle.OP_WILSON, b.cpu().numpy(), U, prm, 1e-12)
-    out["c1_4x4_fp64_cg"]["cpu_baseline"] = {"seconds": dt, "iters": it, "cores": cores, "kind": "oracle"}
+    out["wilson_4x4_fp64_cg"]["cpu_baseline"] = {"seconds": dt, "iters": it, "cores": cores, "kind": "oracle"}
     lqcd.lq_destroy(h)
 
     # 16^3x32 even-odd, smooth links, m = 0.05: FP64 and FP32 hops; FP64 and mixed CG to 1e-10
@@ -871,7 +871,7 @@ def other_configs(lqcd, torch):
                            "cg_seconds_projected": dt_cg / max(it, 1) * res["fp64_cg"]["iters"],
                            "cores": cores, "kind": "oracle",
                            "sample": "one FP64 eo hop; 10 CG iterations, projected to the GPU FP64 CG's count"}
-    out["c2_16x3x32_eo"] = res
+    out["wilson_eo_16x3x32_solves"] = res
     lqcd.lq_destroy(h)
 
     # 24^3x48, m = 0.02, 12 point sources: multi-RHS full-lattice hop (FP32) and solves
@@ -924,7 +924,7 @@ def other_configs(lqcd, torch):
     lqcd.lq_destroy(h)
     res["note"] = ("full-lattice D^dag D, m = 0.02, smooth links, 18-real links; b = D^dag (point source); "
                    "eo_*: the even-odd normal equations Mhat^dag Mhat x_e = Mhat^dag eta_e")
-    out["c4_24x3x48_multi_rhs"] = res
+    out["wilson_24x3x48_12rhs"] = res
 
     # uneven batch: 8^4, 12^4, 16^4, 20^4 x 4 right-hand sides, one persistent graph-captured solve
     # (even-odd normal equations, m = 0.02, FP16 inner, FP64 defect correction to 1e-10),
@@ -961,7 +961,7 @@ def other_configs(lqcd, torch):
     res["sequential_per_lattice"] = {"seconds": time.perf_counter() - t0, "max_true_rel_residual": worst}
     for h_ in hs_:
         lqcd.lq_destroy(h_)
-    out["c4b_uneven_batch"] = res
+    out["uneven_batch_8x4_to_20x4"] = res
 
     # 16^4 x Ls=16 domain wall, FP32
     dims = (16, 16, 16, 16)
@@ -1087,7 +1087,7 @@ def other_configs(lqcd, torch):
     del ae, be_
     lqcd.lq_destroy(hm)
     del a_, b_
-    out["c5_16x4xLs16_dwf"] = res
+    out["dwf_16x4_ls16"] = res
     out["halo_2rank_32x4"] = halo_emulation(lqcd, torch, hbm)
     out["su3_mul"] = su3_sweep(lqcd, torch, st, hbm, 20)
     A = inputs.gauge_field((16, 16, 16, 16), "random", seed=1000).reshape(-1, 3, 3)  # 262,144 matrices
