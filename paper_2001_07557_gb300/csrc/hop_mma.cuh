@@ -26,6 +26,12 @@
 // warp waits on its own copies only, as in the CUDA-core hop.  The outputs
 // leave through the warp's shared memory in the same order.  The block
 // barrier at the end sums the fused norm over the block's 32 sites.
+//
+// Measured on 24^3 x 48 with 12 FP16 fields it takes 1.14 ms against 0.40 ms
+// for the CUDA-core hop: the MMA replaces only the 72 FMAs of a site's SU(3)
+// products, while the loads, projection and reconstruction, spread over three
+// lanes per field, cost more instructions than the whole CUDA-core site.  It
+// therefore runs only when a handle selects it (lq_set_hop_kernel).
 #pragma once
 
 #include <cuda_pipeline.h>
