@@ -269,6 +269,21 @@ def oracle_timed(fn, *a, **k):
     return time.perf_counter() - t0, r
 
 
+def host_cpu():
+    """The host CPU's model name (lscpu), else the machine architecture."""
+    import platform
+    import subprocess
+
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip() + " (" + platform.machine() + ")"
+    except Exception:
+        pass
+    return platform.machine()
+
+
 def host_cores():
     try:
         import oracle
@@ -307,7 +322,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"{args.config}: even-odd Mhat^dag Mhat, oracle on a 16^4 sample",
                    "dims": list(sdims), "mass": mass},
-        "cpu_baseline": {"value": val, "unit": "GFlop/s", "cores": cores, "kind": "oracle",
+        "cpu_baseline": {"value": val, "unit": "GFlop/s", "cores": cores, "cpu": host_cpu(), "kind": "oracle",
                          "sample": "Mhat^dag Mhat on a 16^4 lattice per step (same generator and per-site work)"},
         "e2e": {"value": val, "unit": "GFlop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -1110,7 +1125,8 @@ def cpu_baseline(dims, mass, U, psi_e, Vh):
         dt, out = oracle_normal_op(dims, mass, U, psi_e)
         total += dt
         n += 1
-    return ({"value": 4 * FLOP_PER_SITE * Vh * n / total / 1e9, "unit": "GFlop/s", "cores": cores, "kind": "oracle",
+    return ({"value": 4 * FLOP_PER_SITE * Vh * n / total / 1e9, "unit": "GFlop/s", "cores": cores, "cpu": host_cpu(),
+             "kind": "oracle",
              "sample": f"{n} Mhat^dag Mhat applications on the full {list(dims)} lattice, {total:.1f} s"}, out)
 
 
