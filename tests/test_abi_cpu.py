@@ -66,6 +66,16 @@ def test_null_arguments_are_rejected_before_any_launch(L):
     assert L.lq_create(None, ctypes.byref(p), None, 0, None) == -1
     assert L.dslash_apply(None, None, None, 0, -1, 1, None) == -1
     assert L.lq_destroy(None) == -1
+    # the later entry points: a null handle or pointer is LQ_ERR_ARG before anything else
+    assert L.dwf_schur_apply(None, None, None, 0, 0, None) == -1
+    assert L.dwf_eo_prepare(None, None, None, 0, None) == -1
+    assert L.dwf_eo_reconstruct(None, None, None, None, 0, None) == -1
+    assert L.lq_set_hop_kernel(None, 0) == -1
+    n = ctypes.c_size_t(0)
+    assert L.lq_face_wire_bytes(None, 0x10 | 2, ctypes.byref(n)) == -1
+    assert L.lq_face_pack(None, None, None, 0, 0x10 | 2, 1, 1.0, None) == -1
+    assert L.lq_face_unpack(None, None, 0, None, 0x10 | 2, 1, None) == -1
+    assert L.lq_index_faults(None, None, None) == -1
 
 
 def test_su3_mul_argument_checks_before_any_launch(L):
