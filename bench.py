@@ -448,12 +448,62 @@ def main():
             "what": f"the timed step's output ({args.prec} storage) against the FP64 oracle's Mhat^dag Mhat "
                     "of the same source"}
         line["configs"] = other_configs(lqcd, torch)
+        # last key of the line, so that a reader of the line's tail sees the metric's CG half
+        line["summary"] = summary(line)
     lqcd.lq_destroy(h)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def summary(line):
+    """The metric's second half and the other headline figures in a few hundred bytes:
+    time to a 1e-10 FP64 true residual of the mixed and the plain FP64 CG (32^4), the
+    12-source comparison on 24^3x48 (one FP64 single-RHS solve against the 12-source
+    batched mixed and block solves, full D^dag D and even-odd), the FP64 hop of 32^4 (the
+    paper's precision), and the link-sharing hops' fractions of the HBM roofline."""
+    def r(v, d=4):
+        return None if v is None else float(f"{v:.{d}g}")
+
+    out = {}
+    cg = line.get("cg", {})
+    if cg:
+        out["cg_32x4_1e-10"] = {"fp64_s": r(cg["fp64"]["seconds"]), "mixed_s": r(cg["mixed"]["seconds"]),
+                                "speedup": r(cg["speedup"], 3), "fp64_res": r(cg["fp64"]["true_rel_residual"], 2),
+                                "mixed_res": r(cg["mixed"]["true_rel_residual"], 2),
+                                "inner": cg.get("inner_precision")}
+    c4 = line.get("configs", {}).get("wilson_24x3x48_12rhs", {})
+    if c4:
+        def sec(k):
+            return r(c4[k]["seconds"]) if k in c4 else None
+
+        def ok(k):
+            return k in c4 and c4[k]["status"] == 0 and c4[k]["max_true_rel_residual"] < 1e-10
+        out["cg_24x3x48_12src_1e-10"] = {
+            "full": {"fp64_1rhs_s": sec("fp64_cg_1rhs"), "mixed_12rhs_s": sec("mixed_cg_12rhs_batched_f16"),
+                     "block_12rhs_s": sec("block_cg_12rhs_f32"), "fp64_12rhs_s": sec("fp64_cg_12rhs_batched")},
+            "eo": {"fp64_1rhs_s": sec("eo_fp64_cg_1rhs"), "mixed_12rhs_s": sec("eo_mixed_cg_12rhs_batched_f16"),
+                   "block_12rhs_s": sec("eo_block_cg_12rhs_f32")},
+            "all_reached_1e-10": all(ok(k) for k in ("fp64_cg_1rhs", "mixed_cg_12rhs_batched_f16",
+                                                     "block_cg_12rhs_f32", "eo_fp64_cg_1rhs",
+                                                     "eo_mixed_cg_12rhs_batched_f16", "eo_block_cg_12rhs_f32"))}
+        out["hop_24x3x48_12rhs_frac_hbm"] = {k[4:]: r(v["frac_hbm"], 3) for k, v in c4.items()
+                                             if k.startswith("hop_") and "frac_hbm" in v}
+    f64 = line.get("per_precision", {}).get("f64_r18")
+    if f64:
+        out["hop_32x4_f64"] = {"gflops": r(f64["gflops"]), "us": r(f64["ms"] * 1e3),
+                               "frac_fp64_alu": r(f64["gflops"] / (FP64_PEAK_TFLOPS * 1e3), 3)}
+    dwf = line.get("configs", {}).get("dwf_16x4_ls16", {})
+    if dwf:
+        out["dwf_16x4_ls16_frac_hbm"] = {k[4:]: r(v["frac_hbm"], 3) for k, v in dwf.items()
+                                         if k.startswith("dwf_") and isinstance(v, dict) and "frac_hbm" in v}
+    ub = line.get("configs", {}).get("uneven_batch_8x4_to_20x4", {})
+    if ub and "batched_one_graph" in ub:
+        out["uneven_batch_s"] = {"one_graph": r(ub["batched_one_graph"]["seconds"]),
+                                 "sequential": r(ub["sequential_per_lattice"]["seconds"])}
+    return out
 
 
 def e2e(h, lqcd, torch, dims, psi_e, prec, args, world):

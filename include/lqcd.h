@@ -105,7 +105,10 @@ typedef struct lq_handle lq_handle;
  * lq_create: build a handle for one gauge field.
  *   U       device pointer, site-major gauge field in precision U_prec (LQ_F64
  *           or LQ_F32); read during the call only (packed into the handle's
- *           own native copies).  The links must be SU(3) when compress12 = 1.
+ *           own native copies).  With compress12 = 1 the links must be
+ *           SU(3): a link whose |U^dag U - 1| (largest entry) or |det U - 1|
+ *           exceeds 1e-6 (FP64 links) or 1e-5 (FP32 links), or holds a NaN,
+ *           makes the call fail with LQ_ERR_ARG (no handle is made).
  *   stream  cudaStream_t used for the packing; the call synchronises it.
  * The handle owns its packed links (one copy per precision, made on first
  * use) and its workspace; lq_destroy frees them.
@@ -205,7 +208,8 @@ int dwf_eo_reconstruct(lq_handle *h, void *psi, const void *x_e, const void *eta
  * nrhs pairs of fields (layout and precision fmt, sites as in lq_field_bytes;
  * five_d != 0: one 5-d field of Ls slices).  result: DEVICE pointer to
  * 2 * nrhs doubles, (re, im) per right-hand side, written asynchronously on
- * `stream`.  Products are formed in the field's arithmetic precision and
+ * `stream` (memory the device can address, as for lq_convert: a result or
+ * field pointer the device cannot address is LQ_ERR_LAYOUT).  Products are formed in the field's arithmetic precision and
  * summed in FP64 (warp shuffles, one partial per block, fixed-order final
  * sum by the last block), so repeated calls give identical results.  The
  * reduction partials live in handle workspace that grows (cudaMalloc) on
@@ -225,7 +229,8 @@ int lq_dot(lq_handle *h, double *result, const void *a, const void *b, int fmt, 
  * captured, where allocation calls fail.  This call runs the same reduction
  * with its scratch in a fixed file-scope device array (about 0.6 MB, held by
  * every GPU that loads the library until the process exits) and calls no
- * allocating routine.  Arguments and result are those of lq_dot.
+ * allocating routine.  Arguments, result and argument checks are those of
+ * lq_dot (a result pointer the device cannot address is LQ_ERR_LAYOUT).
  *   - nrhs (1 for five_d) must be <= LQ_DOT_NOALLOC_MAX_RHS, else LQ_ERR_ARG.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
@@ -392,16 +397,20 @@ int lq_face_unpack(lq_handle *h, void *dst, int t_dst, const void *wire, int fmt
  *   - Asynchronous on `stream`.  No handle is needed and nothing is allocated.
  * Tiles of A and B move to shared memory by bulk asynchronous copies that
  * complete on shared-memory barriers, and tiles of C leave by bulk stores.
- * Every wait on a barrier is bounded; a wait that runs out leaves its tile of
- * C unwritten and is counted (see lq_wait_timeouts).
+ * Every wait on a barrier is bounded (about a second); a wait that runs out
+ * leaves its tile of C, and the later tiles of its block, unwritten and is
+ * counted.  The call is asynchronous, so it cannot report that itself: its
+ * status covers the argument checks and the launch.  lq_wait_timeouts
+ * (which synchronises) reports it as LQ_ERR_TIMEOUT.
  */
 int lq_su3_mul(void *C, const void *A, const void *B, long n, int fmt, void *stream);
 
 /*
  * lq_wait_timeouts: the number of device-side barrier waits that ran out
  * since the last call (on the current device), then reset to zero.
- * Synchronises the device.  A nonzero count means some results of the
- * kernels that wait on barriers (lq_su3_mul) were not written.
+ * Synchronises the device.  Returns LQ_ERR_TIMEOUT when the count is not
+ * zero (it is still written): some results of the kernels that wait on
+ * barriers (lq_su3_mul) were not written.  LQ_OK otherwise.
  */
 int lq_wait_timeouts(unsigned *count);
 

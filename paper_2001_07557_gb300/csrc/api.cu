@@ -569,6 +569,10 @@ int wilson_apply(lq_handle* h, void* out, const void* in, int fmt, int parity, i
 
 extern "C" {
 
+// Largest deviation from SU(3) (|U^dag U - 1| entry, |det U - 1|) accepted for
+// two-row link storage: FP64 links are unitary to ~1e-15, FP32 ones to ~1e-7.
+constexpr double kSu3TolF64 = 1e-6, kSu3TolF32 = 1e-5;
+
 int lq_create(lq_handle** hp, const lq_params* p, const void* U, int U_prec, void* stream) {
     lq::TraceRange trace_("lqcd/create");
     if (!hp || !p || !U) return LQ_ERR_ARG;
@@ -618,6 +622,19 @@ int lq_create(lq_handle** hp, const lq_params* p, const void* U, int U_prec, voi
         lq_destroy(h);
         return LQ_ERR_CUDA;
     }
+    if (p->compress12) {
+        // two-row storage rebuilds row 3 from rows 1 and 2, exact only for SU(3) links:
+        // a link further from SU(3) than the input precision's rounding allows is refused
+        double dev = 0.0;
+        if (link_su3_deviation(U_prec, h->U_sm, V * 4, &dev, st) != cudaSuccess) {
+            lq_destroy(h);
+            return LQ_ERR_CUDA;
+        }
+        if (!(dev <= (U_prec == LQ_F64 ? kSu3TolF64 : kSu3TolF32))) {
+            lq_destroy(h);
+            return LQ_ERR_ARG;
+        }
+    }
     *hp = h;
     return LQ_OK;
 }
@@ -651,22 +668,6 @@ int lq_field_bytes(const lq_handle* h, int fmt, int subset, int nrhs, int five_d
     if (nrhs < 1) return LQ_ERR_ARG;
     *bytes = field_bytes(h, fmt, subset, nrhs);
     return LQ_OK;
-}
-
-// Can kernels on the current device dereference p?  Device and managed memory,
-// and pinned host memory mapped into the unified address space, can; other
-// host memory only where the device reads pageable memory (coherent host link).
-static bool device_accessible(const void* p) {
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return true;
-    if (at.type == cudaMemoryTypeHost) return at.devicePointer == p;
-    int dev = 0, pageable = 0;
-    return cudaGetDevice(&dev) == cudaSuccess &&
-           cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev) == cudaSuccess && pageable;
 }
 
 int lq_convert(lq_handle* h, void* dst, int dst_fmt, const void* src, int src_fmt, int subset, int nrhs, int five_d,
@@ -873,6 +874,7 @@ int lq_dot(lq_handle* h, double* result, const void* a, const void* b, int fmt, 
     }
     if (nrhs > 65535) return LQ_ERR_ARG;
     DeviceGuard dg(h->device);
+    if (!device_accessible(result) || !device_accessible(a) || !device_accessible(b)) return LQ_ERR_LAYOUT;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool native = (fmt & LQ_NATIVE) != 0;
     const int prec = fmt & 0xF;

@@ -248,8 +248,21 @@ extern "C" int lq_batch_cg_solve(lq_handle** hs, int nlat, void** xs, const void
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h0->device);
     occ = std::max(occ, 1);
+    // the key names the device model (a cached choice is not carried to other GPUs through
+    // the cache file) and the batch shape
+    char devname[64] = "unknown";
+    {
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, h0->device) == cudaSuccess) {
+            snprintf(devname, sizeof(devname), "%.63s", prop.name);
+            for (char* c = devname; *c; ++c)
+                if (*c == ' ' || *c == ':') *c = '_';
+        } else {
+            cudaGetLastError();
+        }
+    }
     char keybuf[512];
-    int kn = snprintf(keybuf, sizeof(keybuf), "batch:p%d:r%d:op%d:n%d", ip, (int)r12, op, nr);
+    int kn = snprintf(keybuf, sizeof(keybuf), "batch:%s:sm%d:p%d:r%d:op%d:n%d", devname, sms, ip, (int)r12, op, nr);
     for (int l = 0; l < nlat && kn < 480; ++l)
         kn += snprintf(keybuf + kn, sizeof(keybuf) - kn, ":%dx%dx%dx%d", hs[l]->g.L[0], hs[l]->g.L[1], hs[l]->g.L[2],
                        hs[l]->g.L[3]);
@@ -381,7 +394,7 @@ extern "C" int lq_batch_cg_solve(lq_handle** hs, int nlat, void** xs, const void
     }
     std::vector<int> iters(nseg, 0), status(nseg, LQ_OK), outer(nseg, 0);
     std::vector<double> rel(nseg, 0.0), bb(nseg, 0.0);
-    std::vector<char> conv(nseg, 0);
+    std::vector<char> conv(nseg, 0), brk(nseg, 0);  // brk: an inner CG broke down at its first step
     Scratch sc{d_part, d_tick};
     auto norms = [&](int l, char* v, int prec, double* out) -> int {
         Lat& L = lat[l];
@@ -445,6 +458,7 @@ extern "C" int lq_batch_cg_solve(lq_handle** hs, int nlat, void** xs, const void
             for (int g = 0; g < nseg; ++g) {
                 its[g] += host_st[g].iter;
                 m = std::max(m, host_st[g].iter);
+                if (r0[g] > 0 && host_st[g].status == LQ_ERR_BREAKDOWN && host_st[g].iter == 0) brk[g] = 1;
             }
             used += std::max(m, 1);
             most += m;
@@ -572,6 +586,9 @@ extern "C" int lq_batch_cg_solve(lq_handle** hs, int nlat, void** xs, const void
                 for (int g = 0; g < nseg; ++g) {
                     iters[g] += host_st[g].iter;
                     most = std::max(most, host_st[g].iter);
+                    // <p, A p> not positive at the first step, with p = r != 0: A is singular on r
+                    if (!conv[g] && host_st[g].status == LQ_ERR_BREAKDOWN && host_st[g].iter == 0)
+                        status[g] = LQ_ERR_BREAKDOWN;
                 }
             } else {
                 // three precisions, as in cg.cu: an FP32 defect correction (FP32 residuals of every
@@ -580,6 +597,8 @@ extern "C" int lq_batch_cg_solve(lq_handle** hs, int nlat, void** xs, const void
                 if (rc || (rc = middle(std::max(kMiddleTolBatch, reach), itol, cp->maxiter - total_inner,
                                        iters, &most)))
                     break;
+                for (int g = 0; g < nseg; ++g)
+                    if (!conv[g] && brk[g]) status[g] = LQ_ERR_BREAKDOWN;
             }
             for (int g = 0; g < nseg; ++g)
                 if (!conv[g]) outer[g] += 1;

@@ -268,6 +268,55 @@ int true_residual(lq_handle* h, const OpGeom& og, const Ctl& c, const VecRef& x6
     return LQ_OK;
 }
 
+// x += e, with A e = b - A x solved from e = 0 by run_cg for the right-hand
+// sides in `want` whose true residual |b - A x| is not below tol |b| (the
+// others get e = 0), to the reduction that meets margin * tol relative to |b|.
+// x, b native in precision wp (CG precision wp).  Adds the iterations to
+// iters[k] and takes the CG's status into status[k] for those right-hand
+// sides.  Scratch: WS_TMP, WS_CG0 .. WS_CG0 + 4, WS_CG0 + 10.
+int correction_cg(lq_handle* h, const OpGeom& og, const Ctl& c, int wp, const VecRef& X, const VecRef& B,
+                  double tol, double margin, const std::vector<char>& want, int maxiter, cudaStream_t s, int* iters,
+                  int* status) {
+    void *x0, *r0;
+    int rc;
+    if ((rc = ensure_ws(h, WS_TMP, og.bytes(h, wp), &x0)) || (rc = ensure_ws(h, WS_CG0 + 10, og.bytes(h, wp), &r0)))
+        return rc;
+    const VecRef X0 = og.ref(h, x0, wp), R0 = og.ref(h, r0, wp);
+    if (cudaMemcpyAsync(x0, X.ptr, og.bytes(h, wp), cudaMemcpyDeviceToDevice, s) != cudaSuccess) return LQ_ERR_CUDA;
+    CgVecs v;
+    if ((rc = cg_vectors(h, og, wp, wp, WS_CG0, &v))) return rc;
+    if ((rc = apply_normal(h, og, wp, v.q.ptr, X0.ptr, v.t.ptr, v.tmp.ptr, s))) return rc;
+    if (launch_axpby(R0, B, 1.0, 0.0, h->g.Vh, og.nblk, og.nrhs, s) != cudaSuccess ||
+        launch_axpby(R0, v.q, -1.0, 1.0, h->g.Vh, og.nblk, og.nrhs, s) != cudaSuccess)
+        return LQ_ERR_CUDA;
+    std::vector<double> bb(og.nrhs), r0n(og.nrhs);
+    if ((rc = norms_to_host(h, og, c, B, bb.data(), s)) || (rc = norms_to_host(h, og, c, R0, r0n.data(), s)))
+        return rc;
+    // the reduction of |r0| that meets the target relative to |b|; a right-hand side that
+    // needs none keeps e = 0
+    double t = 1.0;
+    bool any = false;
+    std::vector<char> solve(og.nrhs, 0);
+    for (int k = 0; k < og.nrhs; ++k) {
+        if (want[k] && r0n[k] > tol * tol * bb[k]) {
+            any = true;
+            solve[k] = 1;
+            t = std::min(t, margin * tol * std::sqrt(bb[k] / r0n[k]));
+        } else if (cudaMemsetAsync(R0.ptr + k * R0.rhs_stride, 0, R0.rhs_stride, s) != cudaSuccess) {
+            return LQ_ERR_CUDA;
+        }
+    }
+    if (!any) return LQ_OK;
+    if ((rc = run_cg(h, og, c, wp, X, R0, t, maxiter, WS_CG0, s))) return rc;
+    if (launch_axpby(X, X0, 1.0, 1.0, h->g.Vh, og.nblk, og.nrhs, s) != cudaSuccess) return LQ_ERR_CUDA;
+    for (int k = 0; k < og.nrhs; ++k) {
+        if (!solve[k]) continue;
+        iters[k] += c.host[k].iter;
+        status[k] = c.host[k].status;
+    }
+    return LQ_OK;
+}
+
 struct BlockCtx {
     lq_handle* h;
     const OpGeom* og;
@@ -287,9 +336,11 @@ constexpr double kMiddleTol = 1e-5;
 // A e = rhs to relative tolerance `target` with an FP32 defect correction:
 // e, rhs FP32; each pass solves A d = r with the low-precision inner CG to
 // max(itol, what is still needed), adds d to e, and recomputes r = rhs - A e
-// with FP32 hops.  iters[k] accumulates operator applications.
+// with FP32 hops.  iters[k] accumulates operator applications; breakdown[k]
+// is set when an inner CG broke down at its first step.
 int solve_fp32_middle(lq_handle* h, const OpGeom& og, const Ctl& c, int ip, const VecRef& e, const VecRef& rhs,
-                      double target, double itol, int maxiter, cudaStream_t s, int* iters, int* most_out) {
+                      double target, double itol, int maxiter, cudaStream_t s, int* iters, int* most_out,
+                      char* breakdown) {
     lq::TraceRange trace_("lqcd/cg/fp32_middle");
     const int Vh = h->g.Vh, nr = og.nrhs;
     void *rp, *dp, *qp, *tp, *tmpp;
@@ -315,6 +366,8 @@ int solve_fp32_middle(lq_handle* h, const OpGeom& og, const Ctl& c, int ip, cons
         for (int k = 0; k < nr; ++k) {
             iters[k] += c.host[k].iter;
             m = std::max(m, c.host[k].iter);
+            // <p, A p> not positive at the first step, with p = r != 0: A is singular on r
+            if (c.host[k].status == LQ_ERR_BREAKDOWN && c.host[k].iter == 0) breakdown[k] = 1;
         }
         used += std::max(m, 1);
         most += m;
@@ -422,57 +475,54 @@ extern "C" int cg_solve(lq_handle* h, void* x, const void* b, const lq_cg_params
     if (mode == LQ_CG_PLAIN) {
         if (cp->x0_is_guess) {
             // restart from a guess: solve A e = b - A x0, then x = x0 + e
-            void* x0;
-            if ((rc = ensure_ws(h, WS_TMP, og.bytes(h, wp), &x0))) return rc;
-            if (to_native(x0, x) != cudaSuccess) return LQ_ERR_CUDA;
-            CgVecs v;
-            if ((rc = cg_vectors(h, og, wp, wp, WS_CG0, &v))) return rc;
-            VecRef X0 = og.ref(h, x0, wp);
-            if ((rc = apply_normal(h, og, wp, v.q.ptr, X0.ptr, v.t.ptr, v.tmp.ptr, s))) return rc;
-            void* r0;
-            if ((rc = ensure_ws(h, WS_CG0 + 10, og.bytes(h, wp), &r0))) return rc;
-            VecRef R0 = og.ref(h, r0, wp);
-            if (launch_axpby(R0, B, 1.0, 0.0, h->g.Vh, og.nblk, og.nrhs, s) != cudaSuccess ||
-                launch_axpby(R0, v.q, -1.0, 1.0, h->g.Vh, og.nblk, og.nrhs, s) != cudaSuccess)
-                return LQ_ERR_CUDA;
-            // tolerance relative to |b|: scale by |b| / |r0|
-            std::vector<double> bb(og.nrhs), r0n(og.nrhs);
-            if ((rc = norms_to_host(h, og, c, B, bb.data(), s)) || (rc = norms_to_host(h, og, c, R0, r0n.data(), s)))
+            if (to_native(xw, x) != cudaSuccess) return LQ_ERR_CUDA;
+            const std::vector<char> all(og.nrhs, 1);
+            if ((rc = correction_cg(h, og, c, wp, X, B, cp->tol, 1.0, all, cp->maxiter, s, iters.data(),
+                                    status.data())))
                 return rc;
-            // tolerance of the correction, relative to |r0|, that meets tol relative to |b|;
-            // a guess whose residual already meets tol is returned as it is
-            double t = 1.0;
-            bool any = false;
-            for (int k = 0; k < og.nrhs; ++k) {
-                if (r0n[k] > cp->tol * cp->tol * bb[k]) {
-                    any = true;
-                    t = std::min(t, cp->tol * std::sqrt(bb[k] / r0n[k]));
-                } else if (cudaMemsetAsync(R0.ptr + k * R0.rhs_stride, 0, R0.rhs_stride, s) != cudaSuccess) {
-                    return LQ_ERR_CUDA;
-                }
-            }
-            if ((rc = run_cg(h, og, c, wp, X, R0, any ? t : 1.0, cp->maxiter, WS_CG0, s))) return rc;
-            if (launch_axpby(X, X0, 1.0, 1.0, h->g.Vh, og.nblk, og.nrhs, s) != cudaSuccess) return LQ_ERR_CUDA;
         } else {
             if ((rc = run_cg(h, og, c, wp, X, B, cp->tol, cp->maxiter, WS_CG0, s))) return rc;
-        }
-        for (int k = 0; k < og.nrhs; ++k) {
-            iters[k] = c.host[k].iter;
-            status[k] = c.host[k].status;
+            for (int k = 0; k < og.nrhs; ++k) {
+                iters[k] = c.host[k].iter;
+                status[k] = c.host[k].status;
+            }
         }
         // true residual in FP64
-        if (wp == LQ_F64) {
-            if ((rc = true_residual(h, og, c, X, B, WS_CG0 + 5, rel.data(), s))) return rc;
-        } else {
-            void *x64, *b64;
-            if ((rc = ensure_ws(h, WS_CG0 + 10, og.bytes(h, LQ_F64), &x64)) ||
-                (rc = ensure_ws(h, WS_CG0 + 11, og.bytes(h, LQ_F64), &b64)))
-                return rc;
+        void *x64 = nullptr, *b64 = nullptr;
+        if (wp != LQ_F64 && ((rc = ensure_ws(h, WS_CG0 + 11, og.bytes(h, LQ_F64), &x64)) ||
+                             (rc = ensure_ws(h, WS_CG0 + 12, og.bytes(h, LQ_F64), &b64))))
+            return rc;
+        auto residual = [&]() -> int {
+            if (wp == LQ_F64) return true_residual(h, og, c, X, B, WS_CG0 + 5, rel.data(), s);
             VecRef X64 = og.ref(h, x64, LQ_F64), B64 = og.ref(h, b64, LQ_F64);
             if (launch_axpby(X64, X, 1.0, 0.0, h->g.Vh, og.nblk, og.nrhs, s) != cudaSuccess ||
                 launch_axpby(B64, B, 1.0, 0.0, h->g.Vh, og.nblk, og.nrhs, s) != cudaSuccess)
                 return LQ_ERR_CUDA;
-            if ((rc = true_residual(h, og, c, X64, B64, WS_CG0 + 5, rel.data(), s))) return rc;
+            return true_residual(h, og, c, X64, B64, WS_CG0 + 5, rel.data(), s);
+        };
+        if ((rc = residual())) return rc;
+        if (wp == LQ_F64) {
+            // reliable stop: CG stops on its recursive residual, which drifts from the true one
+            // by rounding; a right-hand side whose FP64 true residual is not yet below tol
+            // restarts from its iterate (up to three times, within maxiter)
+            for (int pass = 0; pass < 3; ++pass) {
+                std::vector<char> want(og.nrhs, 0);
+                bool any = false;
+                int used = 0;
+                for (int k = 0; k < og.nrhs; ++k) {
+                    used = std::max(used, iters[k]);
+                    want[k] = status[k] == LQ_OK && !(rel[k] < cp->tol);
+                    any = any || want[k];
+                }
+                if (!any || used >= cp->maxiter) break;
+                if ((rc = correction_cg(h, og, c, wp, X, B, cp->tol, 0.5, want, cp->maxiter - used, s, iters.data(),
+                                        status.data())) ||
+                    (rc = residual()))
+                    return rc;
+                for (int k = 0; k < og.nrhs; ++k) outer[k] += want[k];
+            }
+            for (int k = 0; k < og.nrhs; ++k)
+                if (status[k] == LQ_OK && !(rel[k] < cp->tol)) status[k] = LQ_ERR_NOT_CONVERGED;
         }
     } else {
         // FP64 defect correction around a low-precision inner CG (independent
@@ -510,7 +560,7 @@ extern "C" int cg_solve(lq_handle* h, void* x, const void* b, const lq_cg_params
         }
         std::vector<double> bb(og.nrhs), rr(og.nrhs);
         if ((rc = norms_to_host(h, og, c, B, bb.data(), s))) return rc;
-        std::vector<char> conv(og.nrhs, 0);
+        std::vector<char> conv(og.nrhs, 0), brk(og.nrhs, 0);
         std::vector<double> best(og.nrhs, 1e300);
         std::vector<int> stall(og.nrhs, 0);
         int total_inner = 0;
@@ -598,6 +648,9 @@ extern "C" int cg_solve(lq_handle* h, void* x, const void* b, const lq_cg_params
                     for (int k = 0; k < og.nrhs; ++k) {
                         iters[k] += c.host[k].iter;
                         most = std::max(most, c.host[k].iter);
+                        // <p, A p> not positive at the first step, with p = r != 0: A is singular on r
+                        if (!conv[k] && c.host[k].status == LQ_ERR_BREAKDOWN && c.host[k].iter == 0)
+                            status[k] = LQ_ERR_BREAKDOWN;
                     }
                 } else {
                     // three precisions: an FP32 defect correction (cheap FP32 residuals) around
@@ -605,8 +658,10 @@ extern "C" int cg_solve(lq_handle* h, void* x, const void* b, const lq_cg_params
                     // residuals are needed only about twice per solve
                     const double need = std::max(kMiddleTol, reach);
                     if ((rc = solve_fp32_middle(h, og, c, ip, E, RIN, need, itol, cp->maxiter - total_inner, s,
-                                                iters.data(), &most)))
+                                                iters.data(), &most, brk.data())))
                         return rc;
+                    for (int k = 0; k < og.nrhs; ++k)
+                        if (!conv[k] && brk[k]) status[k] = LQ_ERR_BREAKDOWN;
                 }
                 for (int k = 0; k < og.nrhs; ++k)
                     if (!conv[k]) outer[k] += 1;

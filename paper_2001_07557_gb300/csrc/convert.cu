@@ -4,6 +4,9 @@
 // optional two-row compression).  The paper's Gridarray layout (Sec. 3.1)
 // keeps one degree of freedom of many sites contiguous so that whole SIMD
 // registers load at once; the native layout does the same for a warp.
+#include <algorithm>
+#include <cstring>
+
 #include "lqcd_kernels.h"
 
 namespace lq {
@@ -112,6 +115,64 @@ __global__ void links_kernel(char* dst, const void* src, Geom g, size_t link_blo
 
 constexpr int kBlock = 128;
 
+// Largest deviation of a link from SU(3): max over the entries of |U^dag U - 1|
+// and |det U - 1|, in FP64.  Two-row compression rebuilds row 3 as
+// conj(row 1 x row 2), which is row 3 only for a special unitary matrix.
+template <int SP>
+__global__ void link_su3_deviation_kernel(const void* src, long nlinks, unsigned long long* out) {
+    double dev = 0.0;
+    for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < nlinks; l += (long)gridDim.x * blockDim.x) {
+        cplx<double> u[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            if constexpr (SP == LQ_F64) {
+                const double2 v = reinterpret_cast<const double2*>(src)[l * 9 + k];
+                u[k] = {v.x, v.y};
+            } else {
+                const float2 v = reinterpret_cast<const float2*>(src)[l * 9 + k];
+                u[k] = {(double)v.x, (double)v.y};
+            }
+        }
+        // d = the largest |.| seen; fmax would drop a NaN, so NaNs are tracked in nan_seen
+        double d = 0.0;
+        bool nan_seen = false;
+        auto take = [&](cplx<double> z) {
+            const double v = sqrt(z.re * z.re + z.im * z.im);
+            nan_seen = nan_seen || !(v == v);
+            d = v > d ? v : d;
+        };
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                cplx<double> g = {i == j ? -1.0 : 0.0, 0.0};  // (U^dag U)_ij - delta_ij
+#pragma unroll
+                for (int k = 0; k < 3; ++k) cmac_conj(g, u[3 * k + i], u[3 * k + j]);
+                take(g);
+            }
+        }
+        // det U by the first row's cofactors
+        cplx<double> m0 = {0, 0}, m1 = {0, 0}, m2 = {0, 0};
+        cmac(m0, u[4], u[8]);
+        cmac(m0, cneg(u[5]), u[7]);
+        cmac(m1, u[5], u[6]);
+        cmac(m1, cneg(u[3]), u[8]);
+        cmac(m2, u[3], u[7]);
+        cmac(m2, cneg(u[4]), u[6]);
+        cplx<double> det = {-1.0, 0.0};
+        cmac(det, u[0], m0);
+        cmac(det, u[1], m1);
+        cmac(det, u[2], m2);
+        take(det);
+        if (nan_seen) d = __longlong_as_double(0x7ff0000000000000LL);  // NaN counts as infinitely far
+        dev = fmax(dev, d);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dev = fmax(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+    // non-negative doubles order like their bit patterns
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(dev));
+}
+
 }  // namespace
 
 #define LQ_DP_SWITCH(dp, BODY)                              \
@@ -181,6 +242,25 @@ cudaError_t launch_links_to_native(int dst_prec, bool r12, void* dst, int src_pr
         else { LQ_DP_SWITCH(dst_prec, (links_kernel<DP, false, LQ_F32><<<grid, kBlock, 0, st>>>(d, src, g, lb))) }
     }
     return cudaGetLastError();
+}
+
+cudaError_t link_su3_deviation(int src_prec, const void* src, long nlinks, double* dev, cudaStream_t st) {
+    unsigned long long* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(*d));
+    if (e != cudaSuccess) return e;
+    unsigned long long v = 0;
+    e = cudaMemsetAsync(d, 0, sizeof(*d), st);
+    const int grid = (int)std::min<long>((nlinks + 255) / 256, 4096);
+    if (e == cudaSuccess && nlinks > 0) {
+        if (src_prec == LQ_F64) link_su3_deviation_kernel<LQ_F64><<<grid, 256, 0, st>>>(src, nlinks, d);
+        else link_su3_deviation_kernel<LQ_F32><<<grid, 256, 0, st>>>(src, nlinks, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&v, d, sizeof(v), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d);
+    std::memcpy(dev, &v, sizeof(v));
+    return e;
 }
 
 }  // namespace lq

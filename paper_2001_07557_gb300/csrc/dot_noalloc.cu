@@ -64,6 +64,9 @@ extern "C" int lq_dot_noalloc(lq_handle* h, double* result, const void* a, const
     }
     if (nrhs > LQ_DOT_NOALLOC_MAX_RHS) return LQ_ERR_ARG;  // the static scratch holds at most this many
     DeviceGuard dg(h->device);
+    // the result and both fields must be memory the device can address (a plain host
+    // pointer would be dereferenced by the kernel)
+    if (!device_accessible(result) || !device_accessible(a) || !device_accessible(b)) return LQ_ERR_LAYOUT;
     unsigned char* scratch;
     int rc = scratch_address(h->device, &scratch);
     if (rc) return rc;

@@ -119,6 +119,22 @@ inline size_t field_bytes(const lq_handle* h, int fmt, int subset, int nrhs) {
     return sites * 24 * (prec == LQ_F64 ? 8 : 4) * nrhs;
 }
 
+// Can kernels on the current device dereference p?  Device and managed memory,
+// and pinned host memory mapped into the unified address space, can; other
+// host memory only where the device reads pageable memory (coherent host link).
+inline bool device_accessible(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return true;
+    if (at.type == cudaMemoryTypeHost) return at.devicePointer == p;
+    int dev = 0, pageable = 0;
+    return cudaGetDevice(&dev) == cudaSuccess &&
+           cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev) == cudaSuccess && pageable;
+}
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev) {

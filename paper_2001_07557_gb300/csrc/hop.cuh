@@ -21,19 +21,21 @@ template <int P, bool R12, bool DAG, int EPI, bool RED>
 __global__ void __launch_bounds__(128) wilson_hop_kernel(const HopArgs a) {
     pdl_enter();
     using T = typename Prec<P>::real;
-    // grid.x = site block x rhs (rhs fastest: the right-hand sides, or 5th-dimension
-    // slices, of one site tile run together and share each link through L2/L1);
-    // grid.y = output parity
+    // grid.x = (rhs, output parity, site tile), rhs fastest: the right-hand sides, or
+    // 5th-dimension slices, of one site tile run together and share each link through
+    // L2/L1, and so do the two parities of a tile (one parity's outputs read the other's
+    // block as neighbours, its own as the diagonal / 5th-dimension input)
     const int rhs = blockIdx.x % a.nrhs;
+    const int pt = blockIdx.x / a.nrhs;  // parity x tile index
     const Geom& g = a.g;
     const int end = a.nsite ? a.site0 + a.nsite : g.Vh;
-    const int i0 = a.site0 + (blockIdx.x / a.nrhs) * blockDim.x + threadIdx.x;
+    const int i0 = a.site0 + (pt / a.nparity) * blockDim.x + threadIdx.x;
     const bool active = i0 < end;
     if constexpr (!RED) {
         if (!active) return;
     }
     const int i = active ? i0 : end - 1;  // (fused norm: a thread past the end stores nothing)
-    const int p = a.parity0 + blockIdx.y;
+    const int p = a.parity0 + pt % a.nparity;
     if (a.skip && a.skip[(EPI == EPI_DWF ? 0 : rhs) * a.skip_stride]) return;
 
     const char* __restrict__ in = a.in[p] + (size_t)rhs * a.in_rhs;
@@ -177,9 +179,8 @@ __global__ void __launch_bounds__(128) wilson_hop_kernel(const HopArgs a) {
         // warp partials, group-major: [group][warp of the group's blocks]
         const int wpb = blockDim.x >> 5;
         const int grp = EPI == EPI_DWF ? 0 : rhs;
-        const int nblk = EPI == EPI_DWF ? gridDim.x * gridDim.y : (gridDim.x / a.nrhs) * gridDim.y;
-        const int bidx = EPI == EPI_DWF ? blockIdx.x * gridDim.y + blockIdx.y
-                                        : (blockIdx.x / a.nrhs) * gridDim.y + blockIdx.y;
+        const int nblk = EPI == EPI_DWF ? gridDim.x : gridDim.x / a.nrhs;
+        const int bidx = EPI == EPI_DWF ? blockIdx.x : pt;
         hop_norm_warp(v, a.red_partial + (size_t)grp * nblk * wpb, bidx * wpb + (threadIdx.x >> 5));
     }
 }
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(128) wilson_hop_kernel(const HopArgs a) {
 template <int P>
 cudaError_t launch_hop_prec(const HopArgs& a, bool r12, bool dag, int epi, int block, cudaStream_t st) {
     const int nsite = a.nsite ? a.nsite : a.g.Vh;
-    dim3 grid(((nsite + block - 1) / block) * a.nrhs, a.nparity);
+    dim3 grid(((nsite + block - 1) / block) * a.nrhs * a.nparity);
     dim3 blk(block);
     const bool red = a.red_partial != nullptr;
     if (red && epi == EPI_HOP) return cudaErrorInvalidValue;

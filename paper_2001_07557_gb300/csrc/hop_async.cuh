@@ -437,14 +437,17 @@ template <int P, bool R12, bool DAG, int EPI, int NT, int S, bool RED>
 __global__ void __launch_bounds__(NT) wilson_hop_async_kernel(const HopArgs a) {
     using T = float;
     extern __shared__ __align__(16) unsigned char smem[];
-    // grid.x = site block x rhs (rhs fastest: the right-hand sides, or 5th-dimension
-    // slices, of one site tile run together and share each link through L2/L1);
-    // grid.y = output parity
+    // grid.x = (rhs, output parity, site tile), rhs fastest: the right-hand sides, or
+    // 5th-dimension slices, of one site tile run together and share each link through
+    // L2/L1, and so do the two parities of a tile (one parity's outputs read the other's
+    // block as neighbours, its own as the diagonal / 5th-dimension input).  With the
+    // parities in separate passes a full-lattice launch read its input and links twice.
     const int t = threadIdx.x;
     const int rhs = blockIdx.x % a.nrhs;
+    const int pt = blockIdx.x / a.nrhs;  // parity x tile index
     const Geom& g = a.g;
     const int end = a.nsite ? a.site0 + a.nsite : g.Vh;
-    const int i0 = a.site0 + (blockIdx.x / a.nrhs) * NT + t;
+    const int i0 = a.site0 + (pt / a.nparity) * NT + t;
     const bool active = i0 < end;
     // without the fused norm there is no block barrier: a thread past the end leaves;
     // with it, such a thread recomputes the last site and stores nothing
@@ -452,7 +455,7 @@ __global__ void __launch_bounds__(NT) wilson_hop_async_kernel(const HopArgs a) {
         if (!active) return;
     }
     const int i = active ? i0 : end - 1;
-    const int p = a.parity0 + blockIdx.y;
+    const int p = a.parity0 + pt % a.nparity;
     pdl_enter();  // every global access of the block comes after this (programmatic dependent launch)
     if (a.skip && a.skip[(EPI == EPI_DWF ? 0 : rhs) * a.skip_stride]) return;  // uniform per block
     cplx<T> o[12];
@@ -469,9 +472,8 @@ __global__ void __launch_bounds__(NT) wilson_hop_async_kernel(const HopArgs a) {
         // warp partials, group-major: [group][warp of the group's blocks]
         const int wpb = blockDim.x >> 5;
         const int grp = EPI == EPI_DWF ? 0 : rhs;
-        const int nblk = EPI == EPI_DWF ? gridDim.x * gridDim.y : (gridDim.x / a.nrhs) * gridDim.y;
-        const int bidx = EPI == EPI_DWF ? blockIdx.x * gridDim.y + blockIdx.y
-                                        : (blockIdx.x / a.nrhs) * gridDim.y + blockIdx.y;
+        const int nblk = EPI == EPI_DWF ? gridDim.x : gridDim.x / a.nrhs;
+        const int bidx = EPI == EPI_DWF ? blockIdx.x : pt;
         hop_norm_warp(v, a.red_partial + (size_t)grp * nblk * wpb, bidx * wpb + (threadIdx.x >> 5));
     }
 }
@@ -488,7 +490,7 @@ cudaError_t launch_async_one(const HopArgs& a, cudaStream_t st) {
         configured = true;
     }
     const int nsite = a.nsite ? a.nsite : a.g.Vh;
-    return launch_pdl(kern, dim3(((nsite + NT - 1) / NT) * a.nrhs, a.nparity), dim3(NT), smem, st, a);
+    return launch_pdl(kern, dim3(((nsite + NT - 1) / NT) * a.nrhs * a.nparity), dim3(NT), smem, st, a);
 }
 
 // ---------------------------------------------------------------------------

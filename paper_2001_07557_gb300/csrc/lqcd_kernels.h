@@ -112,6 +112,9 @@ cudaError_t launch_spinor_from_native(int dst_prec, void* dst, int src_prec, con
                                       bool full, int parity, int nrhs, cudaStream_t st);
 cudaError_t launch_native_convert(int dst_prec, void* dst, int src_prec, const void* src, int Vh, int nblocks,
                                   cudaStream_t st);
+// Largest deviation from SU(3) of nlinks site-major 3x3 links (max |U^dag U - 1|
+// entry and |det U - 1|; +inf for a NaN); synchronises st.
+cudaError_t link_su3_deviation(int src_prec, const void* src, long nlinks, double* dev, cudaStream_t st);
 // Gauge links: site-major [site][mu][3][3][2] (F64/F32) -> native [parity][mu] blocks.
 cudaError_t launch_links_to_native(int dst_prec, bool r12, void* dst, int src_prec, const void* src, const Geom& g,
                                    cudaStream_t st);

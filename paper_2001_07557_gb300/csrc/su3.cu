@@ -15,7 +15,12 @@
 // FP32 is bound by HBM bandwidth (216 bytes and 198 flop per matrix).  FP64
 // is bound by the FP64 units: 198 flop take longer at GB300's FP64 rate than
 // its 432 bytes take to move.  Every barrier wait is bounded; a wait that runs
-// out is counted in g_wait_timeouts and its block stops.
+// out is counted in g_wait_timeouts and its block stops.  Before it returns,
+// the block waits (bounded again) for the copies it issued into its other
+// stage, and for its bulk stores, so that no copy into its shared memory is
+// left in flight.  The copies of the stage whose wait ran out are not waited
+// for a second time: that wait already lasted about a second, while a tile's
+// copies take microseconds.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -162,7 +167,13 @@ __global__ void __launch_bounds__(TS) su3_mul_kernel(const char* A, const char* 
             s_ok = ok;
         }
         __syncthreads();  // the tile is visible to every thread (or the wait ran out)
-        if (!s_ok) break;
+        if (!s_ok) {
+            // drain the other stage: its tile's copies were issued one iteration ago
+            if (t == 0 && tile + gridDim.x < ntiles &&
+                !mbar_wait_bounded(smem_u32(&bars[s ^ 1]), (uint32_t)(((it + 1) >> 1) & 1)))
+                atomicAdd(&g_wait_timeouts, 1u);
+            break;
+        }
         const int cnt = count(tile), nb = bulk(cnt);
         unsigned char* cbuf = sm + (4 + (it & 1)) * TB;
         if (t < cnt) {
@@ -263,7 +274,7 @@ int lq_wait_timeouts(unsigned* count) {
         cudaMemcpyToSymbol(lq::g_wait_timeouts, &zero, sizeof zero) != cudaSuccess)
         return LQ_ERR_CUDA;
     *count = v;
-    return LQ_OK;
+    return v ? LQ_ERR_TIMEOUT : LQ_OK;
 }
 
 }  // extern "C"

@@ -60,3 +60,35 @@ def test_measured_peak_is_read(bench):
         assert kind == "measured" and 1000 < hbm < 10000
     else:
         assert (hbm, kind) == (6800.0, "fallback")
+
+
+def test_summary_is_short_and_carries_the_cg_half_of_the_metric(bench):
+    """The line's last key condenses the CG comparison (the metric's second half) so that
+    the tail of the printed line holds it; it stays well inside 1,500 characters."""
+    import json
+
+    solve = {"status": 0, "seconds": 0.5123456, "max_iters": 300, "max_outer": 3, "max_true_rel_residual": 7e-11}
+    line = {
+        "cg": {"fp64": {"seconds": 0.37, "true_rel_residual": 8e-11}, "mixed": {"seconds": 0.034,
+               "true_rel_residual": 2.3e-11}, "speedup": 10.88, "inner_precision": "f16"},
+        "per_precision": {"f64_r18": {"gflops": 768.0, "ms": 0.901}},
+        "configs": {
+            "wilson_24x3x48_12rhs": dict({k: dict(solve) for k in (
+                "fp64_cg_1rhs", "fp64_cg_12rhs_batched", "mixed_cg_12rhs_batched_f16", "block_cg_12rhs_f32",
+                "eo_fp64_cg_1rhs", "eo_mixed_cg_12rhs_batched_f16", "eo_block_cg_12rhs_f32")},
+                hop_f32_12rhs_r18={"frac_hbm": 0.41, "gflops": 1.0}),
+            "dwf_16x4_ls16": {"dwf_f32_r18": {"frac_hbm": 0.38}, "cpu_baseline": {}},
+            "uneven_batch_8x4_to_20x4": {"batched_one_graph": {"seconds": 0.0343},
+                                         "sequential_per_lattice": {"seconds": 0.0383}},
+        },
+    }
+    s = bench.summary(line)
+    assert s["cg_32x4_1e-10"]["speedup"] == 10.9 and s["cg_32x4_1e-10"]["mixed_s"] == 0.034
+    assert s["cg_24x3x48_12src_1e-10"]["all_reached_1e-10"] is True
+    assert s["cg_24x3x48_12src_1e-10"]["full"]["block_12rhs_s"] == 0.5123
+    assert s["hop_24x3x48_12rhs_frac_hbm"] == {"f32_12rhs_r18": 0.41}
+    assert s["hop_32x4_f64"]["frac_fp64_alu"] == pytest.approx(768.0 / (bench.FP64_PEAK_TFLOPS * 1e3), rel=1e-2)
+    assert s["dwf_16x4_ls16_frac_hbm"] == {"f32_r18": 0.38}
+    assert len(json.dumps(s)) < 1200
+    line["configs"]["wilson_24x3x48_12rhs"]["block_cg_12rhs_f32"]["max_true_rel_residual"] = 2e-10
+    assert bench.summary(line)["cg_24x3x48_12src_1e-10"]["all_reached_1e-10"] is False

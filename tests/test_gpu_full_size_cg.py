@@ -4,8 +4,9 @@ applied to each returned solution must reproduce the right-hand side to the
 solver tolerance (the oracle's CG itself would take minutes at this size).
 
   32^4, m = 0.01, smooth links: the mixed solve (FP64 outer, FP32 middle,
-  FP16 inner) and the plain FP64 solve of Mhat^dag Mhat x = b to 1e-10, and
-  their difference (both within cond * 1e-10 of the exact solution).
+  FP16 inner) and the plain FP64 solve of Mhat^dag Mhat x = b to 1e-10: the
+  oracle's |b - A x| / |b| is at most 1e-10 for both, and they agree (both
+  within cond * 1e-10 of the exact solution).
   16^3 x 32, m = 0.05: the FP64 even-odd solve and the mixed one with FP32
   inner solves.
   16^4 x Ls 16: the domain-wall solve refined in FP64, unpreconditioned and
@@ -45,9 +46,8 @@ def test_even_odd_solves_at_full_size(dims, mass, seed, inner):
         x_fp64 = solve(H, b, lqcd.LQ_CG_PLAIN, lqcd.LQ_F32)
     prm = oracle.params(dims, mass=mass)
     for x in (x_mixed, x_fp64):
-        # |b - A x| / |b| from the oracle's operator; 2e-10 leaves room for the rounding of one
-        # FP64 Mhat^dag Mhat application on each side
-        assert rel_err(oracle.apply_normal(oracle.OP_WILSON_EO, x, U, prm), b) < 2e-10
+        # |b - A x| / |b| from the oracle's own operator: the stated target, 1e-10
+        assert rel_err(oracle.apply_normal(oracle.OP_WILSON_EO, x, U, prm), b) <= 1e-10
     assert rel_err(x_mixed, x_fp64) < 1e-7
 
 

@@ -5,6 +5,8 @@ Tolerances, from the arithmetic of one entry (3 complex products summed):
 FP64 1e-14 and FP32 2e-6 of the largest entry (inputs rounded to FP32 once,
 then ~6 rounded operations per entry).
 """
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -97,7 +99,11 @@ def test_a_wait_that_runs_out_is_reported_and_the_device_stays_usable():
     t0 = time.perf_counter()
     lqcd.lq_test_stalled_wait()
     dt = time.perf_counter() - t0
-    assert lqcd.lq_wait_timeouts() == 1
+    # the synchronising read reports the wait that ran out as LQ_ERR_TIMEOUT, with the count
+    count = ctypes.c_uint(0)
+    assert lqcd.lib().lq_wait_timeouts(ctypes.byref(count)) == -7
+    assert count.value == 1
+    assert lqcd.lib().lq_wait_timeouts(ctypes.byref(count)) == 0 and count.value == 0
     assert 0.5 < dt < 20.0, dt
     A, B = matrices(1000, 41), matrices(1000, 42)
     check(run(A, B, lqcd.LQ_F32), oracle.su3_mul(A.astype(np.complex64), B.astype(np.complex64)), lqcd.LQ_F32)

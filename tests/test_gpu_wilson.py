@@ -286,6 +286,30 @@ def test_full_size_multi_rhs_fp16_point_sources():
 
 
 @pytest.mark.slow
+def test_full_size_multi_rhs_fp32_point_sources():
+    """24^3x48, smooth links, m = 0.02, the 12 point sources stored as FP32 spinors
+    (the multi-right-hand-side workload's own precision), 18-real links: the full-lattice
+    D of all twelve in one launch, in the launch configuration the bench times, checked
+    element by element against the oracle for four of the sources (FP32 tolerance)."""
+    dims = (24, 24, 24, 48)
+    V = int(np.prod(dims))
+    U = field(dims, "smooth", 1003)
+    src = inputs.point_sources(V)
+    with Handle(dims, U, mass=0.02) as H:
+        nat = lqcd.LQ_NATIVE | lqcd.LQ_F32
+        x = dev(src, lqcd.LQ_F32)
+        xn = native_buffer(H.h, lqcd.LQ_F32, lqcd.LQ_FULL, 12)
+        yn = native_buffer(H.h, lqcd.LQ_F32, lqcd.LQ_FULL, 12)
+        lqcd.lq_convert(H.h, xn, nat, x, lqcd.LQ_F32, lqcd.LQ_FULL, 12)
+        lqcd.dslash_apply(H.h, yn, xn, nat, lqcd.LQ_FULL, nrhs=12)
+        y = torch.empty_like(x)
+        lqcd.lq_convert(H.h, y, lqcd.LQ_F32, yn, nat, lqcd.LQ_FULL, 12)
+        got = host(y)
+    for k in (0, 4, 7, 11):
+        check(got[k], oracle.wilson_dslash(src[k], U, dims, 0.02), lqcd.LQ_F32)
+
+
+@pytest.mark.slow
 @pytest.mark.parametrize("prec", [lqcd.LQ_F32, lqcd.LQ_F16])
 def test_full_size_domain_wall(prec):
     """16^4 x Ls = 16, M5 = 1.8, mf = 0.01, smooth links, Gaussian 5-d field,

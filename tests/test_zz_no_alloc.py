@@ -71,3 +71,36 @@ def test_noalloc_dot_native_five_d_and_size_limit():
         assert c_abi_call(L.lq_dot_noalloc, H.h, res, x, x, lqcd.LQ_F64, lqcd.LQ_FULL, n) == -1  # LQ_ERR_ARG
         torch.cuda.synchronize()
         assert torch.count_nonzero(res).item() == 0
+
+
+def _pageable_access():
+    """cudaDevAttrPageableMemoryAccess (88) of device 0, read through the toolkit's runtime."""
+    rt = ctypes.CDLL("/usr/local/cuda/lib64/libcudart.so")
+    v = ctypes.c_int(0)
+    assert rt.cudaDeviceGetAttribute(ctypes.byref(v), 88, 0) == 0
+    return v.value
+
+
+def test_noalloc_dot_result_must_be_device_addressable():
+    """The result may be pinned host memory (mapped into the device's address
+    space); a pageable host buffer on a device that cannot read pageable memory
+    is rejected before any launch (LQ_ERR_LAYOUT) and left untouched."""
+    dims = (4, 4, 4, 4)
+    V = int(np.prod(dims))
+    L = lqcd.lib()
+    with Handle(dims, inputs.gauge_field(dims, "unit")) as H:
+        a = dev(inputs.gaussian_spinor(V, seed=31))
+        ref = torch.empty(2, dtype=torch.float64, device="cuda")
+        assert c_abi_call(L.lq_dot, H.h, ref, a, a, lqcd.LQ_F64, lqcd.LQ_FULL, 1) == 0
+        pinned = torch.zeros(2, dtype=torch.float64).pin_memory()
+        assert c_abi_call(L.lq_dot_noalloc, H.h, pinned, a, a, lqcd.LQ_F64, lqcd.LQ_FULL, 1) == 0
+        torch.cuda.synchronize()
+        assert abs(pinned[0].item() - ref[0].item()) <= TOL[lqcd.LQ_F64] * ref[0].item()
+        if _pageable_access():
+            return  # pageable memory is addressable on this device: nothing to reject
+        buf = np.zeros(2, dtype=np.float64)
+        st = torch.cuda.current_stream().cuda_stream
+        rc = L.lq_dot_noalloc(ctypes.c_void_p(H.h), ctypes.c_void_p(buf.ctypes.data), ctypes.c_void_p(a.data_ptr()),
+                              ctypes.c_void_p(a.data_ptr()), lqcd.LQ_F64, lqcd.LQ_FULL, 1, 0, ctypes.c_void_p(st))
+        torch.cuda.synchronize()
+        assert rc == -2 and not buf.any()
