@@ -10,9 +10,14 @@ namespace lq {
 constexpr int kMaxBlockRhs = 16;
 
 // The operator the block CG iterates: out = A in for all N columns at once.
+// For A = K^dag K, kimage (if not null) is the buffer in which apply leaves
+// K in (same column layout and stride as in): then P^dag A P = (K P)^dag (K P)
+// is formed as the Gram of K P with itself, which reads N columns instead of
+// 2N and is Hermitian positive semidefinite by construction.
 struct BlockCgOps {
     void* ctx;
     int (*apply)(void* ctx, char* out, const char* in);
+    const char* kimage;
 };
 
 // Bytes of device scratch block_cg needs for N columns over nsites sites.

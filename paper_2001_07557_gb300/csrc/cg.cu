@@ -622,7 +622,7 @@ extern "C" int cg_solve(lq_handle* h, void* x, const void* b, const lq_cg_params
                 OpGeom ogb = og;
                 ogb.nrhs = nb;
                 bctx.og = &ogb;
-                BlockCgOps ops{&bctx, block_apply};
+                BlockCgOps ops{&bctx, block_apply, bctx.t};  // apply leaves K P in bctx.t
                 int bit = 0;
                 const double need = std::max(itol, reach);
                 rc = block_cg(ops, E.ptr, RIN.ptr, static_cast<char*>(bR), static_cast<char*>(bP),

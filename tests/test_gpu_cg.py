@@ -348,3 +348,40 @@ def test_compressed_links_must_be_su3():
         for kind in ("random", "smooth", "unit"):
             with Handle(dims, inputs.gauge_field(dims, kind, seed=1001), mass=0.1, compress12=True, U_prec=prec):
                 pass
+
+
+@pytest.mark.parametrize("inner", [lqcd.LQ_F32, lqcd.LQ_F16])
+@pytest.mark.parametrize("op", ["wilson_eo", "dwf"])
+def test_mixed_multi_field_solves_on_odd_tile_counts(inner, op):
+    """4x6x2x8 has three 64-site tiles per parity, so the FP32 multi-field hop fills the
+    last fused-norm slots of the 128-site layout with zeros: batched mixed CG of three
+    even-odd sources (FP32 and FP16 inner), and the domain-wall CG (Ls = 5, FP32 inner),
+    each solution checked through the oracle's operator."""
+    dims = (4, 6, 2, 8)
+    V = int(np.prod(dims))
+    U = inputs.gauge_field(dims, "smooth", seed=1006)
+    if op == "wilson_eo":
+        m = 0.05
+        b = inputs.gaussian_spinor(V // 2, seed=2020, nrhs=3)
+        prm = oracle.params(dims, mass=m)
+        kw, opc, ocode, n = dict(mass=m), lqcd.LQ_OP_WILSON_EO_NORMAL, oracle.OP_WILSON_EO, 3
+    else:
+        if inner != lqcd.LQ_F32:
+            pytest.skip("the domain-wall mixed solve takes FP32 inner solves")
+        Ls = 5
+        prm = oracle.params(dims, Ls=Ls, M5=1.8, mf=0.01)
+        b = inputs.gaussian_spinor(V, seed=2021, nrhs=Ls)
+        kw, opc, ocode, n = dict(Ls=Ls, M5=1.8, mf=0.01), lqcd.LQ_OP_DWF_NORMAL, oracle.OP_DWF, 1
+    with Handle(dims, U, **kw) as H:
+        bd = dev(b)
+        xd = torch.zeros_like(bd)
+        cp = lqcd.make_cg_params(opc, lqcd.LQ_CG_MIXED, lqcd.LQ_F64, nrhs=n, tol=1e-10, inner=inner,
+                                 inner_tol=1e-6 if op == "dwf" else 0.0)
+        rc, st = lqcd.cg_solve(H.h, xd, bd, cp)
+        xg = host(xd)
+    assert rc == 0 and all(s.true_rel_residual < 1e-10 for s in st)
+    if op == "wilson_eo":
+        for k in range(3):
+            assert rel_err(oracle.apply_normal(ocode, xg[k], U, prm), b[k]) <= 1e-10
+    else:
+        assert rel_err(oracle.apply_normal(ocode, xg, U, prm), b) <= 1e-10

@@ -346,3 +346,61 @@ def test_convert_reads_and_writes_pinned_host_memory():
         lqcd.lq_convert(H.h, hy, lqcd.LQ_F32, n, lqcd.LQ_NATIVE | lqcd.LQ_F32)
         torch.cuda.synchronize()
         assert torch.equal(hy, hx)
+
+
+SHARED_SHAPES = [((4, 6, 2, 8), (1, 1, 1, -1)),   # Vh = 192: three 64-site tiles (an odd count)
+                 ((8, 2, 6, 4), (1, -1, 1, -1)),  # Vh = 192, antiperiodic y
+                 ((6, 4, 4, 2), (-1, 1, 1, 1))]   # Vh = 96: one full and one ragged tile
+
+
+@pytest.mark.parametrize("dims,bc", SHARED_SHAPES, ids=[str(s[0]) for s in SHARED_SHAPES])
+@pytest.mark.parametrize("prec,r12", [(lqcd.LQ_F32, False), (lqcd.LQ_F32, True), (lqcd.LQ_F16, False),
+                                      (lqcd.LQ_F16, True), (lqcd.LQ_BF16, False)])
+@pytest.mark.parametrize("dag", [False, True])
+def test_multi_rhs_launch_equals_single_launches_bit_for_bit(dims, bc, prec, r12, dag):
+    """A launch of several right-hand sides (FP32: the kernel whose blocks share each
+    link between them) gives every right-hand side bit for bit what a launch of its own
+    gives, for the full operator, an even-odd block and the Schur complement; 5
+    right-hand sides (groups with one and two of them) and 9."""
+    V = int(np.prod(dims))
+    U = field(dims, "smooth", 1001)
+    nat = lqcd.LQ_NATIVE | prec
+    fn = lqcd.dslash_dag_apply if dag else lqcd.dslash_apply
+    with Handle(dims, U, mass=0.05, bc=bc, compress12=r12) as H:
+        for nrhs in (5, 9):
+            psi = inputs.gaussian_spinor(V, seed=2100 + nrhs, nrhs=nrhs)
+            for parity, sub_in, sub_out in ((lqcd.LQ_FULL, lqcd.LQ_FULL, lqcd.LQ_FULL),
+                                            (lqcd.LQ_EVEN, lqcd.LQ_ODD, lqcd.LQ_EVEN),
+                                            (lqcd.LQ_SCHUR_EVEN, lqcd.LQ_EVEN, lqcd.LQ_EVEN)):
+                src = psi if sub_in == lqcd.LQ_FULL else np.stack([inputs.to_half(q, dims, sub_in) for q in psi])
+                xn = native_buffer(H.h, prec, sub_in, nrhs)
+                yn = native_buffer(H.h, prec, sub_out, nrhs)
+                lqcd.lq_convert(H.h, xn, nat, dev(src), lqcd.LQ_F64, sub_in, nrhs)
+                fn(H.h, yn, xn, nat, parity, nrhs=nrhs)
+                one_in = xn.numel() // nrhs
+                one_out = yn.numel() // nrhs
+                for k in range(nrhs):
+                    yk = native_buffer(H.h, prec, sub_out, 1)
+                    fn(H.h, yk, xn[k * one_in:(k + 1) * one_in], nat, parity, nrhs=1)
+                    assert torch.equal(yk, yn[k * one_out:(k + 1) * one_out]), (nrhs, parity, k)
+
+
+@pytest.mark.parametrize("prec", [lqcd.LQ_F32, lqcd.LQ_F16])
+def test_domain_wall_slices_match_their_oracle_on_odd_tile_counts(prec):
+    """Domain wall on 4x6x2x8 (three 64-site tiles per parity) with Ls = 3 and 7:
+    the launch over all slices against the oracle, both daggers."""
+    dims = (4, 6, 2, 8)
+    V = int(np.prod(dims))
+    U = field(dims, "smooth", 1004)
+    for Ls in (3, 7):
+        psi = inputs.gaussian_spinor(V, seed=2300 + Ls, nrhs=Ls)
+        with Handle(dims, U, Ls=Ls, M5=1.8, mf=0.01) as H:
+            nat = lqcd.LQ_NATIVE | prec
+            for dag in (False, True):
+                xn = native_buffer(H.h, prec, five_d=True)
+                yn = native_buffer(H.h, prec, five_d=True)
+                lqcd.lq_convert(H.h, xn, nat, dev(psi), lqcd.LQ_F64, five_d=True)
+                lqcd.dwf_dslash_apply(H.h, yn, xn, nat, dag)
+                y = torch.empty_like(dev(psi))
+                lqcd.lq_convert(H.h, y, lqcd.LQ_F64, yn, nat, five_d=True)
+                check(host(y), oracle.dwf_dslash(psi, U, dims, Ls, 1.8, 0.01, dagger=dag), prec)
