@@ -216,27 +216,20 @@ __global__ void gram_final_kernel(const double2* partial, int nblk, int N, doubl
 }
 
 // X_j += sum_k P_k a[k][j],  R_j -= sum_k Q_k a[k][j]   (a: N x N, row-major, complex).
-// GRAM: also partial[blk][i][j] = <R_i, R_j> of the updated R over the block's
-// tiles (the new R tile goes to shared memory and is multiplied there as in
-// block_gram_kernel), so the next R^dag R needs no second read of R.
-template <bool GRAM>
+// (A variant that also summed R^dag R of the new R tile in shared memory was
+// measured slower than this kernel plus the separate Gram: 706 us against
+// 340 + 213 us on half of 24^3 x 48 with 12 columns, its 126 registers halving
+// the resident blocks.)
 __global__ void __launch_bounds__(32 * ((kMaxBlockRhs + 1) / 2)) block_update_kernel(
     float4* __restrict__ X, const float4* __restrict__ P, float4* __restrict__ R, const float4* __restrict__ Q,
-    size_t stride4, long M, int N, const float2* __restrict__ a, double2* __restrict__ partial) {
+    size_t stride4, long M, int N, const float2* __restrict__ a) {
     pdl_enter();
     extern __shared__ float4 sm[];
     float4* sP = sm;
     float4* sQ = sm + (size_t)N * kTE;
     float2* sa = reinterpret_cast<float2*>(sm + (size_t)2 * N * kTE);
-    // the updated R tile, rows padded to kPad (after the N x N coefficients, 16-byte aligned)
-    float4* sR = sm + (size_t)2 * N * kTE + ((size_t)N * N * sizeof(float2) + 15) / 16;
     for (int e = threadIdx.x; e < N * N; e += blockDim.x) sa[e] = a[e];
     const int lane = threadIdx.x & 31;
-    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int gj = lane & 15, gh = lane >> 4;  // Gram: column gj, element parity gh
-    float2 gacc[GRAM ? kMaxBlockRhs : 1];
-#pragma unroll
-    for (int i = 0; i < (GRAM ? kMaxBlockRhs : 1); ++i) gacc[i] = make_float2(0.f, 0.f);
     const WarpCols wc = warp_cols_split(N);
     const int j0 = wc.c0, j1 = wc.c1;
     const bool has0 = wc.has0, has1 = wc.has1;
@@ -284,48 +277,8 @@ __global__ void __launch_bounds__(32 * ((kMaxBlockRhs + 1) / 2)) block_update_ke
                     R[(size_t)j1 * stride4 + ge] = r[1][u];
                 }
             }
-            if constexpr (GRAM) {
-                // elements past M are zero: their P and Q were zero-filled, X and R read as zero
-                if (has0) sR[(size_t)j0 * kPad + lane + 32 * u] = r[0][u];
-                if (has1) sR[(size_t)j1 * kPad + lane + 32 * u] = r[1][u];
-            }
-        }
-        if constexpr (GRAM) {
-            __syncthreads();  // every column's updated R tile is in shared memory
-            for (int q = w; q < kTE / 2; q += nw) {
-                const int e = 2 * q + gh;
-                const float4 bv = gj < N ? sR[gj * kPad + e] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                for (int i = 0; i < kMaxBlockRhs; ++i) {
-                    if (i < N) cdot4(gacc[i], sR[i * kPad + e], bv);
-                }
-            }
         }
         __syncthreads();
-    }
-    if constexpr (GRAM) {
-        // lanes j and j + 16 -> warp sums in shared memory -> fixed-order sum over warps
-        double2* red = reinterpret_cast<double2*>(sm);  // [warp][i][16], in the P / Q tile area
-#pragma unroll
-        for (int i = 0; i < kMaxBlockRhs; ++i) {
-            if (i < N) {
-                double x = gacc[i].x, y = gacc[i].y;
-                x += __shfl_xor_sync(0xffffffffu, x, 16);
-                y += __shfl_xor_sync(0xffffffffu, y, 16);
-                if (gh == 0) red[((size_t)w * N + i) * 16 + gj] = make_double2(x, y);
-            }
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
-            const int i = t / N, jj = t - i * N;
-            double2 v = make_double2(0.0, 0.0);
-            for (int q = 0; q < nw; ++q) {
-                const double2 rr = red[((size_t)q * N + i) * 16 + jj];
-                v.x += rr.x;
-                v.y += rr.y;
-            }
-            partial[(size_t)blockIdx.x * N * N + t] = v;
-        }
     }
 }
 
@@ -460,20 +413,11 @@ int block_cg(const BlockCgOps& ops, char* X, const char* Bv, char* R, char* P, c
             cudaFuncSetAttribute(block_gram_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, gb / 2) !=
                 cudaSuccess)
             return LQ_ERR_CUDA;
-        // the fused update of 16 columns: P and Q tiles, the coefficients and the padded R tile (51 KB)
-        const int ub = (int)(2 * sizeof(float4) * kMaxBlockRhs * kTE +
-                             (sizeof(float2) * kMaxBlockRhs * kMaxBlockRhs + 15) / 16 * 16 +
-                             sizeof(float4) * kMaxBlockRhs * kPad);
-        if (cudaFuncSetAttribute(block_update_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ub) !=
-            cudaSuccess)
-            return LQ_ERR_CUDA;
         configured = true;
     }
     const int g_same = block_grid(M, block_gram_kernel<true>, kGramThreads, kGramStages * gtile);
     const int g_pair = block_grid(M, block_gram_kernel<false>, kGramThreads, 2 * kGramStages * gtile);
-    // the fused update also holds the padded R tile
-    const size_t upd_smem = 2 * tile + (mat + 15) / 16 * 16 + gtile;
-    const int g_upd = block_grid(M, block_update_kernel<true>, nthr, upd_smem);
+    const int g_upd = block_grid(M, block_update_kernel, nthr, 2 * tile + mat);
     const int g_pup = block_grid(M, block_pupdate_kernel, nthr, tile + mat);
     auto f4 = [](const char* q) { return reinterpret_cast<const float4*>(q); };
     auto w4 = [](char* q) { return reinterpret_cast<float4*>(q); };
@@ -526,10 +470,9 @@ int block_cg(const BlockCgOps& ops, char* X, const char* Bv, char* R, char* P, c
         if ((rc = ops.kimage ? gram(ops.kimage, ops.kimage, delta) : gram(P, Q, delta))) return rc;
         if (!chol_solve(delta, rho, alpha, N)) break;  // block lost rank: hand back to the outer loop
         if ((rc = upload(alpha))) return rc;
-        // X += P alpha ; R -= Q alpha, with the partials of the new R^dag R
-        launch_pdl(block_update_kernel<true>, g_upd, nthr, upd_smem, s, w4(X), f4(P), w4(R), f4(Q), stride4, M, N, Md,
-                   partial);
-        if ((rc = gram_sum(g_upd, true, rhonew))) return rc;
+        // X += P alpha ; R -= Q alpha
+        launch_pdl(block_update_kernel, g_upd, nthr, 2 * tile + mat, s, w4(X), f4(P), w4(R), f4(Q), stride4, M, N, Md);
+        if ((rc = gram(R, R, rhonew))) return rc;
         if (!chol_solve(rho, rhonew, beta, N)) {
             ++it;
             break;

@@ -473,15 +473,19 @@ extern "C" int cg_solve(lq_handle* h, void* x, const void* b, const lq_cg_params
     std::vector<double> rel(og.nrhs, 0.0);
 
     if (mode == LQ_CG_PLAIN) {
+        // FP64: the recursive residual is taken to half of tol, so that the true residual, which
+        // drifts from it by rounding, lands below tol (a restart below covers the rare miss; a
+        // restart loses the Krylov space and costs far more than the few extra iterations)
+        const double first = wp == LQ_F64 ? 0.5 : 1.0;
         if (cp->x0_is_guess) {
             // restart from a guess: solve A e = b - A x0, then x = x0 + e
             if (to_native(xw, x) != cudaSuccess) return LQ_ERR_CUDA;
             const std::vector<char> all(og.nrhs, 1);
-            if ((rc = correction_cg(h, og, c, wp, X, B, cp->tol, 1.0, all, cp->maxiter, s, iters.data(),
+            if ((rc = correction_cg(h, og, c, wp, X, B, cp->tol, first, all, cp->maxiter, s, iters.data(),
                                     status.data())))
                 return rc;
         } else {
-            if ((rc = run_cg(h, og, c, wp, X, B, cp->tol, cp->maxiter, WS_CG0, s))) return rc;
+            if ((rc = run_cg(h, og, c, wp, X, B, first * cp->tol, cp->maxiter, WS_CG0, s))) return rc;
             for (int k = 0; k < og.nrhs; ++k) {
                 iters[k] = c.host[k].iter;
                 status[k] = c.host[k].status;

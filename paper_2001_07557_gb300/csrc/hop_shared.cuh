@@ -19,9 +19,8 @@
 //     current one, and the first ones overlap the staging of the links.
 // Per site and right-hand side the L2 traffic drops from 8 neighbours + 8
 // links to 8 neighbours + 8/N links (24^3 x 48, 12 right-hand sides, FP32:
-// 14.1 -> 8.8 GB per launch).  The kernel holds 128 registers per thread,
-// so two blocks of 256 threads share an SM; measured, FP16/BF16 storage (whose
-// hops are issue-bound) do not gain from it and keep the hop_async.cuh kernel.
+// 14.1 -> 8.8 GB per launch).  Measured, FP16/BF16 storage (whose hops are
+// issue-bound) do not gain from it and keep the hop_async.cuh kernel.
 // The arithmetic per site and right-hand side is that of hop_async.cuh, in the
 // same order, so a right-hand side comes out bit for bit as it does from a
 // launch of its own; the fused-norm partials fill the same slots with the same
@@ -34,9 +33,14 @@
 
 namespace lq {
 
-constexpr int kShSites = 64;   // sites per tile (two warps of one group)
-constexpr int kShGroups = 4;   // groups of threads per block, each taking every kShGroups-th right-hand side
-constexpr int kShMinBlocks = 2;  // resident blocks per SM the register budget is set for
+// Block shape, measured on 24^3 x 48 with 12 right-hand sides (FP32) and on the
+// 16^4 x 16 domain wall: 32 sites x 4 groups with five resident blocks of 128
+// threads (102 registers, 43 KB of shared memory each) 494 / 72 us; 64 x 4 with
+// two blocks of 256 threads (128 registers) 527 / 76 us; 64 x 3 with three
+// blocks 533 / 86 us; 32 x 8 with three blocks 606 / 84 us.
+constexpr int kShSites = 32;     // sites per tile (one warp of each group)
+constexpr int kShGroups = 4;     // groups of threads per block, each taking every kShGroups-th right-hand side
+constexpr int kShMinBlocks = 5;  // resident blocks per SM the register budget is set for
 
 // The tile's links in shared memory: per direction, LinkLayout's 16-byte
 // chunks chunk-major over the tile's sites, then the tail chunk.
@@ -103,6 +107,7 @@ __device__ __forceinline__ size_t shared_red_slot(const HopArgs& a, int epi_dwf,
 template <int P, bool R12, bool DAG, int EPI, int G, int S, bool RED>
 __global__ void __launch_bounds__(kShSites* G, kShMinBlocks) wilson_hop_shared_kernel(const HopArgs a) {
     static_assert(!Prec<P>::has_norm, "the shared-link hop serves FP32 storage");
+    static_assert(kShSites % 32 == 0, "a warp must hold sites of one group (one right-hand side)");
     constexpr int NS = kShSites, NT = NS * G;
     using T = float;
     using St = AsyncStage<P, R12, NT>;
