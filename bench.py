@@ -503,6 +503,9 @@ def summary(line):
     if ub and "batched_one_graph" in ub:
         out["uneven_batch_s"] = {"one_graph": r(ub["batched_one_graph"]["seconds"]),
                                  "sequential": r(ub["sequential_per_lattice"]["seconds"])}
+        shape = ub.get("autotuned_shape")
+        if shape:
+            out["uneven_batch_s"]["sites_per_item"] = list(shape["sites_per_item"].values())
     return out
 
 
@@ -699,13 +702,17 @@ def dwf_hops(lqcd, torch, st, hbm, U, reps, precs=(("f32", 1), ("f16", 2), ("bf1
         a_, b_ = (torch.empty(nb, dtype=torch.uint8, device="cuda") for _ in range(2))
         lqcd.lq_convert(h, a_, nat, torch.from_numpy(inputs.gaussian_spinor(V, seed=2004, nrhs=Ls)).cuda(),
                         lqcd.LQ_F64, five_d=True, stream=st)
-        ms = _time(lambda: lqcd.dwf_dslash_apply(h, b_, a_, nat, False, stream=st), st, reps, torch)
         sp = {1: 96, 2: 52, 3: 52}[p]
         byts = V * (4 * {1: 72, 2: 36, 3: 36}[p] + Ls * 2 * sp)  # minimum: links once per 4-d site, 5-d in once, out once
-        res[f"dwf_{pname}_r18"] = {"gflops_4d": FLOP_PER_SITE * V * Ls / (ms * 1e-3) / 1e9, "ms": ms,
-                                   "model_gbs": byts / (ms * 1e-3) / 1e9,
-                                   "frac_hbm": byts / (ms * 1e-3) / 1e9 / hbm,
-                                   "extra_5d_flop_per_site": 96}
+        kinds = [(lqcd.LQ_HOP_CUDA_CORES, "")] + ([(lqcd.LQ_HOP_TENSOR_CORES, "_tensor_cores")] if p > 1 else [])
+        for kind, suffix in kinds:
+            lqcd.lq_set_hop_kernel(h, kind)
+            ms = _time(lambda: lqcd.dwf_dslash_apply(h, b_, a_, nat, False, stream=st), st, reps, torch)
+            res[f"dwf_{pname}_r18{suffix}"] = {
+                "gflops_4d": FLOP_PER_SITE * V * Ls / (ms * 1e-3) / 1e9, "ms": ms,
+                "model_gbs": byts / (ms * 1e-3) / 1e9, "frac_hbm": byts / (ms * 1e-3) / 1e9 / hbm,
+                "extra_5d_flop_per_site": 96,
+                "kernel": "tensor cores (mma.sync m16n8k8)" if kind == lqcd.LQ_HOP_TENSOR_CORES else "CUDA cores"}
         lqcd.lq_destroy(h)
     return res
 
@@ -1005,6 +1012,10 @@ def other_configs(lqcd, torch):
         xs_.append(torch.zeros_like(bs_[-1]))
     cp = lqcd.make_cg_params(lqcd.LQ_OP_WILSON_EO_NORMAL, lqcd.LQ_CG_MIXED, lqcd.LQ_F64, nrhs=4, tol=1e-10,
                              inner=lqcd.LQ_F16)
+    # the autotuner's choices come back through its cache file (read by the library at its first tuning)
+    import tempfile
+    tune_file = os.path.join(tempfile.mkdtemp(), "lqcd_tune.txt")
+    os.environ["LQCD_TUNE_CACHE"] = tune_file
     for rep in range(2):  # the first call also autotunes the persistent launch
         for x_ in xs_:
             x_.zero_()
@@ -1026,6 +1037,7 @@ def other_configs(lqcd, torch):
     res["sequential_per_lattice"] = {"seconds": time.perf_counter() - t0, "max_true_rel_residual": worst}
     for h_ in hs_:
         lqcd.lq_destroy(h_)
+    res["autotuned_shape"] = read_tune_file(tune_file, shapes)
     out["uneven_batch_8x4_to_20x4"] = res
 
     # 16^4 x Ls=16 domain wall, FP32
@@ -1160,6 +1172,24 @@ def other_configs(lqcd, torch):
     out["su3_mul"]["cpu_baseline"] = {"gflops": 198 * len(A) / dt / 1e9, "n": len(A), "cores": cores,
                                       "kind": "oracle", "sample": "one FP64 product over 16^4 x 4 link matrices"}
     return out
+
+
+def read_tune_file(path, shapes):
+    """The batch autotuner's choice for the lattices `shapes` from its cache file: resident
+    blocks and 128-site tiles per work item of each lattice."""
+    want = ":" + ":".join("x".join(str(d) for d in dd) for dd in shapes)
+    try:
+        with open(path) as f:
+            for line in f:
+                tok = line.split()
+                if len(tok) >= 3 and tok[0].endswith(want) and int(tok[2]) == len(shapes):
+                    mult = [int(v) for v in tok[3:3 + len(shapes)]]
+                    return {"blocks": int(tok[1]),
+                            "sites_per_item": {"x".join(str(d) for d in dd): 128 * m for dd, m in zip(shapes, mult)},
+                            "key": tok[0]}
+    except OSError:
+        pass
+    return None
 
 
 def inputs_odd(psi_e):

@@ -151,11 +151,12 @@ int dslash_dag_apply(lq_handle *h, void *out, const void *in, int fmt, int parit
  * lq_set_hop_kernel: which kernel computes the Wilson hops of this handle.
  * The paper's kernels are CUDA-core code (Sec. 3.3); the tensor-core variant
  * is this library's own.  LQ_HOP_CUDA_CORES (the default): the CUDA-core hop.
- * LQ_HOP_TENSOR_CORES: a launch of at least 8 right-hand sides with FP16/BF16
- * storage and 18-real links, over whole parity blocks and with a Wilson
- * epilogue, runs its SU(3) x half-spinor products on the tensor cores (one
- * 16x8x8 MMA with FP32 accumulation per site, direction and group of 8
- * right-hand sides); every other launch keeps the CUDA-core hop.  The two
+ * LQ_HOP_TENSOR_CORES: a launch of at least 8 right-hand sides (or a
+ * domain-wall operator of at least 8 slices, which share each link like
+ * right-hand sides) with FP16/BF16 storage and 18-real links, over whole
+ * parity blocks, runs its SU(3) x half-spinor products on the tensor cores
+ * (one 16x8x8 MMA with FP32 accumulation per site, direction and group of 8
+ * right-hand sides or slices); every other launch keeps the CUDA-core hop.  The two
  * agree to the rounding of FP32 sums.  On GB300 the tensor-core variant is
  * the slower of the two (24^3 x 48, 12 right-hand sides, FP16: 1.1 ms against
  * 0.40 ms), so it is not the default.  Takes effect for launches made after
@@ -310,6 +311,12 @@ int cg_solve(lq_handle *h, void *x, const void *b, const lq_cg_params *cp, lq_cg
  * of all lattices is one launch of a persistent kernel walking a work list,
  * and the iteration is captured once in a CUDA graph and replayed.  xs[i],
  * bs[i] belong to hs[i]; stats holds nlat * cp->nrhs entries (lattice-major).
+ * The persistent hop's shape -- sites per work item of each lattice (1, 2, 4
+ * or 8 tiles of 128) and the resident blocks -- is timed on the batch at its
+ * first solve and kept per device model and batch shape.  With the
+ * environment variable LQCD_TUNE_CACHE naming a file, the choices are read
+ * from and written to it, one line per batch shape:
+ *   <key> <blocks> <nlat> <tiles per item of lattice 0> ... (lattice nlat-1)
  */
 int lq_batch_cg_solve(lq_handle **hs, int nlat, void **xs, const void **bs, const lq_cg_params *cp,
                       lq_cg_stats *stats, void *stream);

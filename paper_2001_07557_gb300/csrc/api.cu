@@ -12,11 +12,11 @@
 namespace lq {
 
 cudaError_t launch_hop_batch(int prec, const HopArgs* args, const int* lat_off, int nlat, bool r12, bool dag, int epi,
-                             int mult, int grid, cudaStream_t st, int* occ) {
+                             int grid, cudaStream_t st, int* occ) {
     switch (prec) {
-    case LQ_F32: return launch_hop_batch_f32(args, lat_off, nlat, r12, dag, epi, mult, grid, st, occ);
-    case LQ_F16: return launch_hop_batch_f16(args, lat_off, nlat, r12, dag, epi, mult, grid, st, occ);
-    case LQ_BF16: return launch_hop_batch_bf16(args, lat_off, nlat, r12, dag, epi, mult, grid, st, occ);
+    case LQ_F32: return launch_hop_batch_f32(args, lat_off, nlat, r12, dag, epi, grid, st, occ);
+    case LQ_F16: return launch_hop_batch_f16(args, lat_off, nlat, r12, dag, epi, grid, st, occ);
+    case LQ_BF16: return launch_hop_batch_bf16(args, lat_off, nlat, r12, dag, epi, grid, st, occ);
     default: return cudaErrorInvalidValue;  // the FP64 hop has no batched form
     }
 }

@@ -37,8 +37,10 @@ namespace {
 constexpr int kIters = 8;  // iterations per graph replay
 constexpr double kMiddleTolBatch = 1e-5;  // the FP32 middle level's target, as in cg.cu
 
+// A launch shape of the persistent hop: 128-site tiles per work item of each
+// lattice, and resident blocks.
 struct Tune {
-    int mult;
+    std::vector<int> mult;
     int grid;
 };
 
@@ -46,6 +48,8 @@ std::mutex g_tune_mutex;
 std::map<std::string, Tune> g_tune;
 bool g_tune_file_loaded = false;
 
+// Cache file (LQCD_TUNE_CACHE): one line per batch shape,
+//   <key> <grid> <nlat> <mult of lattice 0> ... <mult of lattice nlat-1>
 void tune_file_load() {
     if (g_tune_file_loaded) return;
     g_tune_file_loaded = true;
@@ -54,8 +58,14 @@ void tune_file_load() {
     FILE* f = fopen(path, "r");
     if (!f) return;
     char key[512];
-    int m, gr;
-    while (fscanf(f, "%511s %d %d", key, &m, &gr) == 3) g_tune[key] = Tune{m, gr};
+    int gr, n;
+    while (fscanf(f, "%511s %d %d", key, &gr, &n) == 3 && n >= 1 && n <= 64) {
+        Tune tu{std::vector<int>(n), gr};
+        bool ok = true;
+        for (int l = 0; l < n && ok; ++l) ok = fscanf(f, "%d", &tu.mult[l]) == 1 && tu.mult[l] >= 1;
+        if (!ok) break;
+        g_tune[key] = tu;
+    }
     fclose(f);
 }
 
@@ -64,7 +74,11 @@ void tune_file_save() {
     if (!path) return;
     FILE* f = fopen(path, "w");
     if (!f) return;
-    for (const auto& kv : g_tune) fprintf(f, "%s %d %d\n", kv.first.c_str(), kv.second.mult, kv.second.grid);
+    for (const auto& kv : g_tune) {
+        fprintf(f, "%s %d %d", kv.first.c_str(), kv.second.grid, (int)kv.second.mult.size());
+        for (int m : kv.second.mult) fprintf(f, " %d", m);
+        fprintf(f, "\n");
+    }
     fclose(f);
 }
 
@@ -237,12 +251,10 @@ extern "C" int lq_batch_cg_solve(lq_handle** hs, int nlat, void** xs, const void
         h->skip = nullptr;
         if (rc) return rc;
     }
-    if (cudaMemcpyAsync(d_args, args.data(), sizeof(HopArgs) * args.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return LQ_ERR_CUDA;
 
-    // autotuning of the persistent hop: sites per work item (x 128) and resident blocks
+    // autotuning of the persistent hop: sites per work item (x 128) of each lattice and resident blocks
     int occ = 0;
-    if (launch_hop_batch(ip, d_args, d_off, nlat, r12, false, op == LQ_OP_WILSON_NORMAL ? EPI_DIAG : EPI_HOP, 1, 0, s,
+    if (launch_hop_batch(ip, d_args, d_off, nlat, r12, false, op == LQ_OP_WILSON_NORMAL ? EPI_DIAG : EPI_HOP, 0, s,
                          &occ) != cudaSuccess)
         return LQ_ERR_CUDA;
     int sms = 0;
@@ -267,16 +279,23 @@ extern "C" int lq_batch_cg_solve(lq_handle** hs, int nlat, void** xs, const void
         kn += snprintf(keybuf + kn, sizeof(keybuf) - kn, ":%dx%dx%dx%d", hs[l]->g.L[0], hs[l]->g.L[1], hs[l]->g.L[2],
                        hs[l]->g.L[3]);
     const std::string key(keybuf);
-    auto offsets_for = [&](int mult) -> int {
+    // work-item offsets and the lattices' tile sizes in the launch descriptors, for a shape
+    auto shape_for = [&](const Tune& tu) -> int {
         for (int l = 0; l < nlat; ++l) {
-            const int tiles = (hs[l]->g.Vh + kHopThreads * mult - 1) / (kHopThreads * mult);
+            const int m = tu.mult[l];
+            const int tiles = (hs[l]->g.Vh + kHopThreads * m - 1) / (kHopThreads * m);
             off1[l + 1] = off1[l] + tiles * nr;
             off2[l + 1] = off2[l] + tiles * nr * 2;
+            for (int k = 0; k < nhopk; ++k) args[k * nlat + l].batch_mult = m;
         }
         std::vector<int> both(off1);
         both.insert(both.end(), off2.begin(), off2.end());
         return cudaMemcpyAsync(d_off, both.data(), sizeof(int) * both.size(), cudaMemcpyHostToDevice, s) ==
-                       cudaSuccess ? LQ_OK : LQ_ERR_CUDA;
+                               cudaSuccess &&
+                       cudaMemcpyAsync(d_args, args.data(), sizeof(HopArgs) * args.size(), cudaMemcpyHostToDevice,
+                                       s) == cudaSuccess
+                   ? LQ_OK
+                   : LQ_ERR_CUDA;
     };
     auto op_launches = [&](const Tune& tu) -> cudaError_t {
         cudaError_t e = cudaSuccess;
@@ -285,22 +304,18 @@ extern "C" int lq_batch_cg_solve(lq_handle** hs, int nlat, void** xs, const void
             const int epi = full ? EPI_DIAG : ((k & 1) ? EPI_DIAG : EPI_HOP);
             const bool dag = full ? (k == 1) : (k >= 2);
             e = launch_hop_batch(ip, d_args + k * nlat, full ? d_off + (nlat + 1) : d_off, nlat, r12, dag, epi,
-                                 tu.mult, tu.grid, s, nullptr);
+                                 tu.grid, s, nullptr);
         }
         return e;
     };
-    Tune best{1, sms * occ};
+    Tune best{std::vector<int>(nlat, 1), sms * occ};
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         tune_file_load();
         auto it = g_tune.find(key);
-        if (it != g_tune.end()) {
+        if (it != g_tune.end() && (int)it->second.mult.size() == nlat) {
             best = it->second;
         } else {
-            // candidates: one or two waves of resident blocks, 1/2/4 tiles of 128 sites per item
-            std::vector<Tune> cand;
-            for (int m : {1, 2, 4})
-                for (int w : {1, 2}) cand.push_back(Tune{m, std::max(1, sms * occ * w / 2)});
             // the operator reads p: give it a defined value (zero) for the timing runs
             for (auto& L : lat)
                 if (cudaMemsetAsync(L.p, 0, L.bp, s) != cudaSuccess) return LQ_ERR_CUDA;
@@ -308,19 +323,41 @@ extern "C" int lq_batch_cg_solve(lq_handle** hs, int nlat, void** xs, const void
             cudaEvent_t e0, e1;
             cudaEventCreate(&e0);
             cudaEventCreate(&e1);
-            float best_ms = 1e30f;
-            for (const Tune& c : cand) {
-                if ((rc = offsets_for(c.mult))) break;
-                if (op_launches(c) != cudaSuccess) {
-                    rc = LQ_ERR_CUDA;
-                    break;
-                }
+            auto time_of = [&](const Tune& c, float* ms) -> int {
+                int r = shape_for(c);
+                if (r) return r;
+                if (op_launches(c) != cudaSuccess) return LQ_ERR_CUDA;  // warm-up
                 cudaEventRecord(e0, s);
-                for (int r = 0; r < 3; ++r) op_launches(c);
+                for (int k = 0; k < 3; ++k) op_launches(c);
                 cudaEventRecord(e1, s);
-                cudaEventSynchronize(e1);
+                if (cudaEventSynchronize(e1) != cudaSuccess) return LQ_ERR_CUDA;
+                cudaEventElapsedTime(ms, e0, e1);
+                return LQ_OK;
+            };
+            // coordinate descent: each lattice's tile size (1, 2, 4 or 8 tiles of 128 sites per item)
+            // with the others held, smallest lattice first, at one wave of resident blocks; then the
+            // grid (one, two or four waves) for the chosen sizes
+            float best_ms = 1e30f;
+            rc = time_of(best, &best_ms);
+            for (int l = 0; l < nlat && !rc; ++l) {
+                for (int m : {2, 4, 8}) {
+                    if (kHopThreads * m > 2 * hs[l]->g.Vh) break;  // a single item would exceed the lattice
+                    Tune c = best;
+                    c.mult[l] = m;
+                    float ms = 0;
+                    if ((rc = time_of(c, &ms))) break;
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best = c;
+                    }
+                }
+            }
+            for (int w : {2, 4}) {
+                if (rc) break;
+                Tune c = best;
+                c.grid = sms * occ * w;
                 float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
+                if ((rc = time_of(c, &ms))) break;
                 if (ms < best_ms) {
                     best_ms = ms;
                     best = c;
@@ -333,7 +370,7 @@ extern "C" int lq_batch_cg_solve(lq_handle** hs, int nlat, void** xs, const void
             tune_file_save();
         }
     }
-    if ((rc = offsets_for(best.mult))) return rc;
+    if ((rc = shape_for(best))) return rc;
 
     // segment table for the vector steps
     std::vector<BSeg> seg(nseg);

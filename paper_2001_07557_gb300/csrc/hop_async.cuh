@@ -496,12 +496,13 @@ cudaError_t launch_async_one(const HopArgs& a, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // Persistent hop over a batch of lattices of different sizes: one launch of
 // `grid` blocks walks the flattened work list of every lattice's
-// (site tile, right-hand side, parity) items, tile = mult x NT sites, item k
-// of lattice l at lat_off[l] + k.  The per-lattice launch descriptors
-// (pointers, geometry, links, skip flags) live in device memory.
+// (site tile, right-hand side, parity) items, tile = batch_mult x NT sites
+// (each lattice its own, chosen by the autotuner), item k of lattice l at
+// lat_off[l] + k.  The per-lattice launch descriptors (pointers, geometry,
+// links, skip flags, tile size) live in device memory.
 template <int P, bool R12, bool DAG, int EPI, int NT, int S>
 __global__ void __launch_bounds__(NT) wilson_hop_batch_kernel(const HopArgs* __restrict__ args,
-                                                              const int* __restrict__ lat_off, int nlat, int mult) {
+                                                              const int* __restrict__ lat_off, int nlat) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int t = threadIdx.x;
     const int total = lat_off[nlat];
@@ -516,6 +517,7 @@ __global__ void __launch_bounds__(NT) wilson_hop_batch_kernel(const HopArgs* __r
         const int tile = local / a.nrhs;
         if (a.skip && a.skip[rhs * a.skip_stride]) continue;
         const int p = a.parity0 + pidx;
+        const int mult = a.batch_mult;
         for (int m = 0; m < mult; ++m) {
             const int i = (tile * mult + m) * NT + t;
             if (i < a.g.Vh) {
@@ -528,7 +530,7 @@ __global__ void __launch_bounds__(NT) wilson_hop_batch_kernel(const HopArgs* __r
 }
 
 template <int P, bool R12, bool DAG, int EPI>
-cudaError_t launch_batch_one(const HopArgs* args, const int* lat_off, int nlat, int mult, int grid, cudaStream_t st,
+cudaError_t launch_batch_one(const HopArgs* args, const int* lat_off, int nlat, int grid, cudaStream_t st,
                              int* max_blocks_per_sm) {
     constexpr int NT = AsyncCfg<P>::NT, S = AsyncCfg<P>::S;
     constexpr int smem = async_smem_bytes<P, R12, NT, EPI>(S);
@@ -540,18 +542,18 @@ cudaError_t launch_batch_one(const HopArgs* args, const int* lat_off, int nlat, 
         configured = true;
     }
     if (max_blocks_per_sm) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, kern, NT, smem);
-    kern<<<grid, NT, smem, st>>>(args, lat_off, nlat, mult);
+    kern<<<grid, NT, smem, st>>>(args, lat_off, nlat);
     return cudaGetLastError();
 }
 
 // Batched hop launch (grid = 0: report the occupancy in *max_blocks_per_sm instead).
 template <int P>
 cudaError_t launch_hop_batch_prec(const HopArgs* args, const int* lat_off, int nlat, bool r12, bool dag, int epi,
-                                  int mult, int grid, cudaStream_t st, int* max_blocks_per_sm) {
+                                  int grid, cudaStream_t st, int* max_blocks_per_sm) {
     if (epi == EPI_DWF) return cudaErrorInvalidValue;
 #define LQ_B_EPI(R, D)                                                                                       \
-    return epi == EPI_HOP ? launch_batch_one<P, R, D, EPI_HOP>(args, lat_off, nlat, mult, grid, st, max_blocks_per_sm) \
-                          : launch_batch_one<P, R, D, EPI_DIAG>(args, lat_off, nlat, mult, grid, st, max_blocks_per_sm);
+    return epi == EPI_HOP ? launch_batch_one<P, R, D, EPI_HOP>(args, lat_off, nlat, grid, st, max_blocks_per_sm) \
+                          : launch_batch_one<P, R, D, EPI_DIAG>(args, lat_off, nlat, grid, st, max_blocks_per_sm);
     if (r12) {
         if (dag) { LQ_B_EPI(true, true) } else { LQ_B_EPI(true, false) }
     } else {

@@ -13,7 +13,7 @@ cudaError_t launch_hop_bf16(const HopArgs& a, bool r12, bool dag, int epi, int b
     return launch_hop_async<LQ_BF16>(a, r12, dag, epi, st);
 }
 cudaError_t launch_hop_batch_bf16(const HopArgs* args, const int* lat_off, int nlat, bool r12, bool dag, int epi,
-                                 int mult, int grid, cudaStream_t st, int* occ) {
-    return launch_hop_batch_prec<LQ_BF16>(args, lat_off, nlat, r12, dag, epi, mult, grid, st, occ);
+                                 int grid, cudaStream_t st, int* occ) {
+    return launch_hop_batch_prec<LQ_BF16>(args, lat_off, nlat, r12, dag, epi, grid, st, occ);
 }
 }  // namespace lq

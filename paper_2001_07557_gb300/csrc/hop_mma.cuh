@@ -153,9 +153,11 @@ __global__ void __launch_bounds__(mma::kThreads, MINB) wilson_hop_mma_kernel(con
     const int nsv = max(0, min(kSitesPerWarp, Vh - site0));  // valid sites of the warp
 
     pdl_enter();  // every global access of the block comes after this (programmatic dependent launch)
-    // right-hand sides computed and stored (a set skip flag leaves one out)
+    // right-hand sides computed and stored (a set skip flag leaves one out; the domain wall's
+    // slices share the flag of their 5-d system)
     const unsigned live =
-        __ballot_sync(0xffffffffu, lane < nr && !(a.skip && a.skip[(rhs0 + lane) * a.skip_stride])) & 0xffu;
+        __ballot_sync(0xffffffffu, lane < nr && !(a.skip && a.skip[(EPI == EPI_DWF ? 0 : rhs0 + lane) * a.skip_stride])) &
+        0xffu;
     if (live == 0) return;  // uniform over the block: every right-hand side of the group is finished
     if (lane < kSitesPerWarp) {
         unsigned bits = 0;
@@ -322,6 +324,38 @@ __global__ void __launch_bounds__(mma::kThreads, MINB) wilson_hop_mma_kernel(con
                 }
             }
         }
+        if constexpr (EPI == EPI_DWF) {
+            // (5 - M5) psi(s) + c_up P+ psi(s_up) + c_dn P- psi(s_dn) at the lane's site, slice and
+            // colour, read from the native blocks (mostly L2 hits: the slices of a tile run together)
+            if (q < 3 && m < nsv && ((live >> gq) & 1u)) {
+                const int i = site0 + m, Ls = a.Ls, sl = rhs0 + gq;
+                const int s_up = DAG ? (sl + 1 == Ls ? 0 : sl + 1) : (sl == 0 ? Ls - 1 : sl - 1);
+                const int s_dn = DAG ? (sl == 0 ? Ls - 1 : sl - 1) : (sl + 1 == Ls ? 0 : sl + 1);
+                const bool wrap_up = DAG ? (sl + 1 == Ls) : (sl == 0);
+                const bool wrap_dn = DAG ? (sl == 0) : (sl + 1 == Ls);
+                const float c_up = wrap_up ? (float)(-a.c_shift * a.mf) : (float)a.c_shift;
+                const float c_dn = wrap_dn ? (float)(-a.c_shift * a.mf) : (float)a.c_shift;
+                auto word = [&](const char* blk, int c) {  // complex number c = 3 spin + colour of the site
+                    return __ldg(reinterpret_cast<const uint32_t*>(blk + ((size_t)(c >> 2) * Vh + i) * 16) + (c & 3));
+                };
+                auto norm = [&](const char* blk) { return __ldg(reinterpret_cast<const float*>(blk + (size_t)48 * Vh) + i); };
+                const char* xs = a.x[p] + (size_t)sl * a.x_rhs;
+                const char* xu = a.x[p] + (size_t)s_up * a.x_rhs;
+                const char* xd = a.x[p] + (size_t)s_dn * a.x_rhs;
+                const float cd = (float)a.c_diag * norm(xs), cu = c_up * norm(xu), cdn = c_dn * norm(xd);
+#pragma unroll
+                for (int sp = 0; sp < 4; ++sp) {
+                    const float2 v = h2f(word(xs, 3 * sp + q), tag);
+                    o[2 * sp] = fmaf(cd, v.x, o[2 * sp]);
+                    o[2 * sp + 1] = fmaf(cd, v.y, o[2 * sp + 1]);
+                    // only P+ psi(s_up) (spins 0, 1) and P- psi(s_dn) (spins 2, 3)
+                    const float2 w = h2f(word(sp < 2 ? xu : xd, 3 * sp + q), tag);
+                    const float cw = sp < 2 ? cu : cdn;
+                    o[2 * sp] = fmaf(cw, w.x, o[2 * sp]);
+                    o[2 * sp + 1] = fmaf(cw, w.y, o[2 * sp + 1]);
+                }
+            }
+        }
         float mx = 0.f, q2 = 0.f;
         if (q < 3) {
 #pragma unroll
@@ -356,7 +390,9 @@ __global__ void __launch_bounds__(mma::kThreads, MINB) wilson_hop_mma_kernel(con
     }
     if constexpr (RED) {
         // one FP64 partial per (rhs, tile, parity) in the slots of the CUDA-core hop's warp
-        // partials (hop_red_warps per rhs); tile 0 zeroes the slots no tile uses
+        // partials (hop_red_warps per rhs); tile 0 zeroes the slots no tile uses.  The domain
+        // wall's one group holds the slices' slot sets one after another, so the same indexing
+        // with the slice for the right-hand side fills it.
         if (q == 0) red[warp * kRhs + gq] = rsum;
         __syncthreads();
         const int nslots = ((Vh + kHopThreads - 1) / kHopThreads) * (kHopThreads / 32) * (int)gridDim.y;  // hop_red_warps
@@ -395,17 +431,22 @@ cudaError_t launch_mma_one(const HopArgs& a, cudaStream_t st) {
     return launch_mma_cfg<P, DAG, EPI, RED, 3, 3>(a, st);
 }
 
-// The tensor-core hop (selected with lq_set_hop_kernel) takes 18-real links, the
-// Wilson epilogues (no domain-wall terms), whole parity blocks and at least one
-// full group of right-hand sides.
+// The tensor-core hop (selected with lq_set_hop_kernel) takes 18-real links, whole
+// parity blocks and at least one full group of right-hand sides (or domain-wall
+// slices, which share each link like right-hand sides).
 inline bool hop_mma_applies(const HopArgs& a, bool r12, int epi) {
-    return a.mma && !r12 && epi != EPI_DWF && a.nsite == 0 && a.nrhs >= mma::kRhs;
+    (void)epi;
+    return a.mma && !r12 && a.nsite == 0 && a.nrhs >= mma::kRhs;
 }
 
 template <int P>
 cudaError_t launch_hop_mma(const HopArgs& a, bool dag, int epi, cudaStream_t st) {
     const bool red = a.red_partial != nullptr;
     if (red && epi == EPI_HOP) return cudaErrorInvalidValue;
+    if (epi == EPI_DWF) {
+        if (red) return dag ? launch_mma_one<P, true, EPI_DWF, true>(a, st) : launch_mma_one<P, false, EPI_DWF, true>(a, st);
+        return dag ? launch_mma_one<P, true, EPI_DWF, false>(a, st) : launch_mma_one<P, false, EPI_DWF, false>(a, st);
+    }
     if (epi == EPI_HOP) return dag ? launch_mma_one<P, true, EPI_HOP, false>(a, st) : launch_mma_one<P, false, EPI_HOP, false>(a, st);
     if (red) return dag ? launch_mma_one<P, true, EPI_DIAG, true>(a, st) : launch_mma_one<P, false, EPI_DIAG, true>(a, st);
     return dag ? launch_mma_one<P, true, EPI_DIAG, false>(a, st) : launch_mma_one<P, false, EPI_DIAG, false>(a, st);

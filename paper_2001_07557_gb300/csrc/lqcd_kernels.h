@@ -44,6 +44,8 @@ struct HopArgs {
     double* red_partial;
     unsigned* red_ticket;  // unused by the hop (kept for the layout of callers)
     CgScalars* red_st;
+    // persistent batch hop only: 128-site tiles per work item of this lattice (its autotuned size)
+    int batch_mult;
 };
 
 // Every hop launch uses blocks of this many threads (the fused-norm partial
@@ -94,13 +96,14 @@ cudaError_t launch_hop_bf16(const HopArgs& a, bool r12, bool dag, int epi, int b
 
 // Persistent hop over a batch of lattices (FP32 / FP16 / BF16 storage):
 // args[nlat] device launch descriptors, lat_off[nlat + 1] device prefix sums
-// of each lattice's work items (ceil(Vh / (128 mult)) x nrhs x nparity).
-// grid == 0: *occ receives the resident blocks per SM (nothing is launched).
+// of each lattice's work items (ceil(Vh / (128 args[l].batch_mult)) x nrhs x
+// nparity).  grid == 0: *occ receives the resident blocks per SM (nothing is
+// launched).
 cudaError_t launch_hop_batch(int prec, const HopArgs* args, const int* lat_off, int nlat, bool r12, bool dag, int epi,
-                             int mult, int grid, cudaStream_t st, int* occ);
-cudaError_t launch_hop_batch_f32(const HopArgs*, const int*, int, bool, bool, int, int, int, cudaStream_t, int*);
-cudaError_t launch_hop_batch_f16(const HopArgs*, const int*, int, bool, bool, int, int, int, cudaStream_t, int*);
-cudaError_t launch_hop_batch_bf16(const HopArgs*, const int*, int, bool, bool, int, int, int, cudaStream_t, int*);
+                             int grid, cudaStream_t st, int* occ);
+cudaError_t launch_hop_batch_f32(const HopArgs*, const int*, int, bool, bool, int, int, cudaStream_t, int*);
+cudaError_t launch_hop_batch_f16(const HopArgs*, const int*, int, bool, bool, int, int, cudaStream_t, int*);
+cudaError_t launch_hop_batch_bf16(const HopArgs*, const int*, int, bool, bool, int, int, cudaStream_t, int*);
 
 // ----------------------------------------------------------- conversions
 // Spinor fields.  "site-major" = [rhs][site][4][3][2] in F64/F32, sites either

@@ -92,3 +92,16 @@ def test_summary_is_short_and_carries_the_cg_half_of_the_metric(bench):
     assert len(json.dumps(s)) < 1200
     line["configs"]["wilson_24x3x48_12rhs"]["block_cg_12rhs_f32"]["max_true_rel_residual"] = 2e-10
     assert bench.summary(line)["cg_24x3x48_12src_1e-10"]["all_reached_1e-10"] is False
+
+
+def test_tune_file_reader(bench, tmp_path):
+    """The bench reads the batch autotuner's per-lattice choice from the cache file's line format
+    (<key> <blocks> <nlat> <tiles per item of each lattice>)."""
+    f = tmp_path / "tune.txt"
+    shapes = [(8, 8, 8, 8), (12, 12, 12, 12)]
+    f.write_text("batch:NVIDIA_GB300:sm152:p2:r1:op1:n4:4x4x4x4 608 1 2\n"
+                 "batch:NVIDIA_GB300:sm152:p2:r1:op1:n4:8x8x8x8:12x12x12x12 912 2 1 4\n")
+    got = bench.read_tune_file(str(f), shapes)
+    assert got["blocks"] == 912
+    assert got["sites_per_item"] == {"8x8x8x8": 128, "12x12x12x12": 512}
+    assert bench.read_tune_file(str(tmp_path / "missing.txt"), shapes) is None

@@ -126,3 +126,51 @@ def test_set_hop_kernel_rejects_unknown_kinds():
     with Handle(dims, inputs.gauge_field(dims, "unit")) as H:
         with pytest.raises(lqcd.LqError):
             lqcd.lq_set_hop_kernel(H.h, 2)
+
+
+@pytest.mark.parametrize("prec", [lqcd.LQ_F16, lqcd.LQ_BF16])
+@pytest.mark.parametrize("dims,Ls", [((4, 4, 2, 6), 8), ((4, 6, 2, 4), 12), ((4, 4, 4, 4), 16)])
+def test_domain_wall_matches_oracle_and_cuda_cores(prec, dims, Ls):
+    """The domain-wall operator with its Ls slices as the tensor-core kernel's right-hand
+    sides (Ls = 12: a partly filled second group), both daggers, against the oracle's
+    D_dw and the CUDA-core hop of the same handle."""
+    V = int(np.prod(dims))
+    U = inputs.gauge_field(dims, "smooth", seed=1402)
+    psi = inputs.gaussian_spinor(V, seed=2402, nrhs=Ls)
+    nat = lqcd.LQ_NATIVE | prec
+    with Handle(dims, U, Ls=Ls, M5=1.8, mf=0.01) as H:
+        for dag in (False, True):
+            out = {}
+            for kind in (lqcd.LQ_HOP_TENSOR_CORES, lqcd.LQ_HOP_CUDA_CORES):
+                lqcd.lq_set_hop_kernel(H.h, kind)
+                xn, yn = native_buffer(H.h, prec, five_d=True), native_buffer(H.h, prec, five_d=True)
+                lqcd.lq_convert(H.h, xn, nat, dev(psi), lqcd.LQ_F64, five_d=True)
+                lqcd.dwf_dslash_apply(H.h, yn, xn, nat, dag)
+                y = torch.empty_like(dev(psi))
+                lqcd.lq_convert(H.h, y, lqcd.LQ_F64, yn, nat, five_d=True)
+                out[kind] = host(y)
+            want = oracle.dwf_dslash(psi, U, dims, Ls, 1.8, 0.01, dagger=dag)
+            check(out[lqcd.LQ_HOP_TENSOR_CORES], want, prec)
+            check(out[lqcd.LQ_HOP_CUDA_CORES], want, prec)
+
+
+def test_domain_wall_mixed_cg_on_the_tensor_cores():
+    """CG on D_dw^dag D_dw (Ls = 8) refined in FP64 around FP16 inner solves whose operator
+    runs on the tensor cores, with the fused norm of the 5-d system in the kernel's slots:
+    the oracle's D_dw maps the solution back to eta."""
+    dims, Ls = (4, 4, 4, 4), 8
+    V = int(np.prod(dims))
+    U = inputs.gauge_field(dims, "smooth", seed=1403)
+    eta = inputs.gaussian_spinor(V, seed=2403, nrhs=Ls)
+    prm = oracle.params(dims, Ls=Ls, M5=1.8, mf=0.01)
+    b = oracle.apply_op(oracle.OP_DWF, eta, U, prm, dagger=True)
+    with Handle(dims, U, Ls=Ls, M5=1.8, mf=0.01) as H:
+        lqcd.lq_set_hop_kernel(H.h, lqcd.LQ_HOP_TENSOR_CORES)
+        bd = dev(b)
+        xd = torch.zeros_like(bd)
+        cp = lqcd.make_cg_params(lqcd.LQ_OP_DWF_NORMAL, lqcd.LQ_CG_MIXED, lqcd.LQ_F64, tol=1e-10, maxiter=40000,
+                                 inner=lqcd.LQ_F16)
+        rc, st = lqcd.cg_solve(H.h, xd, bd, cp)
+        xg = host(xd)
+    assert rc == 0 and st[0].true_rel_residual < 1e-10
+    assert rel_err(oracle.apply_op(oracle.OP_DWF, xg, U, prm), eta) < 1e-8
