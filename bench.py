@@ -294,24 +294,30 @@ def host_cores():
         return os.cpu_count() or 1
 
 
+def workload_config(args, dims, mass, world):
+    """The `config` of the bench line: the workload both arms run (the GPU arm in the storage precision
+    --prec, the reference arm in the oracle's FP64)."""
+    prec = PREC_NAMES[args.prec]
+    return {"workload": f"{args.config}: even-odd Wilson Mhat^dag Mhat, {args.prec} storage"
+                        f"{' + per-site norms' if prec >= 2 else ''}, {'12' if args.compress12 else '18'}-real links",
+            "dims": list(dims), "mass": mass, "links": "smooth exp(0.3iH), seed " + str(CONFIGS[args.config][2]),
+            "l2": "inputs larger than L2 (links + 3 half spinors > 129 MB); no flush",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle applying the bench's own step (Mhat^dag Mhat on the full
+    lattice of the workload, the same generator and source) on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    mass = CONFIGS[args.config][1]
-    # bounded sample: the same operator on a 16^4 sub-volume of the same generator
-    # (the per-site work is identical; GFlop/s is intensive)
-    sdims = (16, 16, 16, 16)
-    from paper_2001_07557_gb300 import inputs
-
-    Us = inputs.gauge_field(sdims, "smooth", seed=CONFIGS[args.config][2])
-    ps = inputs.gaussian_spinor(int(np.prod(sdims)) // 2, seed=2002)
-    Vh = int(np.prod(sdims)) // 2
+    dims, mass, U, psi_e = setup(args.config)
+    Vh = int(np.prod(dims)) // 2
     for _ in range(args.warmup):
-        oracle_normal_op(sdims, mass, Us, ps)
+        oracle_normal_op(dims, mass, U, psi_e)
     t = 0.0
     for _ in range(args.steps):
-        dt, _ = oracle_normal_op(sdims, mass, Us, ps)
+        dt, _ = oracle_normal_op(dims, mass, U, psi_e)
         t += dt
     flops = 4 * FLOP_PER_SITE * Vh * args.steps
     val = flops / t / 1e9
@@ -320,10 +326,10 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": val, "unit": "GFlop/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.config}: even-odd Mhat^dag Mhat, oracle on a 16^4 sample",
-                   "dims": list(sdims), "mass": mass},
+        "config": workload_config(args, dims, mass, int(os.environ.get("WORLD_SIZE", "1"))),
         "cpu_baseline": {"value": val, "unit": "GFlop/s", "cores": cores, "cpu": host_cpu(), "kind": "oracle",
-                         "sample": "Mhat^dag Mhat on a 16^4 lattice per step (same generator and per-site work)"},
+                         "sample": f"Mhat^dag Mhat on the full {list(dims)} lattice per step, FP64 oracle "
+                                   "(dense gamma matrices, OpenMP over sites)"},
         "e2e": {"value": val, "unit": "GFlop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -419,11 +425,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "GFlop/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32", "data": "synthetic",
-        "config": {"workload": f"{args.config}: even-odd Wilson Mhat^dag Mhat, {args.prec} storage"
-                               f"{' + per-site norms' if prec >= 2 else ''}, {'12' if r12 else '18'}-real links",
-                   "dims": list(dims), "mass": mass, "links": "smooth exp(0.3iH), seed " + str(CONFIGS[args.config][2]),
-                   "l2": "inputs larger than L2 (links + 3 half spinors > 129 MB); no flush",
-                   "parallelism": f"replicas x{world}"},
+        "config": workload_config(args, dims, mass, world),
         "roofline": roofline_entry(prec, bytes_launch, launch_ms, Vh, hbm, peak_kind, traffic),
         "gpu_launches": 4 * args.steps,
         "clocks": clocks.summary(),
