@@ -104,3 +104,33 @@ def test_uneven_batch_with_a_zero_right_hand_side():
     finally:
         for H in Hs:
             H.close()
+
+
+def test_autotuner_cache_file_holds_a_tile_size_per_lattice(tmp_path):
+    """The batch autotuner writes one line per batch shape to LQCD_TUNE_CACHE: a key naming the
+    device model and the lattices, the resident blocks, the lattice count and each lattice's
+    tiles per work item (1, 2, 4 or 8).  A second process reads the line back instead of tuning
+    and solves to the same result."""
+    import json
+    import os
+    import subprocess
+    import sys
+
+    cache = tmp_path / "tune.txt"
+    env = dict(os.environ, LQCD_TUNE_CACHE=str(cache))
+    script = os.path.join(os.path.dirname(__file__), "batch_tune_workload.py")
+    runs = []
+    for _ in range(2):
+        out = subprocess.run([sys.executable, script], env=env, capture_output=True, text=True, timeout=600)
+        assert out.returncode == 0, out.stderr
+        runs.append(json.loads(out.stdout.strip().splitlines()[-1]))
+    assert all(r["rc"] == 0 and r["worst"] < 1e-10 for r in runs)
+    assert runs[0]["x0"] == runs[1]["x0"]  # same shape, same arithmetic: the same solution
+    lines = cache.read_text().split("\n")
+    lines = [ln for ln in lines if ln.strip()]
+    assert len(lines) == 1
+    tok = lines[0].split()
+    key, blocks, nlat, mult = tok[0], int(tok[1]), int(tok[2]), [int(v) for v in tok[3:]]
+    name = torch.cuda.get_device_name(0).replace(" ", "_").replace(":", "_")
+    assert key.startswith("batch:" + name[:63] + ":sm") and key.endswith(":4x4x4x4:6x6x6x6:8x8x8x8")
+    assert blocks >= 1 and nlat == 3 and len(mult) == 3 and all(m in (1, 2, 4, 8) for m in mult)
