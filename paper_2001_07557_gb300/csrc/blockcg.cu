@@ -3,15 +3,15 @@
 //
 //   R = B - A X,  P = R
 //   repeat:  Q = A P                      (one multi-RHS operator launch set)
-//            Delta = P^dag Q,  rho = R^dag R          (N x N, FP64 sums;
-//                    Delta = (K P)^dag (K P) for A = K^dag K)
+//            Delta = P^dag Q = (K P)^dag (K P),  rho = R^dag R
+//                                                      (N x N, FP64 sums)
 //            alpha = Delta^{-1} rho
 //            X += P alpha,  R -= Q alpha
 //            beta = rho^{-1} (R^dag R)_new,  P = R + P beta
-//
+
 // The block vectors live in FP32 storage (FP32 arithmetic); the N x N Gram
-// matrices are summed on the device (FP32 per-thread sums, FP64 lane, warp
-// and block reductions in a fixed order) and the N x N algebra (Cholesky
+// matrices are summed on the device (FP32 per-thread sums, FP64 lane and
+// block reductions in a fixed order) and the N x N algebra (Cholesky
 // solves) runs in FP64 on the host.  Every block kernel reads each column
 // once per call (tiles of all N columns staged in shared memory); P is
 // updated in place.  As a mixed-precision solver
@@ -38,9 +38,11 @@ namespace {
 // array of M float4 (2 complex numbers each) at base + j * stride4 float4s.
 // Every block kernel below walks tiles of kTE consecutive float4 of all N
 // columns: the CTA stages the tile of each input matrix in shared memory with
-// cp.async (one read of every column from memory), then warp w < ceil(N/2)
-// works on the output columns w and N-1-w, lane l on the tile elements l and
-// l + 32.  Blocks have a whole number of kTE-thread groups (see block_threads).
+// cp.async (one read of every column from memory), then in the update kernels
+// warp w < ceil(N/2) works on the output columns w and w + ceil(N/2), lane l
+// on the tile elements l and l + 32 (the Gram kernel splits the work by blocks
+// of the result instead).  Blocks have a whole number of kTE-thread groups
+// (see block_threads).
 constexpr int kTE = 64;
 constexpr int kGrid = 152 * 4;  // grid of the block kernels (partials sized for it)
 constexpr int kGramStages = 3;
@@ -55,32 +57,21 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-// s[j * pitch + e] = column j, element e0 + e (zero past M)
+// s[j * kTE + e] = column j, element e0 + e (zero past M)
 __device__ __forceinline__ void stage_tile(float4* s, const float4* __restrict__ base, size_t stride4, long e0,
-                                           long M, int N, int pitch = kTE) {
+                                           long M, int N) {
     const int e = threadIdx.x & (kTE - 1);  // blockDim.x is a multiple of kTE
     const bool ok = e0 + e < M;
     const float4* src = base + (ok ? e0 + e : 0);
     for (int j = threadIdx.x / kTE; j < N; j += blockDim.x / kTE)
-        cp_async16(s + j * pitch + e, src + (size_t)j * stride4, ok);
+        cp_async16(s + j * kTE + e, src + (size_t)j * stride4, ok);
 }
 
-// the output columns of this warp: c0 = w and c1 = N-1-w (if different)
+// the output columns of this warp in the update kernels: c0 = w, c1 = w + ceil(N/2)
 struct WarpCols {
     int c0, c1;
     bool has0, has1;
 };
-__device__ __forceinline__ WarpCols warp_cols(int N) {
-    const int w = threadIdx.x >> 5;
-    WarpCols c;
-    c.c0 = w;
-    c.c1 = N - 1 - w;
-    c.has0 = w < (N + 1) / 2;
-    c.has1 = c.has0 && c.c1 > c.c0;
-    return c;
-}
-
-// for the update kernels: c0 = w, c1 = w + ceil(N/2)
 __device__ __forceinline__ WarpCols warp_cols_split(int N) {
     const int w = threadIdx.x >> 5, h = (N + 1) / 2;
     WarpCols c;
@@ -115,84 +106,130 @@ __device__ __forceinline__ void cmac4(float4& y, const float2 c, const float4 x)
     y.w = fmaf(c.y, x.z, y.w);
 }
 
-// partial[blk][i][j] = sum over the block's tiles of <A_i, B_j> (conj on A).
-// The tile of column j sits in shared memory at row j with a pitch of kPad
-// float4 (one float4 of padding spreads the rows over the banks).  Lane
-// (j = l & 15, h = l >> 4) of a warp owns column j and the elements of parity
-// h of each element pair the warp takes; it reads B_j once per element and
-// the N row values A_i as broadcasts, and keeps one complex sum per row.
-// kGramStages tile buffers: the copies of the next tiles are in flight while
-// the current one is multiplied.  Sums in FP32 per thread; the reductions
-// over lanes, warps and blocks in FP64.  The kernel is issue-bound: one
-// shared-memory load per 8 FMA, about 40% of the issue slots used.
-constexpr int kPad = kTE + 1;
-constexpr int kGramThreads = 256;
+// partial[blk][i][j] = sum over the block's tiles of <A_i, A_j> (conj on the
+// first), for i <= j (the rest of the Hermitian result is its conjugate; the
+// kernel writes zeros there).  The N columns form groups of kGramGroup; warp w
+// owns one kGramGroup x kGramGroup block (I, J), I <= J, of the result and
+// keeps its complex sums in registers (on a diagonal block I = J only those
+// with r <= c).  A pipeline stage holds kGramSub sub-tiles of kTE float4 of
+// every column, column j of a sub-tile at row j (no padding: lane l reads
+// element l + 32 u, so a warp's 16-byte loads cover consecutive banks).  Per
+// float4 a lane loads the 4 + 4 column values of its block (4 when I = J) and
+// does 16 (10) complex products of two complex pairs, from immediate offsets
+// of one shared address; whether the block is diagonal and whether all its
+// columns exist (N a multiple of 4, or not the last group) are resolved once
+// per sub-tile by a warp-uniform branch.  kGramStages stages: the copies of
+// the next ones are in flight while the current one is multiplied.  Sums in
+// FP32 per lane; the reductions over lanes and blocks in FP64, in a fixed
+// order.
+constexpr int kGramGroup = 4;
+constexpr int kGramSub = 2;
 
-template <bool SAME>
-__global__ void __launch_bounds__(kGramThreads) block_gram_kernel(const float4* __restrict__ A,
-                                                                  const float4* __restrict__ B, size_t stride4,
-                                                                  long M, int N, double2* partial) {
+__host__ __device__ constexpr int gram_groups(int N) { return (N + kGramGroup - 1) / kGramGroup; }
+__host__ __device__ constexpr int gram_blocks(int N) { return gram_groups(N) * (gram_groups(N) + 1) / 2; }
+// one warp per result block, rounded up to whole kTE-thread groups (tile staging)
+__host__ __device__ constexpr int gram_threads(int N) { return kTE * ((32 * gram_blocks(N) + kTE - 1) / kTE); }
+constexpr int kGramMaxThreads = gram_threads(kMaxBlockRhs);
+
+// acc[r][c] += conj(a_r) b_c for one float4 of the sub-tile: a_r at sa[r * kTE]
+// (column 4I + r), b_c at sb[c * kTE] (column 4J + c); na, nb: columns of the
+// two groups that exist.  DIAG: sb = sa, and only r <= c.  FULL: na = nb = 4.
+template <bool DIAG, bool FULL>
+__device__ __forceinline__ void gram_accumulate(float2 (&acc)[kGramGroup][kGramGroup], const float4* sa,
+                                                const float4* sb, int na, int nb) {
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 a[kGramGroup], b[kGramGroup];
+#pragma unroll
+    for (int c = 0; c < kGramGroup; ++c) {
+        a[c] = (FULL || c < na) ? sa[c * kTE] : z4;
+        if (!DIAG) b[c] = (FULL || c < nb) ? sb[c * kTE] : z4;
+    }
+#pragma unroll
+    for (int r = 0; r < kGramGroup; ++r)
+#pragma unroll
+        for (int c = 0; c < kGramGroup; ++c)
+            if (!DIAG || r <= c) cdot4(acc[r][c], a[r], DIAG ? a[c] : b[c]);
+}
+
+__global__ void __launch_bounds__(kGramMaxThreads) block_gram_kernel(const float4* __restrict__ A, size_t stride4,
+                                                                     long M, int N, double2* partial) {
     pdl_enter();
     extern __shared__ float4 sm[];
-    const size_t buf = (size_t)(SAME ? 1 : 2) * N * kPad;  // float4 per tile buffer
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int j = lane & 15, h = lane >> 4;
-    const bool act = j < N;
-    float2 acc[kMaxBlockRhs];
+    const size_t sub = (size_t)N * kTE, buf = kGramSub * sub;  // float4 per sub-tile, per stage
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int ng = gram_groups(N);
+    const bool busy = w < gram_blocks(N);
+    int I = 0, r = w;  // this warp's block (I, J) of the result
+    while (I < ng && r >= ng - I) {  // row I of the upper triangle holds ng - I blocks
+        r -= ng - I;
+        ++I;
+    }
+    const int J = I + r;
+    const int na = min(kGramGroup, N - kGramGroup * I), nb = min(kGramGroup, N - kGramGroup * J);
+    const int mode = (I == J ? 2 : 0) + (na == kGramGroup && nb == kGramGroup ? 1 : 0);
+    float2 acc[kGramGroup][kGramGroup];
 #pragma unroll
-    for (int i = 0; i < kMaxBlockRhs; ++i) acc[i] = make_float2(0.f, 0.f);
-    const long step = (long)gridDim.x * kTE;
+    for (int a = 0; a < kGramGroup; ++a)
+#pragma unroll
+        for (int b = 0; b < kGramGroup; ++b) acc[a][b] = make_float2(0.f, 0.f);
+    const long span = (long)kGramSub * kTE, step = (long)gridDim.x * span;
     auto stage = [&](long e0, int k) {
         if (e0 < M) {
-            float4* sA = sm + k * buf;
-            stage_tile(sA, A, stride4, e0, M, N, kPad);
-            if (!SAME) stage_tile(sA + (size_t)N * kPad, B, stride4, e0, M, N, kPad);
+#pragma unroll
+            for (int q = 0; q < kGramSub; ++q) stage_tile(sm + k * buf + q * sub, A, stride4, e0 + q * kTE, M, N);
         }
-        asm volatile("cp.async.commit_group;\n" ::: "memory");  // one group per tile (maybe empty)
+        asm volatile("cp.async.commit_group;\n" ::: "memory");  // one group per stage (maybe empty)
     };
 #pragma unroll
-    for (int k = 0; k < kGramStages - 1; ++k) stage((long)blockIdx.x * kTE + k * step, k);
+    for (int k = 0; k < kGramStages - 1; ++k) stage((long)blockIdx.x * span + k * step, k);
     int k = 0;
-    for (long e0 = (long)blockIdx.x * kTE; e0 < M; e0 += step) {
+    for (long e0 = (long)blockIdx.x * span; e0 < M; e0 += step) {
         stage(e0 + (kGramStages - 1) * step, (k + kGramStages - 1) % kGramStages);
-        asm volatile("cp.async.wait_group %0;\n" ::"n"(kGramStages - 1) : "memory");  // tile e0 has landed
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(kGramStages - 1) : "memory");  // stage e0 has landed
         __syncthreads();
-        const float4* sA = sm + k * buf;
-        const float4* sB = SAME ? sA : sA + (size_t)N * kPad;
-        for (int q = w; q < kTE / 2; q += nw) {
-            const int e = 2 * q + h;
-            const float4 bv = act ? sB[j * kPad + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (busy) {
 #pragma unroll
-            for (int i = 0; i < kMaxBlockRhs; ++i) {
-                if (i < N) cdot4(acc[i], sA[i * kPad + e], bv);
+            for (int q = 0; q < kGramSub; ++q) {
+                // elements past M are zero-filled
+                const float4* sa = sm + k * buf + q * sub + kGramGroup * I * kTE + lane;
+                const float4* sb = sm + k * buf + q * sub + kGramGroup * J * kTE + lane;
+#pragma unroll
+                for (int u = 0; u < kTE / 32; ++u) {
+                    switch (mode) {
+                        case 3: gram_accumulate<true, true>(acc, sa + 32 * u, sa + 32 * u, na, nb); break;
+                        case 2: gram_accumulate<true, false>(acc, sa + 32 * u, sa + 32 * u, na, nb); break;
+                        case 1: gram_accumulate<false, true>(acc, sa + 32 * u, sb + 32 * u, na, nb); break;
+                        default: gram_accumulate<false, false>(acc, sa + 32 * u, sb + 32 * u, na, nb); break;
+                    }
+                }
             }
         }
-        __syncthreads();  // buffer k is refilled by a later iteration's copies
+        __syncthreads();  // stage k is refilled by a later iteration's copies
         k = (k + 1) % kGramStages;
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    // lanes j and j + 16 -> warp sums in shared memory -> fixed-order sum over warps
-    double2* red = reinterpret_cast<double2*>(sm);  // [warp][i][16]
+    __syncthreads();
+    // lane sums -> one FP64 entry per (i, j) in shared memory (zero where no warp sums) -> partial
+    double2* red = reinterpret_cast<double2*>(sm);  // [N][N]
+    for (int t = threadIdx.x; t < N * N; t += blockDim.x) red[t] = make_double2(0.0, 0.0);
+    __syncthreads();
+    if (busy) {
 #pragma unroll
-    for (int i = 0; i < kMaxBlockRhs; ++i) {
-        if (i < N) {
-            double x = acc[i].x, y = acc[i].y;
-            x += __shfl_xor_sync(0xffffffffu, x, 16);
-            y += __shfl_xor_sync(0xffffffffu, y, 16);
-            if (h == 0) red[((size_t)w * N + i) * 16 + j] = make_double2(x, y);
-        }
+        for (int a = 0; a < kGramGroup; ++a)
+#pragma unroll
+            for (int b = 0; b < kGramGroup; ++b) {
+                double x = acc[a][b].x, y = acc[a][b].y;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    x += __shfl_xor_sync(0xffffffffu, x, o);
+                    y += __shfl_xor_sync(0xffffffffu, y, o);
+                }
+                const int i = kGramGroup * I + a, j = kGramGroup * J + b;
+                if (lane == 0 && i <= j && i < N && j < N) red[i * N + j] = make_double2(x, y);
+            }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
-        const int i = t / N, jj = t - i * N;
-        double2 v = make_double2(0.0, 0.0);
-        for (int q = 0; q < nw; ++q) {
-            const double2 r = red[((size_t)q * N + i) * 16 + jj];
-            v.x += r.x;
-            v.y += r.y;
-        }
-        partial[(size_t)blockIdx.x * N * N + t] = v;
-    }
+    for (int t = threadIdx.x; t < N * N; t += blockDim.x) partial[(size_t)blockIdx.x * N * N + t] = red[t];
 }
 
 // G = sum over blocks of the partials: one warp per entry, lanes stride over
@@ -396,55 +433,46 @@ bool chol_solve(const std::vector<cd>& H, const std::vector<cd>& Y, std::vector<
 int block_cg(const BlockCgOps& ops, char* X, const char* Bv, char* R, char* P, char* Q, size_t stride, long nsites,
              int N, double tol, int maxiter, void* ws, double2* hostbuf, cudaStream_t s, int* iters) {
     lq::TraceRange trace_("lqcd/cg/block");
-    if (N < 1 || N > kMaxBlockRhs || stride % 16 != 0) return LQ_ERR_ARG;
+    if (N < 1 || N > kMaxBlockRhs || stride % 16 != 0 || !ops.kimage) return LQ_ERR_ARG;
     const long M = nsites * (spinor_site_bytes(LQ_F32) / 16);  // float4 per column
     const size_t stride4 = stride / 16;
     const int nthr = block_threads(N);
     const size_t tile = sizeof(float4) * N * kTE, mat = sizeof(float2) * N * N;
-    const size_t gtile = sizeof(float4) * N * kPad;  // Gram tile buffer (padded rows)
+    const size_t gtile = sizeof(float4) * N * kTE * kGramSub;  // Gram stage buffer
+    const int t_gram = gram_threads(N);
     double2* partial = static_cast<double2*>(ws);
     double2* Gd = partial + (size_t)kGrid * N * N;
     float2* Md = reinterpret_cast<float2*>(Gd + N * N);
-    static bool configured = false;  // the Gram of 16 columns takes 100 KB of tile buffers
+    static bool configured = false;  // the Gram of 16 columns takes 96 KB of stage buffers
     if (!configured) {
-        const int gb = (int)(2 * kGramStages * sizeof(float4) * kMaxBlockRhs * kPad);
-        if (cudaFuncSetAttribute(block_gram_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, gb) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(block_gram_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, gb / 2) !=
-                cudaSuccess)
+        const int gb = (int)(kGramStages * sizeof(float4) * kMaxBlockRhs * kTE * kGramSub);
+        if (cudaFuncSetAttribute(block_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, gb) != cudaSuccess)
             return LQ_ERR_CUDA;
         configured = true;
     }
-    const int g_same = block_grid(M, block_gram_kernel<true>, kGramThreads, kGramStages * gtile);
-    const int g_pair = block_grid(M, block_gram_kernel<false>, kGramThreads, 2 * kGramStages * gtile);
+    const int g_gram = block_grid(M, block_gram_kernel, t_gram, kGramStages * gtile);
     const int g_upd = block_grid(M, block_update_kernel, nthr, 2 * tile + mat);
     const int g_pup = block_grid(M, block_pupdate_kernel, nthr, tile + mat);
     auto f4 = [](const char* q) { return reinterpret_cast<const float4*>(q); };
     auto w4 = [](char* q) { return reinterpret_cast<float4*>(q); };
-    // the N x N sum of nb blocks' partials into host memory (same = A^dag A: made exactly Hermitian)
-    auto gram_sum = [&](int nb, bool same, std::vector<cd>& G) -> int {
-        launch_pdl(gram_final_kernel, (N * N + 7) / 8, 256, 0, s, partial, nb, N, Gd);
+    // G = A^dag A: the N x N sum of the blocks' partials into host memory, made exactly Hermitian
+    auto gram = [&](const char* A, std::vector<cd>& G) -> int {
+        // tile buffers; the final reduction reuses them (N x N double2 fit in one buffer)
+        launch_pdl(block_gram_kernel, g_gram, t_gram, kGramStages * gtile, s, f4(A), stride4, M, N, partial);
+        launch_pdl(gram_final_kernel, (N * N + 7) / 8, 256, 0, s, partial, g_gram, N, Gd);
         if (cudaMemcpyAsync(hostbuf, Gd, sizeof(double2) * N * N, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return LQ_ERR_CUDA;
         G.resize(N * N);
-        for (int e = 0; e < N * N; ++e) G[e] = cd(hostbuf[e].x, hostbuf[e].y);
-        if (same)
-            for (int i = 0; i < N; ++i)
-                for (int j = 0; j < i; ++j) G[i * N + j] = std::conj(G[j * N + i]);
+        for (int i = 0; i < N; ++i)
+            for (int j = 0; j < N; ++j) {
+                const double2 v = hostbuf[i <= j ? i * N + j : j * N + i];
+                G[i * N + j] = i <= j ? cd(v.x, v.y) : cd(v.x, -v.y);
+            }
         return LQ_OK;
     };
-    auto gram = [&](const char* A, const char* Bm, std::vector<cd>& G) -> int {
-        // tile buffers; the final reduction reuses them ([8 warps][N][16] double2 fit in kGramStages buffers)
-        const int nb = A == Bm ? g_same : g_pair;
-        if (A == Bm)
-            launch_pdl(block_gram_kernel<true>, nb, kGramThreads, kGramStages * gtile, s, f4(A), f4(Bm), stride4, M, N,
-                                                                                 partial);
-        else
-            launch_pdl(block_gram_kernel<false>, nb, kGramThreads, 2 * kGramStages * gtile, s, f4(A), f4(Bm), stride4, M, N,
-                                                                                      partial);
-        return gram_sum(nb, A == Bm, G);
-    };
+    // an N x N matrix to the device (through hostbuf: every gram() synchronises the stream before the
+    // host writes hostbuf again, so the copy has been made by then)
     auto upload = [&](const std::vector<cd>& Mx) -> int {
         float2* hf = reinterpret_cast<float2*>(hostbuf);
         for (int e = 0; e < N * N; ++e) hf[e] = make_float2((float)Mx[e].real(), (float)Mx[e].imag());
@@ -457,7 +485,7 @@ int block_cg(const BlockCgOps& ops, char* X, const char* Bv, char* R, char* P, c
         cudaMemcpyAsync(P, Bv, stride * N, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return LQ_ERR_CUDA;
     std::vector<cd> rho, rho0, delta, alpha, beta, rhonew;
-    int rc = gram(R, R, rho);
+    int rc = gram(R, rho);
     if (rc) return rc;
     rho0 = rho;
     int it = 0;
@@ -466,13 +494,13 @@ int block_cg(const BlockCgOps& ops, char* X, const char* Bv, char* R, char* P, c
         for (int j = 0; j < N; ++j) done = done && rho[j * N + j].real() <= tol * tol * rho0[j * N + j].real();
         if (done) break;
         if ((rc = ops.apply(ops.ctx, Q, P))) return rc;
-        // Delta = P^dag A P: from K P when the operator leaves it (A = K^dag K)
-        if ((rc = ops.kimage ? gram(ops.kimage, ops.kimage, delta) : gram(P, Q, delta))) return rc;
+        // Delta = P^dag A P = (K P)^dag (K P), from the K P the operator leaves in kimage
+        if ((rc = gram(ops.kimage, delta))) return rc;
         if (!chol_solve(delta, rho, alpha, N)) break;  // block lost rank: hand back to the outer loop
         if ((rc = upload(alpha))) return rc;
         // X += P alpha ; R -= Q alpha
         launch_pdl(block_update_kernel, g_upd, nthr, 2 * tile + mat, s, w4(X), f4(P), w4(R), f4(Q), stride4, M, N, Md);
-        if ((rc = gram(R, R, rhonew))) return rc;
+        if ((rc = gram(R, rhonew))) return rc;
         if (!chol_solve(rho, rhonew, beta, N)) {
             ++it;
             break;

@@ -9,11 +9,11 @@ namespace lq {
 
 constexpr int kMaxBlockRhs = 16;
 
-// The operator the block CG iterates: out = A in for all N columns at once.
-// For A = K^dag K, kimage (if not null) is the buffer in which apply leaves
-// K in (same column layout and stride as in): then P^dag A P = (K P)^dag (K P)
-// is formed as the Gram of K P with itself, which reads N columns instead of
-// 2N and is Hermitian positive semidefinite by construction.
+// The operator the block CG iterates: out = A in for all N columns at once,
+// A = K^dag K.  kimage is the buffer in which apply leaves K in (same column
+// layout and stride as in): P^dag A P = (K P)^dag (K P) is formed as the Gram
+// of K P with itself, which reads N columns instead of 2N and is Hermitian
+// positive semidefinite by construction.
 struct BlockCgOps {
     void* ctx;
     int (*apply)(void* ctx, char* out, const char* in);
@@ -30,6 +30,8 @@ inline size_t block_cg_scratch_bytes(int N) {
 // scratch fields of the same shape; ws: block_cg_scratch_bytes(N) device
 // bytes; hostbuf: N*N pinned double2.  Stops when every column's residual is
 // below tol times its start, when the block loses rank, or after maxiter.
+// LQ_ERR_ARG if N is outside 1..kMaxBlockRhs, stride is not a multiple of 16
+// or ops.kimage is null.
 int block_cg(const BlockCgOps& ops, char* X, const char* B, char* R, char* P, char* Q, size_t stride, long nsites,
              int N, double tol, int maxiter, void* ws, double2* hostbuf, cudaStream_t s, int* iters);
 
