@@ -43,6 +43,13 @@ CONFIGS = {
 }
 
 
+# single solves for profiling: 24^3x48, m = 0.02, smooth links (18-real), the 12 point sources of one
+# site, to 1e-10 (full D^dag D or the even-odd normal equations; block CG over the 12, or FP64 CG on
+# the first); the uneven batch 8^4..20^4 x 4 (even-odd, FP16 inner) batched or one lattice after another
+SOLVES = ("eo_block_24x3x48", "full_block_24x3x48", "eo_fp64_24x3x48", "full_fp64_24x3x48",
+          "batch_uneven_8x4_to_20x4", "seq_uneven_8x4_to_20x4")
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -58,6 +65,8 @@ def parse():
                     help="time only the 12-RHS and domain-wall hops (the workload of their ncu captures)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the CPU baseline, e2e and per-precision table (for profiler runs)")
+    ap.add_argument("--solve", choices=sorted(SOLVES),
+                    help="run only this solve, --steps times, one JSON line each (the workload of its ncu captures)")
     return ap.parse_args()
 
 
@@ -345,6 +354,9 @@ def main():
         return
     if args.su3_only:
         su3_only(args)
+        return
+    if args.solve:
+        solve_only(args)
         return
 
     import torch
@@ -780,6 +792,71 @@ def hops_only(args):
     U5 = inputs.gauge_field((16, 16, 16, 16), "smooth", seed=1004)
     out.update(dwf_hops(lqcd, torch, st, hbm, U5, args.steps, precs=(("f32", 1), ("f16", 2))))
     print(json.dumps({"hops_only": out}))
+
+
+def solve_only(args):
+    """One named solve (SOLVES), run args.steps times: the workload of the solver profiles."""
+    import torch
+
+    from paper_2001_07557_gb300 import build as lqbuild
+    from paper_2001_07557_gb300 import inputs, lqcd
+
+    lqbuild.build()
+    name = args.solve
+    if "uneven" in name:
+        shapes = [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 16), (20, 20, 20, 20)]
+        hs, bs, xs = [], [], []
+        for i, dd in enumerate(shapes):
+            Vd = int(np.prod(dd))
+            hs.append(lqcd.lq_create(lqcd.make_params(dd, mass=0.02, compress12=True),
+                                     torch.from_numpy(inputs.gauge_field(dd, "smooth", seed=1300 + i)).cuda()))
+            bs.append(torch.from_numpy(inputs.gaussian_spinor(Vd // 2, seed=2300 + i, nrhs=4)).cuda())
+            xs.append(torch.zeros_like(bs[-1]))
+        cp = lqcd.make_cg_params(lqcd.LQ_OP_WILSON_EO_NORMAL, lqcd.LQ_CG_MIXED, lqcd.LQ_F64, nrhs=4, tol=1e-10,
+                                 inner=lqcd.LQ_F16)
+
+        def run():
+            if name.startswith("batch"):
+                return lqcd.lq_batch_cg_solve(hs, xs, bs, cp, check=False)
+            rc, st = 0, []
+            for h, x, b in zip(hs, xs, bs):
+                r, s_ = lqcd.cg_solve(h, x, b, cp, check=False)
+                rc, st = rc or r, st + list(s_)
+            return rc, st
+    else:
+        dims = (24, 24, 24, 48)
+        V = int(np.prod(dims))
+        U = inputs.gauge_field(dims, "smooth", seed=1003)
+        h = lqcd.lq_create(lqcd.make_params(dims, mass=0.02, compress12=False), torch.from_numpy(U).cuda())
+        eo = name.startswith("eo")
+        src = inputs.point_sources(V)
+        if eo:
+            src = np.ascontiguousarray(inputs.to_half(src, dims, 0))
+        src = torch.from_numpy(src).cuda()
+        b = torch.empty_like(src)
+        lqcd.dslash_dag_apply(h, b, src, lqcd.LQ_F64, lqcd.LQ_SCHUR_EVEN if eo else lqcd.LQ_FULL, nrhs=12)
+        del src
+        n = 12 if "block" in name else 1
+        b = b[:n].contiguous()
+        xs = [torch.zeros_like(b)]
+        op = lqcd.LQ_OP_WILSON_EO_NORMAL if eo else lqcd.LQ_OP_WILSON_NORMAL
+        mode = lqcd.LQ_CG_BLOCK if n == 12 else lqcd.LQ_CG_PLAIN
+        cp = lqcd.make_cg_params(op, mode, lqcd.LQ_F64, nrhs=n, tol=1e-10, inner=lqcd.LQ_F32)
+
+        def run():
+            return lqcd.cg_solve(h, xs[0], b, cp, check=False)
+    for _ in range(args.steps):
+        for x in xs:
+            x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, st = run()
+        sec = time.perf_counter() - t0
+        print(json.dumps({"solve": name, "status": rc, "seconds": sec, "max_iters": max(z.iters for z in st),
+                          "max_outer": max(z.outer_iters for z in st),
+                          "max_true_rel_residual": max(z.true_rel_residual for z in st)}), flush=True)
+        if rc:
+            sys.exit(1)
 
 
 def halo_emulation(lqcd, torch, hbm, reps=20):

@@ -44,7 +44,7 @@ namespace {
 // of the result instead).  Blocks have a whole number of kTE-thread groups
 // (see block_threads).
 constexpr int kTE = 64;
-constexpr int kGrid = 152 * 4;  // grid of the block kernels (partials sized for it)
+constexpr int kGrid = 152 * 4;  // most blocks of the Gram kernel (its partial sums are sized for it)
 constexpr int kGramStages = 3;
 
 __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, bool valid) {
@@ -371,16 +371,17 @@ __global__ void __launch_bounds__(32 * ((kMaxBlockRhs + 1) / 2)) block_pupdate_k
 }
 
 // grid of a block kernel: every SM gets the same number of resident blocks
-// (a partial second wave would leave most SMs idle at the end), at most kGrid
+// (a partial second wave would leave most SMs idle at the end), at most cap
+// (kGrid for the Gram kernel, whose partial sums are sized for it)
 template <typename K>
-int block_grid(long M, K kern, int threads, size_t smem) {
+int block_grid(long M, K kern, int threads, size_t smem, long cap = kGrid) {
     const long want = (M + kTE - 1) / kTE;
     int per_sm = 0, dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess || per_sm < 1)
         per_sm = 1, sms = 152;
-    const long resident = std::min<long>((long)per_sm * sms, kGrid);
+    const long resident = std::min<long>((long)per_sm * sms, cap);
     return (int)std::min<long>(want, resident);
 }
 
@@ -451,8 +452,8 @@ int block_cg(const BlockCgOps& ops, char* X, const char* Bv, char* R, char* P, c
         configured = true;
     }
     const int g_gram = block_grid(M, block_gram_kernel, t_gram, kGramStages * gtile);
-    const int g_upd = block_grid(M, block_update_kernel, nthr, 2 * tile + mat);
-    const int g_pup = block_grid(M, block_pupdate_kernel, nthr, tile + mat);
+    const int g_upd = block_grid(M, block_update_kernel, nthr, 2 * tile + mat, 1L << 30);
+    const int g_pup = block_grid(M, block_pupdate_kernel, nthr, tile + mat, 1L << 30);
     auto f4 = [](const char* q) { return reinterpret_cast<const float4*>(q); };
     auto w4 = [](char* q) { return reinterpret_cast<float4*>(q); };
     // G = A^dag A: the N x N sum of the blocks' partials into host memory, made exactly Hermitian
