@@ -456,13 +456,28 @@ int block_cg(const BlockCgOps& ops, char* X, const char* Bv, char* R, char* P, c
     const int g_pup = block_grid(M, block_pupdate_kernel, nthr, tile + mat, 1L << 30);
     auto f4 = [](const char* q) { return reinterpret_cast<const float4*>(q); };
     auto w4 = [](char* q) { return reinterpret_cast<float4*>(q); };
-    // G = A^dag A: the N x N sum of the blocks' partials into host memory, made exactly Hermitian
-    auto gram = [&](const char* A, std::vector<cd>& G) -> int {
+    // the Gram of K P runs on a second stream beside the operator's K^dag stage
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t kdone = nullptr;
+    struct Release {
+        cudaStream_t& s2;
+        cudaEvent_t& ev;
+        ~Release() {
+            if (ev) cudaEventDestroy(ev);
+            if (s2) cudaStreamDestroy(s2);
+        }
+    } release_{s2, kdone};
+    if (cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&kdone, cudaEventDisableTiming) != cudaSuccess)
+        return LQ_ERR_CUDA;
+    // G = A^dag A: the N x N sum of the blocks' partials into host memory, made exactly Hermitian;
+    // the kernels and the copy run on stream q, and the host waits for them
+    auto gram = [&](const char* A, std::vector<cd>& G, cudaStream_t q) -> int {
         // tile buffers; the final reduction reuses them (N x N double2 fit in one buffer)
-        launch_pdl(block_gram_kernel, g_gram, t_gram, kGramStages * gtile, s, f4(A), stride4, M, N, partial);
-        launch_pdl(gram_final_kernel, (N * N + 7) / 8, 256, 0, s, partial, g_gram, N, Gd);
-        if (cudaMemcpyAsync(hostbuf, Gd, sizeof(double2) * N * N, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess)
+        launch_pdl(block_gram_kernel, g_gram, t_gram, kGramStages * gtile, q, f4(A), stride4, M, N, partial);
+        launch_pdl(gram_final_kernel, (N * N + 7) / 8, 256, 0, q, partial, g_gram, N, Gd);
+        if (cudaMemcpyAsync(hostbuf, Gd, sizeof(double2) * N * N, cudaMemcpyDeviceToHost, q) != cudaSuccess ||
+            cudaStreamSynchronize(q) != cudaSuccess)
             return LQ_ERR_CUDA;
         G.resize(N * N);
         for (int i = 0; i < N; ++i)
@@ -486,7 +501,7 @@ int block_cg(const BlockCgOps& ops, char* X, const char* Bv, char* R, char* P, c
         cudaMemcpyAsync(P, Bv, stride * N, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return LQ_ERR_CUDA;
     std::vector<cd> rho, rho0, delta, alpha, beta, rhonew;
-    int rc = gram(R, rho);
+    int rc = gram(R, rho, s);
     if (rc) return rc;
     rho0 = rho;
     int it = 0;
@@ -494,14 +509,20 @@ int block_cg(const BlockCgOps& ops, char* X, const char* Bv, char* R, char* P, c
         bool done = true;
         for (int j = 0; j < N; ++j) done = done && rho[j * N + j].real() <= tol * tol * rho0[j * N + j].real();
         if (done) break;
-        if ((rc = ops.apply(ops.ctx, Q, P))) return rc;
-        // Delta = P^dag A P = (K P)^dag (K P), from the K P the operator leaves in kimage
-        if ((rc = gram(ops.kimage, delta))) return rc;
+        // T = K P; then Delta = P^dag A P = T^dag T on s2 while Q = K^dag T runs on s.  The host
+        // waits for Delta only (the Gram kernels read T, which the K^dag stage only reads too; s2's
+        // copy into hostbuf comes after s's last use of it, which precedes K P in s)
+        if ((rc = ops.apply(ops.ctx, Q, P, 0))) return rc;
+        if (cudaEventRecord(kdone, s) != cudaSuccess || cudaStreamWaitEvent(s2, kdone, 0) != cudaSuccess)
+            return LQ_ERR_CUDA;
+        if ((rc = ops.apply(ops.ctx, Q, P, 1))) return rc;
+        if ((rc = gram(ops.kimage, delta, s2))) return rc;
+        // s2's Gram sums (partial, Gd) are read again by s's next Gram only after this point
         if (!chol_solve(delta, rho, alpha, N)) break;  // block lost rank: hand back to the outer loop
         if ((rc = upload(alpha))) return rc;
         // X += P alpha ; R -= Q alpha
         launch_pdl(block_update_kernel, g_upd, nthr, 2 * tile + mat, s, w4(X), f4(P), w4(R), f4(Q), stride4, M, N, Md);
-        if ((rc = gram(R, rhonew))) return rc;
+        if ((rc = gram(R, rhonew, s))) return rc;
         if (!chol_solve(rho, rhonew, beta, N)) {
             ++it;
             break;

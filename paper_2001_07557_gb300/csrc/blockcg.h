@@ -9,14 +9,16 @@ namespace lq {
 
 constexpr int kMaxBlockRhs = 16;
 
-// The operator the block CG iterates: out = A in for all N columns at once,
-// A = K^dag K.  kimage is the buffer in which apply leaves K in (same column
-// layout and stride as in): P^dag A P = (K P)^dag (K P) is formed as the Gram
-// of K P with itself, which reads N columns instead of 2N and is Hermitian
-// positive semidefinite by construction.
+// The operator the block CG iterates, A = K^dag K, for all N columns at once
+// and in two stages on the solver's stream: apply(ctx, out, in, 0) leaves
+// K in in kimage (same column layout and stride as in), apply(ctx, out, in, 1)
+// writes out = K^dag kimage.  P^dag A P = (K P)^dag (K P) is formed as the
+// Gram of K P with itself, which reads N columns instead of 2N and is
+// Hermitian positive semidefinite by construction; it runs on a second stream
+// while the second stage runs.
 struct BlockCgOps {
     void* ctx;
-    int (*apply)(void* ctx, char* out, const char* in);
+    int (*apply)(void* ctx, char* out, const char* in, int stage);
     const char* kimage;
 };
 

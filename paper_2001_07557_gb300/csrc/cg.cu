@@ -102,8 +102,9 @@ int make_ctl(lq_handle* h, const OpGeom& og, Ctl* c, cudaStream_t s) {
     return LQ_OK;
 }
 
-int apply_normal(lq_handle* h, const OpGeom& og, int prec, char* out, const char* in, char* t, char* tmp,
-                 cudaStream_t st, const Ctl* c) {
+// t = K in, the first half of the normal operator (with the fused |K in|^2 when c is given)
+int apply_k(lq_handle* h, const OpGeom& og, int prec, char* t, const char* in, char* tmp, cudaStream_t st,
+            const Ctl* c = nullptr) {
     int rc;
     if (c) {
         h->red_partial = c->hop_partial;
@@ -120,13 +121,23 @@ int apply_normal(lq_handle* h, const OpGeom& og, int prec, char* out, const char
     h->red_partial = nullptr;
     h->red_ticket = nullptr;
     h->red_st = nullptr;
-    if (rc) return rc;
+    return rc;
+}
+
+// out = K^dag t, the second half
+int apply_kdag(lq_handle* h, const OpGeom& og, int prec, char* out, const char* t, char* tmp, cudaStream_t st) {
     switch (og.op) {
     case LQ_OP_WILSON_NORMAL: return native_wilson_full(h, prec, out, t, og.nrhs, true, st);
     case LQ_OP_WILSON_EO_NORMAL: return native_wilson_schur(h, prec, out, t, tmp, og.nrhs, true, st);
     case LQ_OP_DWF_EO_NORMAL: return native_dwf_schur(h, prec, out, t, tmp, true, st);
     default: return native_dwf(h, prec, out, t, true, st);
     }
+}
+
+int apply_normal(lq_handle* h, const OpGeom& og, int prec, char* out, const char* in, char* t, char* tmp,
+                 cudaStream_t st, const Ctl* c) {
+    const int rc = apply_k(h, og, prec, t, in, tmp, st, c);
+    return rc ? rc : apply_kdag(h, og, prec, out, t, tmp, st);
 }
 
 // warp partials per group written by the fused-norm launch of apply_normal
@@ -325,9 +336,11 @@ struct BlockCtx {
     cudaStream_t s;
 };
 
-int block_apply(void* ctx, char* out, const char* in) {
+// stage 0: t = K in; stage 1: out = K^dag t
+int block_apply(void* ctx, char* out, const char* in, int stage) {
     BlockCtx* c = static_cast<BlockCtx*>(ctx);
-    return apply_normal(c->h, *c->og, LQ_F32, out, in, c->t, c->tmp, c->s);
+    return stage == 0 ? apply_k(c->h, *c->og, LQ_F32, c->t, in, c->tmp, c->s)
+                      : apply_kdag(c->h, *c->og, LQ_F32, out, c->t, c->tmp, c->s);
 }
 
 // FP32 residuals of the middle level are accurate to roughly this relative size.
