@@ -517,7 +517,7 @@ int block_cg(const BlockCgOps& ops, char* X, const char* Bv, char* R, char* P, c
             return LQ_ERR_CUDA;
         if ((rc = ops.apply(ops.ctx, Q, P, 1))) return rc;
         if ((rc = gram(ops.kimage, delta, s2))) return rc;
-        // s2's Gram sums (partial, Gd) are read again by s's next Gram only after this point
+        // s2 is idle from here on: s's next Gram may overwrite partial and Gd
         if (!chol_solve(delta, rho, alpha, N)) break;  // block lost rank: hand back to the outer loop
         if ((rc = upload(alpha))) return rc;
         // X += P alpha ; R -= Q alpha
