@@ -105,3 +105,22 @@ def test_tune_file_reader(bench, tmp_path):
     assert got["blocks"] == 912
     assert got["sites_per_item"] == {"8x8x8x8": 128, "12x12x12x12": 512}
     assert bench.read_tune_file(str(tmp_path / "missing.txt"), shapes) is None
+
+
+def test_solve_names_parse_and_name_a_workload(bench, monkeypatch):
+    """Every --solve name parses and names one workload: the uneven batch (batched or one lattice
+    after another) or a 24^3x48 solve (full or even-odd; block CG over the 12 sources or FP64 CG)."""
+    import sys
+
+    for name in bench.SOLVES:
+        monkeypatch.setattr(sys, "argv", ["bench.py", "--solve", name, "--steps", "1"])
+        args = bench.parse()
+        assert args.solve == name and args.steps == 1
+        if "uneven" in name:
+            assert name.split("_")[0] in ("batch", "seq")
+        else:
+            head, kind, shape = name.split("_")
+            assert head in ("eo", "full") and kind in ("block", "fp64") and shape == "24x3x48"
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--solve", "no_such_solve"])
+    with pytest.raises(SystemExit):
+        bench.parse()
