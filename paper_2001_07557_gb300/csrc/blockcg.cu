@@ -325,16 +325,26 @@ __global__ void __launch_bounds__(32 * ((kMaxBlockRhs + 1) / 2)) block_pupdate_k
     float4* __restrict__ P, const float4* __restrict__ R, size_t stride4, long M, int N, const float2* __restrict__ b) {
     pdl_enter();
     extern __shared__ float4 sm[];
-    float4* sP = sm;
-    float2* sb = reinterpret_cast<float2*>(sm + (size_t)N * kTE);
+    const size_t buf = (size_t)N * kTE;  // the P tile of one of the two stages
+    float2* sb = reinterpret_cast<float2*>(sm + 2 * buf);
     for (int e = threadIdx.x; e < N * N; e += blockDim.x) sb[e] = b[e];
     const int lane = threadIdx.x & 31;
     const WarpCols wc = warp_cols_split(N);
     const int j0 = wc.c0, j1 = wc.c1;
     const bool has0 = wc.has0, has1 = wc.has1;
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (long e0 = (long)blockIdx.x * kTE; e0 < M; e0 += (long)gridDim.x * kTE) {
-        stage_tile(sP, P, stride4, e0, M, N);
+    const long step = (long)gridDim.x * kTE;
+    auto stage = [&](long e0, int k) {
+        if (e0 < M) stage_tile(sm + k * buf, P, stride4, e0, M, N);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");  // one group per tile (maybe empty)
+    };
+    stage((long)blockIdx.x * kTE, 0);
+    int kb = 0;
+    for (long e0 = (long)blockIdx.x * kTE; e0 < M; e0 += step, kb ^= 1) {
+        // the next tile's copies run while this one is updated (it is this block's own, and
+        // written only in a later iteration)
+        stage(e0 + step, kb ^ 1);
+        const float4* sP = sm + kb * buf;
         float4 y[2][2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
@@ -343,7 +353,7 @@ __global__ void __launch_bounds__(32 * ((kMaxBlockRhs + 1) / 2)) block_pupdate_k
             y[0][u] = ok ? R[(size_t)j0 * stride4 + ge] : z4;
             y[1][u] = ok && has1 ? R[(size_t)j1 * stride4 + ge] : z4;
         }
-        cp_async_wait_all();
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // this tile has landed
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < kMaxBlockRhs; ++k) {
@@ -358,7 +368,7 @@ __global__ void __launch_bounds__(32 * ((kMaxBlockRhs + 1) / 2)) block_pupdate_k
                 }
             }
         }
-        __syncthreads();  // every warp has read the tile of P before it is overwritten
+        __syncthreads();  // every warp has read stage kb before the next iteration refills it
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             const long ge = e0 + lane + 32 * u;
@@ -368,6 +378,7 @@ __global__ void __launch_bounds__(32 * ((kMaxBlockRhs + 1) / 2)) block_pupdate_k
             }
         }
     }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 // grid of a block kernel: every SM gets the same number of resident blocks
@@ -452,8 +463,10 @@ int block_cg(const BlockCgOps& ops, char* X, const char* Bv, char* R, char* P, c
         configured = true;
     }
     const int g_gram = block_grid(M, block_gram_kernel, t_gram, kGramStages * gtile);
-    const int g_upd = block_grid(M, block_update_kernel, nthr, 2 * tile + mat, 1L << 30);
-    const int g_pup = block_grid(M, block_pupdate_kernel, nthr, tile + mat, 1L << 30);
+    const size_t s_upd = 2 * tile + mat;  // the P and Q tiles + the N x N matrix
+    const size_t s_pup = 2 * tile + mat;  // two stages of the P tile + the N x N matrix
+    const int g_upd = block_grid(M, block_update_kernel, nthr, s_upd, 1L << 30);
+    const int g_pup = block_grid(M, block_pupdate_kernel, nthr, s_pup, 1L << 30);
     auto f4 = [](const char* q) { return reinterpret_cast<const float4*>(q); };
     auto w4 = [](char* q) { return reinterpret_cast<float4*>(q); };
     // the Gram of K P runs on a second stream beside the operator's K^dag stage
@@ -521,7 +534,7 @@ int block_cg(const BlockCgOps& ops, char* X, const char* Bv, char* R, char* P, c
         if (!chol_solve(delta, rho, alpha, N)) break;  // block lost rank: hand back to the outer loop
         if ((rc = upload(alpha))) return rc;
         // X += P alpha ; R -= Q alpha
-        launch_pdl(block_update_kernel, g_upd, nthr, 2 * tile + mat, s, w4(X), f4(P), w4(R), f4(Q), stride4, M, N, Md);
+        launch_pdl(block_update_kernel, g_upd, nthr, s_upd, s, w4(X), f4(P), w4(R), f4(Q), stride4, M, N, Md);
         if ((rc = gram(R, rhonew, s))) return rc;
         if (!chol_solve(rho, rhonew, beta, N)) {
             ++it;
@@ -529,7 +542,7 @@ int block_cg(const BlockCgOps& ops, char* X, const char* Bv, char* R, char* P, c
         }
         if ((rc = upload(beta))) return rc;
         // P = R + P beta
-        launch_pdl(block_pupdate_kernel, g_pup, nthr, tile + mat, s, w4(P), f4(R), stride4, M, N, Md);
+        launch_pdl(block_pupdate_kernel, g_pup, nthr, s_pup, s, w4(P), f4(R), stride4, M, N, Md);
         rho = rhonew;
     }
     *iters = it;
