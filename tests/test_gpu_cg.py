@@ -250,6 +250,36 @@ def test_block_cg_even_odd_gaussian():
         assert rel_err(xg[k], x_or) < 1e-7
 
 
+@pytest.mark.parametrize("op", [lqcd.LQ_OP_WILSON_EO_NORMAL, lqcd.LQ_OP_WILSON_NORMAL])
+def test_block_cg_repeats_bit_for_bit(op):
+    """The Gram of K P runs on a second stream beside the K^dag stage of the operator; the order of
+    the two streams' work is fixed by events, so repeated solves give the same bits (a missing
+    dependency would let the Gram read a half-written K P, or overwrite the sums the other stream
+    reads, and change the iterates).  Checked against the oracle's operator once."""
+    dims = (12, 12, 12, 16)
+    V = int(np.prod(dims))
+    m = 0.05
+    U = inputs.gauge_field(dims, "smooth", seed=1009)
+    n = V // 2 if op == lqcd.LQ_OP_WILSON_EO_NORMAL else V
+    b = inputs.gaussian_spinor(n, seed=2009, nrhs=12)
+    with Handle(dims, U, mass=m) as H:
+        bd = dev(b)
+        cp = lqcd.make_cg_params(op, lqcd.LQ_CG_BLOCK, lqcd.LQ_F64, nrhs=12, tol=1e-10)
+        runs = []
+        for _ in range(3):
+            xd = torch.zeros_like(bd)
+            rc, st = lqcd.cg_solve(H.h, xd, bd, cp)
+            assert rc == 0
+            runs.append((xd, [s_.iters for s_ in st], [s_.true_rel_residual for s_ in st]))
+    for xd, iters, res in runs[1:]:
+        assert torch.equal(xd, runs[0][0]) and iters == runs[0][1] and res == runs[0][2]
+    assert max(runs[0][2]) < 1e-10
+    oop = oracle.OP_WILSON_EO if op == lqcd.LQ_OP_WILSON_EO_NORMAL else oracle.OP_WILSON
+    xg = host(runs[0][0])
+    prm = oracle.params(dims, mass=m)
+    assert rel_err(oracle.apply_normal(oop, xg[5], U, prm), b[5]) < 1e-9
+
+
 @pytest.mark.parametrize("nrhs", [1, 3, 16])
 def test_block_cg_ragged_tiles_and_sizes(nrhs):
     """Block sizes 1, 3 (odd: one warp owns a single column) and 16 (the
