@@ -280,10 +280,12 @@ def test_block_cg_repeats_bit_for_bit(op):
     assert rel_err(oracle.apply_normal(oop, xg[5], U, prm), b[5]) < 1e-9
 
 
-@pytest.mark.parametrize("nrhs", [1, 3, 16])
+@pytest.mark.parametrize("nrhs", [1, 3, 4, 9, 16])
 def test_block_cg_ragged_tiles_and_sizes(nrhs):
-    """Block sizes 1, 3 (odd: one warp owns a single column) and 16 (the
-    largest) on a lattice whose field length is not a whole number of tiles."""
+    """Block sizes 1, 3 (odd: one warp owns a single column), 4 (one whole
+    group of the Gram kernel), 9 (a last group of one column: every kind of
+    Gram block, diagonal or not, whole or ragged) and 16 (the largest) on a
+    lattice whose field length is not a whole number of tiles."""
     dims = (6, 2, 2, 6)
     V = int(np.prod(dims))
     m = 0.1
